@@ -1,0 +1,152 @@
+/*
+ * map.h -- C ABI of the GB300 MAP accepting-cycle detection library (libmapgpu.so).
+ *
+ * MAP (Section 2 of Barnat, Brim, Ceska, "DiVinE-CUDA -- A Tool for GPU
+ * Accelerated LTL Model Checking", PDMC 2009) decides whether a directed graph
+ * with accepting vertices has a cycle through an accepting vertex.  It fixes an
+ * order on the accepting vertices and computes, for every vertex, its maximal
+ * accepting predecessor map(v) by propagating values to a fix-point; an
+ * accepting vertex that is its own map value lies on an accepting cycle;
+ * otherwise every map value is made non-accepting and the procedure restarts,
+ * until a cycle is found or no accepting vertex is left.  The propagation is a
+ * (max, id) sparse matrix-vector product over a CSR matrix (Section 2),
+ * repeated to the fix-point.
+ *
+ * GRAPH CONVENTION.  The CSR handed in is the pull matrix of the transposed
+ * graph on which MAP runs (Section 2): row v lists the successors of state v in
+ * the state graph G, i.e. the predecessors of v in the transposed graph.  So
+ *     map(v) = max { u accepting : v reaches u along rows by >= 1 edge }.
+ * The order on accepting vertices is the vertex id; "no value" is below every
+ * id and is reported as MAP_NONE.
+ *
+ * All entry points return a map_status code; nothing else crosses the ABI (no
+ * exceptions, no aborts).  map_last_error() gives a message for the calling
+ * host thread's last failure.  A map_graph is used by one host thread at a time.
+ */
+#ifndef MAPGPU_MAP_H
+#define MAPGPU_MAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define MAP_API __attribute__((visibility("default")))
+#else
+#define MAP_API
+#endif
+
+#define MAP_NONE 0xFFFFFFFFu /* "no value" in map vectors; "no witness" */
+
+typedef enum {
+    MAP_OK = 0,
+    MAP_ERR_ARG = 1,       /* bad argument (NULL handle, n out of range, ...) */
+    MAP_ERR_CSR = 2,       /* invalid CSR: rowptr[0] != 0, decreasing rowptr, colidx >= n */
+    MAP_ERR_OOM = 3,       /* device or host allocation failed */
+    MAP_ERR_CUDA = 4,      /* a CUDA call failed; see map_last_error() */
+    MAP_ERR_TIMEOUT = 5,   /* a bounded device-side wait gave up */
+    MAP_ERR_LIMIT = 6,     /* max_outer / max_inner reached before the verdict */
+    MAP_ERR_NOT_READY = 7, /* (serving) the job has not finished yet */
+    MAP_ERR_BUSY = 8       /* (serving) no room for the job now */
+} map_status;
+
+enum { MAP_NO_CYCLE = 0, MAP_CYCLE = 1 };
+
+/* Propagation schedule.
+ *  MAP_SCHED_SYNC: synchronous rounds -- round k computes every value from the
+ *    values of round k-1; round 1 relaxes every row, round k+1 the rows that
+ *    read a vertex changed in round k.  Round counts and relaxation counts are
+ *    canonical (identical to the CPU reference) and include the final round in
+ *    which nothing changed.
+ *  MAP_SCHED_ASYNC: in-place sweeps over the same frontiers; values written in
+ *    a sweep may be read in the same sweep.  The fix-point (the least one, which
+ *    is unique) and therefore every map vector, the verdict, the witness and the
+ *    outer count are the same as under SYNC; the sweep count is at most the
+ *    SYNC round count. */
+enum { MAP_SCHED_SYNC = 0, MAP_SCHED_ASYNC = 1 };
+
+/* opts.flags */
+#define MAP_FLAG_PROFILE 1u /* time the dense-round kernel with CUDA events (result.dense_ms) */
+
+/* Called after the fix-point of every outer iteration, before the cycle test
+ * and the elimination: map[v] is map(v) of that iteration (MAP_NONE if none),
+ * host memory valid during the call only; rounds is that iteration's round
+ * (or sweep) count.  Costs one device-to-host copy of n words per iteration. */
+typedef void (*map_trace_fn)(void *user, uint32_t outer, const uint32_t *map, uint32_t n, uint32_t rounds);
+
+typedef struct {
+    uint32_t sched;       /* MAP_SCHED_SYNC (0, default) or MAP_SCHED_ASYNC */
+    uint32_t max_outer;   /* stop with MAP_ERR_LIMIT after this many outer iterations; 0 = no limit */
+    uint32_t max_inner;   /* per outer iteration; 0 = n + 1, which the synchronous schedule never exceeds */
+    uint32_t flags;       /* MAP_FLAG_* */
+    map_trace_fn trace;   /* optional, see above */
+    void *user;           /* passed to trace */
+    uint32_t *rounds_out; /* optional host array: round count of outer iteration i at [i] */
+    uint32_t rounds_cap;  /* entries of rounds_out; later iterations are not stored */
+    uint32_t reserved[4]; /* must be zero */
+} map_opts;
+
+typedef struct {
+    uint32_t verdict;         /* MAP_CYCLE or MAP_NO_CYCLE */
+    uint32_t witness;         /* smallest v with map(v) = v, or MAP_NONE */
+    uint32_t outer_iters;     /* outer iterations executed (0 if no vertex is accepting) */
+    uint32_t inner_canonical; /* 1 if inner_iters counts synchronous rounds (SYNC), 0 for ASYNC sweeps */
+    uint64_t inner_iters;     /* rounds (or sweeps) summed over outer iterations */
+    uint64_t relaxations;     /* edges examined, summed over rounds */
+    uint64_t edges_total;     /* m x outer_iters: the edges a fix-point must examine at least once */
+    double device_ms;         /* stream time of the whole run (CUDA events) */
+    double dense_ms;          /* with MAP_FLAG_PROFILE: summed time of the dense-round kernel */
+    uint32_t dense_launches;  /* with MAP_FLAG_PROFILE: its launches */
+    uint32_t accepting_left;  /* accepting vertices left at the end */
+    uint64_t launches;        /* kernel launches issued by this run */
+} map_result;
+
+typedef struct map_graph map_graph; /* opaque: the device-resident graph and its work space */
+
+/*
+ * map_create -- copy a graph to the device and prepare it for map_run.
+ *   n        vertices, 1 <= n < 2^31 - 1 (bit 31 of a value word is reserved).
+ *   rowptr   n + 1 entries (u32), rowptr[0] = 0, non-decreasing; m = rowptr[n].
+ *   colidx   m entries (u32), each < n; may be NULL when m = 0.  Self-loops and
+ *            duplicate entries are allowed.
+ *   acc_bits ceil(n / 32) words: vertex v is accepting iff bit (v & 31) of word
+ *            v >> 5 is set (LSB first); bits at or above n are ignored.
+ *   cuda_stream  the cudaStream_t all work of this graph is issued on (NULL:
+ *            the legacy default stream).
+ * Every pointer may be host or device memory (told apart with
+ * cudaPointerGetAttributes); the library copies them and the caller keeps
+ * ownership.  Validation runs on the device; an invalid CSR returns
+ * MAP_ERR_CSR and no handle.  On success *out owns about
+ * 4*(2m + 6n) bytes of device memory until map_destroy.
+ */
+MAP_API int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const uint32_t *acc_bits,
+               void *cuda_stream, map_graph **out);
+
+/*
+ * map_run -- run MAP to its verdict (Section 2: propagate to the fix-point,
+ * self-map test, eliminate, restart).
+ *   opts     NULL for defaults (SYNC, no limits, no trace).
+ *   res      filled on MAP_OK and on MAP_ERR_LIMIT (with what was computed).
+ *   map_out  optional, n entries, host or device memory: the map vector of the
+ *            last outer iteration (all MAP_NONE when no vertex is accepting).
+ * The graph is not changed: the accepting set is restored at every call, so
+ * runs repeat exactly.  Blocks the calling thread until the result is known.
+ */
+MAP_API int map_run(map_graph *g, const map_opts *opts, map_result *res, uint32_t *map_out);
+
+/* map_destroy -- free the graph's device memory. NULL is accepted. */
+MAP_API int map_destroy(map_graph *g);
+
+/* map_graph_info -- n and m of a graph (either pointer may be NULL). */
+MAP_API int map_graph_info(const map_graph *g, uint32_t *n, uint64_t *m);
+
+/* map_last_error -- message of the calling thread's last failed call ("" if none). */
+MAP_API const char *map_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,228 @@
+"""Python binding of libmapgpu.so, the GB300 MAP accepting-cycle detection library.
+
+Argument marshalling only: every step of MAP (Section 2 of the DiVinE-CUDA paper)
+runs in the library's CUDA kernels.  The names follow the C ABI of
+``include/map.h``: ``map_create``, ``map_run``, ``map_destroy``.  Inputs may be
+numpy arrays (host memory) or CUDA torch tensors (device memory); PyTorch is
+used only for device memory and streams.
+
+There is no CPU fallback: importing works without a GPU, but every call that
+reaches the library fails loudly if the compiled library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmapgpu.so")
+
+MAP_NONE = 0xFFFFFFFF
+MAP_OK, MAP_ERR_ARG, MAP_ERR_CSR, MAP_ERR_OOM, MAP_ERR_CUDA, MAP_ERR_TIMEOUT, MAP_ERR_LIMIT, \
+    MAP_ERR_NOT_READY, MAP_ERR_BUSY = range(9)
+MAP_NO_CYCLE, MAP_CYCLE = 0, 1
+MAP_SCHED_SYNC, MAP_SCHED_ASYNC = 0, 1
+MAP_FLAG_PROFILE = 1
+STATUS_NAMES = ["MAP_OK", "MAP_ERR_ARG", "MAP_ERR_CSR", "MAP_ERR_OOM", "MAP_ERR_CUDA", "MAP_ERR_TIMEOUT",
+                "MAP_ERR_LIMIT", "MAP_ERR_NOT_READY", "MAP_ERR_BUSY"]
+
+# exported symbols of include/map.h (checked by the tests)
+EXPORTS = ["map_create", "map_run", "map_destroy", "map_graph_info", "map_last_error"]
+
+TRACE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32),
+                            ctypes.c_uint32, ctypes.c_uint32)
+
+
+class MapOpts(ctypes.Structure):
+    _fields_ = [
+        ("sched", ctypes.c_uint32),
+        ("max_outer", ctypes.c_uint32),
+        ("max_inner", ctypes.c_uint32),
+        ("flags", ctypes.c_uint32),
+        ("trace", TRACE_FN),
+        ("user", ctypes.c_void_p),
+        ("rounds_out", ctypes.POINTER(ctypes.c_uint32)),
+        ("rounds_cap", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 4),
+    ]
+
+
+class MapResult(ctypes.Structure):
+    _fields_ = [
+        ("verdict", ctypes.c_uint32),
+        ("witness", ctypes.c_uint32),
+        ("outer_iters", ctypes.c_uint32),
+        ("inner_canonical", ctypes.c_uint32),
+        ("inner_iters", ctypes.c_uint64),
+        ("relaxations", ctypes.c_uint64),
+        ("edges_total", ctypes.c_uint64),
+        ("device_ms", ctypes.c_double),
+        ("dense_ms", ctypes.c_double),
+        ("dense_launches", ctypes.c_uint32),
+        ("accepting_left", ctypes.c_uint32),
+        ("launches", ctypes.c_uint64),
+    ]
+
+
+class MapError(RuntimeError):
+    def __init__(self, code: int, what: str, msg: str):
+        self.code = code
+        super().__init__(f"{what}: {STATUS_NAMES[code] if 0 <= code < len(STATUS_NAMES) else code}: {msg}")
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the compiled library; raise if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmapgpu.so not found at {path}: build it with "
+                           f"`python -c 'import __graft_entry__ as g; g.build()'` (no CPU fallback exists)")
+    lib = ctypes.CDLL(path)
+    vp, u32 = ctypes.c_void_p, ctypes.c_uint32
+    lib.map_create.argtypes = [u32, vp, vp, vp, vp, ctypes.POINTER(vp)]
+    lib.map_run.argtypes = [vp, ctypes.POINTER(MapOpts), ctypes.POINTER(MapResult), vp]
+    lib.map_destroy.argtypes = [vp]
+    lib.map_graph_info.argtypes = [vp, ctypes.POINTER(u32), ctypes.POINTER(ctypes.c_uint64)]
+    lib.map_last_error.restype = ctypes.c_char_p
+    for f in ("map_create", "map_run", "map_destroy", "map_graph_info"):
+        getattr(lib, f).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().map_last_error().decode()
+
+
+def _ptr(x):
+    """(address, keep-alive) of a numpy array or torch tensor (host or device)."""
+    if x is None:
+        return None, None
+    if hasattr(x, "data_ptr"):  # torch tensor
+        return x.data_ptr(), x
+    a = np.ascontiguousarray(x, dtype=np.uint32)
+    return a.ctypes.data, a
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def map_create(n: int, rowptr, colidx, acc_bits, stream=None):
+    """Create a device-resident graph (see include/map.h).  Returns an opaque handle."""
+    lib = load()
+    rp, k1 = _ptr(rowptr)
+    ci, k2 = _ptr(colidx)
+    ab, k3 = _ptr(acc_bits)
+    h = ctypes.c_void_p()
+    rc = lib.map_create(n, rp, ci, ab, _stream_handle(stream), ctypes.byref(h))
+    if rc != MAP_OK:
+        raise MapError(rc, "map_create", last_error())
+    return h
+
+
+def map_destroy(handle) -> None:
+    if handle is not None and handle.value:
+        load().map_destroy(handle)
+        handle.value = None
+
+
+@dataclass
+class RunResult:
+    status: int
+    verdict: int
+    witness: int
+    outer: int
+    rounds: list
+    inner_iters: int
+    inner_canonical: bool
+    relaxations: int
+    edges_total: int
+    device_ms: float
+    dense_ms: float
+    dense_launches: int
+    accepting_left: int
+    launches: int
+    trace: list
+
+
+def map_run(handle, sched: int = MAP_SCHED_SYNC, max_outer: int = 0, max_inner: int = 0, flags: int = 0,
+            map_out=None, keep_trace: bool = False, hash_trace=None, rounds_cap: int = 1 << 16,
+            allow_limit: bool = False) -> RunResult:
+    """Run MAP on a created graph.  map_out: optional uint32 numpy array or CUDA tensor of n entries."""
+    lib = load()
+    opts = MapOpts()
+    opts.sched, opts.max_outer, opts.max_inner, opts.flags = sched, max_outer, max_inner, flags
+    rounds = np.zeros(max(rounds_cap, 1), dtype=np.uint32)
+    opts.rounds_out = rounds.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+    opts.rounds_cap = rounds_cap
+    tr = []
+    if keep_trace or hash_trace is not None:
+        def _cb(_user, outer, mptr, nn, k):
+            vec = np.ctypeslib.as_array(mptr, shape=(nn,))
+            tr.append((int(outer), hash_trace(vec) if hash_trace else vec.copy(), int(k)))
+        cb = TRACE_FN(_cb)
+        opts.trace = cb
+    res = MapResult()
+    out_ptr, keep = (None, None)
+    if map_out is not None:
+        if hasattr(map_out, "data_ptr"):
+            out_ptr = map_out.data_ptr()
+        else:
+            assert isinstance(map_out, np.ndarray) and map_out.dtype == np.uint32 and map_out.flags.c_contiguous
+            out_ptr = map_out.ctypes.data
+    rc = lib.map_run(handle, ctypes.byref(opts), ctypes.byref(res), out_ptr)
+    if rc != MAP_OK and not (allow_limit and rc == MAP_ERR_LIMIT):
+        raise MapError(rc, "map_run", last_error())
+    return RunResult(rc, res.verdict, res.witness, res.outer_iters,
+                     [int(x) for x in rounds[:min(res.outer_iters, rounds_cap)]], res.inner_iters,
+                     bool(res.inner_canonical), res.relaxations, res.edges_total, res.device_ms, res.dense_ms,
+                     res.dense_launches, res.accepting_left, res.launches, tr)
+
+
+def pack_bits(flags) -> np.ndarray:
+    """Accepting flags (one byte per vertex) -> LSB-first uint32 bitmap, the layout map_create takes."""
+    flags = np.ascontiguousarray(flags, dtype=np.uint8)
+    n = flags.shape[0]
+    padded = np.zeros(((n + 31) // 32) * 32, dtype=np.uint8)
+    padded[:n] = flags != 0
+    return np.packbits(padded, bitorder="little").view("<u4").astype(np.uint32)
+
+
+class Graph:
+    """Owning wrapper: ``with Graph(n, rowptr, colidx, acc_flags) as g: g.run()``."""
+
+    def __init__(self, n, rowptr, colidx, acc_flags=None, acc_bits=None, stream=None):
+        if acc_bits is None:
+            acc_bits = pack_bits(acc_flags)
+        self.n = int(n)
+        self.handle = map_create(self.n, rowptr, colidx, acc_bits, stream)
+
+    def run(self, **kw) -> RunResult:
+        return map_run(self.handle, **kw)
+
+    def close(self):
+        map_destroy(self.handle)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,203 @@
+"""GPU <-> oracle parity through the C ABI (bit-exact: MAP is integer work).
+
+Compared element by element: verdict, witness, outer count, round count of every outer
+iteration, relaxation count, the map vector of every outer iteration (full vectors for the
+small graphs, a blake2b digest per iteration for the large ones) and the final map vector.
+Under the asynchronous schedule everything but the round and relaxation counts must match,
+and the sweep count never exceeds the synchronous round count.
+"""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+import mapgen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CASES = json.load(open(os.path.join(HERE, "golden", "hand_cases.json")))["cases"]
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_0912_2555_gb300 as p
+
+    return p
+
+
+def digest(vec):
+    return hashlib.blake2b(np.ascontiguousarray(vec).tobytes(), digest_size=16).hexdigest()
+
+
+def gpu_run(pkg, g, sched=0, on_device=False, keep_trace=True, hash_trace=None, **kw):
+    if on_device:
+        rp = torch.from_numpy(g.rowptr.view(np.int32)).cuda()
+        ci = torch.from_numpy(g.colidx.view(np.int32) if g.m else np.zeros(1, np.int32)).cuda()
+        ab = torch.from_numpy(pkg.pack_bits(g.acc).view(np.int32)).cuda()
+        out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        stream = torch.cuda.current_stream()
+    else:
+        rp, ci, ab = g.rowptr, (g.colidx if g.m else None), pkg.pack_bits(g.acc)
+        out = np.empty(g.n, np.uint32)
+        stream = None
+    h = pkg.map_create(g.n, rp, ci, ab, stream)
+    try:
+        r = pkg.map_run(h, sched=sched, map_out=out, keep_trace=keep_trace and hash_trace is None,
+                        hash_trace=hash_trace, **kw)
+    finally:
+        pkg.map_destroy(h)
+    final = out.cpu().numpy().view(np.uint32) if on_device else out
+    return r, final
+
+
+def assert_parity(pkg, g, sched=0, on_device=False, hashed=False):
+    want = oracle.run_graph(g, keep_trace=not hashed, hash_trace=digest if hashed else None)
+    got, final = gpu_run(pkg, g, sched, on_device, keep_trace=not hashed, hash_trace=digest if hashed else None)
+    assert got.status == pkg.MAP_OK
+    assert (got.verdict, got.witness, got.outer) == (want.verdict, want.witness, want.outer)
+    assert np.array_equal(final, want.map)
+    assert len(got.trace) == len(want.trace) == want.outer
+    for (o1, m1, k1), (o2, m2, k2) in zip(got.trace, want.trace):
+        assert o1 == o2
+        if hashed:
+            assert m1 == m2, f"map differs at outer iteration {o1}"
+        else:
+            assert np.array_equal(m1, m2), f"map differs at outer iteration {o1}"
+    if sched == pkg.MAP_SCHED_SYNC:
+        assert got.rounds == want.rounds
+        assert got.relaxations == want.relaxations
+        assert got.inner_iters == want.inner_total and got.inner_canonical
+    else:
+        assert all(a <= b for a, b in zip(got.rounds, want.rounds))
+        assert not got.inner_canonical
+    assert got.edges_total == g.m * want.outer
+    return got, want
+
+
+@pytest.mark.parametrize("sched", [0, 1])
+@pytest.mark.parametrize("case", CASES, ids=[c["name"] for c in CASES])
+def test_hand_cases(pkg, case, sched):
+    g = mapgen.from_lists(case["rows"], case["acc"])
+    assert_parity(pkg, g, sched)
+
+
+@pytest.mark.parametrize("sched", [0, 1])
+def test_random_small(pkg, sched):
+    for seed in range(150):
+        rng = np.random.default_rng(7000 + seed)
+        n = int(rng.integers(1, 300))
+        g = mapgen.tiny_graph(seed, n, max_deg=int(rng.integers(0, 9)),
+                              acc_p=float(rng.choice([0.0, 0.02, 0.1, 0.3, 1.0])))
+        assert_parity(pkg, g, sched)
+
+
+@pytest.mark.parametrize("variant", ["cycle", "nocycle"])
+@pytest.mark.parametrize("on_device", [False, True])
+def test_random_16k(pkg, variant, on_device):
+    g = mapgen.random_16k(variant)
+    got, want = assert_parity(pkg, g, 0, on_device)
+    if variant == "cycle":
+        assert got.verdict == 1 and got.witness == g.meta["planted"] and got.outer == 1
+    assert_parity(pkg, g, 1, on_device)
+
+
+@pytest.mark.parametrize("G_deg", [(1, 1), (2, 3), (5, 9), (10, 20), (20, 40), (40, 80)])
+def test_degree_ranges_select_every_group_size(pkg, G_deg):
+    lo, hi = G_deg
+    g = mapgen.random_graph(3001, lo, hi, 0.05, seed=lo * 100 + hi, variant="plain")
+    assert_parity(pkg, g, 0)
+    assert_parity(pkg, g, 1)
+
+
+def test_ragged_and_degenerate(pkg):
+    # n not a multiple of 32, empty rows, a 60k-edge row, self-loops, duplicates
+    rng = np.random.default_rng(3)
+    n = 1000 + 17
+    rows = [[] if v % 7 == 0 else [int(x) for x in rng.integers(0, n, size=int(rng.integers(1, 5)))] for v in range(n)]
+    rows[5] = [int(x) for x in rng.integers(0, n, size=60000)]
+    rows[9] = [9, 9, 9]
+    acc = (rng.random(n) < 0.05).astype(np.uint8)
+    acc[9] = 0
+    for a in (acc, np.ones(n, np.uint8), np.zeros(n, np.uint8)):
+        g = mapgen.from_lists(rows, a)
+        assert_parity(pkg, g, 0)
+        assert_parity(pkg, g, 1)
+    # single vertex, no edges
+    assert_parity(pkg, mapgen.from_lists([[]], [1]), 0)
+    # graph without any edge at all
+    assert_parity(pkg, mapgen.from_lists([[] for _ in range(100)], np.ones(100, np.uint8)), 0)
+
+
+def test_layered_medium(pkg):
+    g = mapgen.layered_graph(1 << 20, 62, seed=3)
+    assert_parity(pkg, g, 0, on_device=True)
+    assert_parity(pkg, g, 1, on_device=True)
+    gp = mapgen.layered_graph(1 << 20, 62, seed=3, plant=True)
+    got, _ = assert_parity(pkg, gp, 0, on_device=True)
+    assert got.verdict == 1
+
+
+def test_product_8x7_full(pkg):
+    g = mapgen.product_8x7()
+    got, want = assert_parity(pkg, g, 0, on_device=True, hashed=True)
+    assert_parity(pkg, g, 1, on_device=True, hashed=True)
+
+
+def test_product_interleaved_small(pkg):
+    g = mapgen.product_graph(6, 6, interleave=True)
+    assert_parity(pkg, g, 0)
+    assert_parity(pkg, g, 1)
+
+
+def test_runs_repeat_exactly(pkg):
+    g = mapgen.layered_graph(200000, 12, seed=9)
+    h = pkg.map_create(g.n, g.rowptr, g.colidx, pkg.pack_bits(g.acc))
+    try:
+        outs = []
+        for _ in range(3):
+            out = np.empty(g.n, np.uint32)
+            r = pkg.map_run(h, map_out=out)
+            outs.append((r.verdict, r.witness, r.outer, tuple(r.rounds), r.relaxations, digest(out)))
+        assert outs[0] == outs[1] == outs[2]
+    finally:
+        pkg.map_destroy(h)
+
+
+def test_invalid_csr_and_limits(pkg):
+    with pytest.raises(pkg.MapError) as e:
+        pkg.map_create(2, np.array([0, 1, 2], np.uint32), np.array([1, 2], np.uint32), np.array([1], np.uint32))
+    assert e.value.code == pkg.MAP_ERR_CSR
+    with pytest.raises(pkg.MapError) as e:
+        pkg.map_create(2, np.array([0, 2, 1], np.uint32), np.array([1, 0], np.uint32), np.array([1], np.uint32))
+    assert e.value.code == pkg.MAP_ERR_CSR
+    with pytest.raises(pkg.MapError) as e:
+        pkg.map_create(2, np.array([1, 1, 2], np.uint32), np.array([1, 0], np.uint32), np.array([1], np.uint32))
+    assert e.value.code == pkg.MAP_ERR_CSR
+    g = mapgen.from_lists([[1], [2], []], [1, 1, 1])
+    h = pkg.map_create(g.n, g.rowptr, g.colidx, pkg.pack_bits(g.acc))
+    try:
+        r = pkg.map_run(h, max_outer=2, allow_limit=True)
+        assert r.status == pkg.MAP_ERR_LIMIT and r.outer == 2
+        r = pkg.map_run(h, max_inner=2, allow_limit=True)
+        assert r.status == pkg.MAP_ERR_LIMIT
+        r = pkg.map_run(h)
+        assert r.status == pkg.MAP_OK and r.outer == 3 and r.rounds == [3, 2, 1]
+    finally:
+        pkg.map_destroy(h)
+
+
+def test_layered_64m_full_size(pkg):
+    """The 2^26-vertex layered no-cycle graph, 4,000 layers: full parity, map digests per outer iteration."""
+    g = mapgen.layered_64m()
+    got, want = assert_parity(pkg, g, 0, on_device=True, hashed=True)
+    assert got.verdict == 0 and got.outer > 10
