@@ -86,7 +86,8 @@ typedef struct {
     void *user;           /* passed to trace */
     uint32_t *rounds_out; /* optional host array: round count of outer iteration i at [i] */
     uint32_t rounds_cap;  /* entries of rounds_out; later iterations are not stored */
-    uint32_t reserved[4]; /* must be zero */
+    uint32_t timeout_ms;  /* the loop stops with MAP_ERR_TIMEOUT after this long; 0 = 120000 */
+    uint32_t reserved[3]; /* must be zero */
 } map_opts;
 
 typedef struct {

@@ -46,7 +46,8 @@ class MapOpts(ctypes.Structure):
         ("user", ctypes.c_void_p),
         ("rounds_out", ctypes.POINTER(ctypes.c_uint32)),
         ("rounds_cap", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32 * 4),
+        ("timeout_ms", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 3),
     ]
 
 
@@ -159,7 +160,7 @@ class RunResult:
 
 def map_run(handle, sched: int = MAP_SCHED_SYNC, max_outer: int = 0, max_inner: int = 0, flags: int = 0,
             map_out=None, keep_trace: bool = False, hash_trace=None, rounds_cap: int = 1 << 16,
-            allow_limit: bool = False) -> RunResult:
+            allow_limit: bool = False, timeout_ms: int = 0) -> RunResult:
     """Run MAP on a created graph.  map_out: optional uint32 numpy array or CUDA tensor of n entries."""
     lib = load()
     opts = MapOpts()
@@ -167,6 +168,7 @@ def map_run(handle, sched: int = MAP_SCHED_SYNC, max_outer: int = 0, max_inner: 
     rounds = np.zeros(max(rounds_cap, 1), dtype=np.uint32)
     opts.rounds_out = rounds.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
     opts.rounds_cap = rounds_cap
+    opts.timeout_ms = timeout_ms
     tr = []
     if keep_trace or hash_trace is not None:
         def _cb(_user, outer, mptr, nn, k):

@@ -10,6 +10,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -74,16 +76,25 @@ struct map_graph {
     uint32_t words = 0;
     int G = 4;
     int sms = 0;
+    int dense_grid = 0;  // blocks of the dense-round kernel
+    int sparse_grid = 0; // blocks of the frontier-round kernels
+    int check_grid = 0;  // blocks of the self-map / elimination kernel
     cudaStream_t stream = nullptr;
     uint32_t *rowptr = nullptr, *colidx = nullptr, *rrowptr = nullptr, *rcol = nullptr;
     uint32_t *acc0 = nullptr, *acc = nullptr, *mval = nullptr, *fbits = nullptr, *queue = nullptr;
     uint32_t *chv = nullptr, *chval = nullptr;
+    uint32_t *hist = nullptr; // rounds per outer iteration
+    uint32_t hist_cap = 0;
     Ctl *ctl = nullptr;
     Ctl *h_ctl = nullptr;        // pinned mirror
     uint32_t *h_stage = nullptr; // pinned n words for traces / host output
+    uint32_t *h_hist = nullptr;  // pinned mirror of hist
     uint32_t nacc0 = 0;
-    uint64_t export_launches = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // the whole run as one CUDA graph, per schedule (built on first use)
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    mapk::Handles handles[2] = {};
 };
 
 namespace {
@@ -91,12 +102,17 @@ namespace {
 void free_graph(map_graph *g)
 {
     if (!g) return;
-    void *dev[] = {g->rowptr, g->colidx, g->rrowptr, g->rcol, g->acc0, g->acc, g->mval,
-                   g->fbits,  g->queue,  g->chv,     g->chval, g->ctl};
+    for (int i = 0; i < 2; ++i) {
+        if (g->exec[i]) cudaGraphExecDestroy(g->exec[i]);
+        if (g->graph[i]) cudaGraphDestroy(g->graph[i]);
+    }
+    void *dev[] = {g->rowptr, g->colidx, g->rrowptr, g->rcol, g->acc0, g->acc,  g->mval,
+                   g->fbits,  g->queue,  g->chv,     g->chval, g->hist, g->ctl};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (g->h_ctl) cudaFreeHost(g->h_ctl);
     if (g->h_stage) cudaFreeHost(g->h_stage);
+    if (g->h_hist) cudaFreeHost(g->h_hist);
     for (auto &e : g->ev)
         if (e) cudaEventDestroy(e);
     cudaGetLastError();
@@ -134,12 +150,6 @@ int scan_inclusive(uint32_t *x, uint64_t len, cudaStream_t s)
     return MAP_OK;
 }
 
-template <int G>
-void launch_transpose(map_graph *g, uint32_t *cursor)
-{
-    mapk::k_transpose<G><<<grid_for(g, g->n, G), 256, 0, g->stream>>>(g->n, g->rowptr, g->colidx, cursor, g->rcol);
-}
-
 #define DISPATCH_G(G, CALL)                                                                                        \
     switch (G) {                                                                                                   \
     case 1: { constexpr int GG = 1; CALL; } break;                                                                 \
@@ -157,17 +167,143 @@ int read_ctl(map_graph *g)
     return MAP_OK;
 }
 
-int export_map(map_graph *g, uint32_t *dst, bool dst_is_device)
+// --- the steps of a run, issued on stream s (shared by both drivers) -------
+
+int launch_dense(map_graph *g, cudaStream_t s, mapk::Handles hd)
 {
-    uint32_t *d = dst_is_device ? dst : g->chv; // chv is free between rounds
-    mapk::k_export<<<grid_for(g, g->n, 1), 256, 0, g->stream>>>(g->n, g->mval, d);
+    mapk::k_dense<<<g->dense_grid, mapk::DT_THREADS, 0, s>>>(g->n, g->rowptr, g->colidx, g->acc, g->mval,
+                                                              g->rrowptr, g->rcol, g->fbits, g->queue, g->ctl, hd);
     CK(cudaGetLastError());
-    g->export_launches++;
-    if (!dst_is_device) {
-        CK(cudaMemcpyAsync(g->h_stage, d, (size_t)g->n * 4, cudaMemcpyDeviceToHost, g->stream));
-        CK(cudaStreamSynchronize(g->stream));
-        if (dst != g->h_stage) memcpy(dst, g->h_stage, (size_t)g->n * 4);
+    return MAP_OK;
+}
+
+int launch_round(map_graph *g, cudaStream_t s, bool sync_sched, mapk::Handles hd)
+{
+    const int G = g->G;
+    if (sync_sched) {
+        DISPATCH_G(G, (mapk::k_sync_compute<GG><<<g->sparse_grid, 256, 0, s>>>(
+                          g->rowptr, g->colidx, g->acc, g->mval, g->queue, g->fbits, g->n, g->words, g->chv,
+                          g->chval, g->ctl, hd)));
+        DISPATCH_G(G, (mapk::k_sync_apply<GG><<<g->sparse_grid, 256, 0, s>>>(
+                          g->chv, g->chval, g->mval, g->rrowptr, g->rcol, g->queue, g->fbits, g->n, g->words,
+                          g->ctl, hd)));
+    } else {
+        DISPATCH_G(G, (mapk::k_async_sweep<GG><<<g->sparse_grid, 256, 0, s>>>(
+                          g->rowptr, g->colidx, g->acc, g->mval, g->rrowptr, g->rcol, g->queue, g->fbits, g->n,
+                          g->words, g->ctl, hd)));
     }
+    CK(cudaGetLastError());
+    return MAP_OK;
+}
+
+int launch_check(map_graph *g, cudaStream_t s, mapk::Handles hd)
+{
+    mapk::k_check_eliminate<<<g->check_grid, 256, 0, s>>>(g->n, g->mval, g->acc, g->ctl, hd);
+    CK(cudaGetLastError());
+    return MAP_OK;
+}
+
+int launch_reset(map_graph *g, cudaStream_t s)
+{
+    CK(cudaMemcpyAsync(g->acc, g->acc0, (size_t)g->words * 4, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(g->fbits, 0, (size_t)2 * g->words * 4, s));
+    return MAP_OK;
+}
+
+int launch_export(map_graph *g, cudaStream_t s, uint32_t *override_dst)
+{
+    mapk::k_export<<<g->check_grid, 256, 0, s>>>(g->n, g->mval, g->ctl, override_dst);
+    CK(cudaGetLastError());
+    return MAP_OK;
+}
+
+// --- the run as a CUDA graph: outer WHILE { dense; WHILE { round }; check } --
+
+int add_while(cudaStream_t cs, unsigned long long handle, cudaGraph_t *body)
+{
+    cudaStreamCaptureStatus st;
+    cudaGraph_t cap = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(cs, &st, nullptr, &cap, &deps, nullptr, &nd));
+    if (st != cudaStreamCaptureStatusActive) return fail(MAP_ERR_CUDA, "add_while: stream not capturing");
+    cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+    p.conditional.handle = handle;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, cap, deps, nullptr, nd, &p));
+    *body = p.conditional.phGraph_out[0];
+    CK(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return MAP_OK;
+}
+
+int build_run_graph(map_graph *g, int sched)
+{
+    if (g->exec[sched]) return MAP_OK;
+    const bool sync_sched = sched == MAP_SCHED_SYNC;
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    int rc = MAP_OK;
+    cudaGraph_t top = nullptr, outer_body = nullptr, inner_body = nullptr;
+    mapk::Handles hd{};
+    auto fin = [&](int code) {
+        cudaStreamDestroy(cs);
+        if (code != MAP_OK && top) cudaGraphDestroy(top);
+        cudaGetLastError();
+        return code;
+    };
+#define GK(call)                                                                                                   \
+    do {                                                                                                           \
+        cudaError_t e_ = (call);                                                                                   \
+        if (e_ != cudaSuccess) {                                                                                   \
+            cudaGetLastError();                                                                                    \
+            return fin(fail(MAP_ERR_CUDA, "graph build: %s: %s", #call, cudaGetErrorString(e_)));                \
+        }                                                                                                          \
+    } while (0)
+    GK(cudaGraphCreate(&top, 0));
+    GK(cudaGraphConditionalHandleCreate(&hd.outer, top, 0, cudaGraphCondAssignDefault));
+    // top level: reset, run_begin, outer WHILE, export
+    GK(cudaStreamBeginCaptureToGraph(cs, top, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    if ((rc = launch_reset(g, cs)) == MAP_OK) {
+        mapk::k_run_begin<<<1, 32, 0, cs>>>(g->ctl, hd);
+        rc = add_while(cs, hd.outer, &outer_body);
+        if (rc == MAP_OK) rc = launch_export(g, cs, nullptr);
+    }
+    {
+        cudaGraph_t got = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cs, &got);
+        if (rc) return fin(rc);
+        GK(e);
+    }
+    // outer body: dense round, fix-point WHILE, self-map test + elimination
+    GK(cudaGraphConditionalHandleCreate(&hd.inner, outer_body, 0, cudaGraphCondAssignDefault));
+    GK(cudaStreamBeginCaptureToGraph(cs, outer_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    rc = launch_dense(g, cs, hd);
+    if (rc == MAP_OK) rc = add_while(cs, hd.inner, &inner_body);
+    if (rc == MAP_OK) rc = launch_check(g, cs, hd);
+    {
+        cudaGraph_t got = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cs, &got);
+        if (rc) return fin(rc);
+        GK(e);
+    }
+    // inner body: one round (compute + apply, or one sweep)
+    GK(cudaStreamBeginCaptureToGraph(cs, inner_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    rc = launch_round(g, cs, sync_sched, hd);
+    {
+        cudaGraph_t got = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cs, &got);
+        if (rc) return fin(rc);
+        GK(e);
+    }
+    cudaGraphExec_t exec = nullptr;
+    GK(cudaGraphInstantiate(&exec, top, 0));
+#undef GK
+    g->graph[sched] = top;
+    g->exec[sched] = exec;
+    g->handles[sched] = hd;
+    cudaStreamDestroy(cs);
     return MAP_OK;
 }
 
@@ -221,6 +357,14 @@ int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev);
     if (g->sms <= 0) g->sms = 1;
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mapk::k_dense, mapk::DT_THREADS, 0);
+    if (occ <= 0) occ = 1;
+    const uint64_t ntiles = ((uint64_t)n + mapk::DT_ROWS - 1) / mapk::DT_ROWS;
+    g->dense_grid = (int)std::min<uint64_t>(ntiles, (uint64_t)g->sms * occ);
+    g->sparse_grid = (int)std::min<uint64_t>(((uint64_t)n * g->G + 255) / 256 + 1, (uint64_t)g->sms * 4);
+    g->check_grid = (int)std::min<uint64_t>(((uint64_t)n / 4 + 255) / 256 + 1, (uint64_t)g->sms * 4);
+    g->hist_cap = 1u << 16;
 
     auto alloc = [&](uint32_t **p, uint64_t words) -> int {
         CK(cudaMalloc((void **)p, (words + 4) * sizeof(uint32_t))); // 16 bytes of slack at the end
@@ -231,7 +375,8 @@ int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const
     if ((rc = alloc(&g->rowptr, (uint64_t)n + 1)) || (rc = alloc(&g->colidx, m)) ||
         (rc = alloc(&g->rrowptr, (uint64_t)n + 1)) || (rc = alloc(&g->rcol, m)) || (rc = alloc(&g->acc0, W)) ||
         (rc = alloc(&g->acc, W)) || (rc = alloc(&g->mval, n)) || (rc = alloc(&g->fbits, 2 * W)) ||
-        (rc = alloc(&g->queue, 2 * (uint64_t)n)) || (rc = alloc(&g->chv, n)) || (rc = alloc(&g->chval, n))) {
+        (rc = alloc(&g->queue, 2 * (uint64_t)n)) || (rc = alloc(&g->chv, n)) || (rc = alloc(&g->chval, n)) ||
+        (rc = alloc(&g->hist, g->hist_cap))) {
         free_graph(g);
         return rc;
     }
@@ -243,7 +388,8 @@ int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const
     };
     if ((rc = ck(cudaMalloc((void **)&g->ctl, sizeof(Ctl)), "ctl")) ||
         (rc = ck(cudaMallocHost((void **)&g->h_ctl, sizeof(Ctl)), "h_ctl")) ||
-        (rc = ck(cudaMallocHost((void **)&g->h_stage, (size_t)n * 4), "h_stage"))) {
+        (rc = ck(cudaMallocHost((void **)&g->h_stage, (size_t)n * 4), "h_stage")) ||
+        (rc = ck(cudaMallocHost((void **)&g->h_hist, (size_t)g->hist_cap * 4), "h_hist"))) {
         free_graph(g);
         return rc;
     }
@@ -272,17 +418,18 @@ int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const
     }
     if ((rc = ck(cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), s), "memset ctl")) ||
         (rc = ck(cudaMemsetAsync(g->colidx + m, 0, 16, s), "pad")) ||
+        (rc = ck(cudaMemsetAsync(g->mval, 0, ((size_t)n + 4) * 4, s), "memset mval")) ||
         (rc = ck(cudaMemsetAsync(g->fbits, 0, 2 * W * 4, s), "memset fbits"))) {
         free_graph(g);
         return rc;
     }
-    mapk::k_validate<<<grid_for(g, m > n ? m : n, 1), 256, 0, s>>>(n, g->rowptr, m, g->colidx, g->ctl);
+    mapk::k_validate<<<grid_for(g, m > n ? m : n, 1), 256, 0, s>>>(n, g->rowptr, m, g->colidx, &g->ctl->ccnt);
     mapk::k_acc_init<<<grid_for(g, W, 1), 256, 0, s>>>(n, acc_in, g->acc0, &g->ctl->elim);
     if ((rc = ck(cudaGetLastError(), "validate")) || (rc = read_ctl(g))) {
         free_graph(g);
         return rc;
     }
-    if (g->h_ctl->bad) {
+    if (g->h_ctl->ccnt) {
         free_graph(g);
         return fail(MAP_ERR_CSR, "map_create: invalid CSR (decreasing rowptr or colidx >= n)");
     }
@@ -303,7 +450,8 @@ int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const
         free_graph(g);
         return rc;
     }
-    DISPATCH_G(g->G, launch_transpose<GG>(g, g->queue));
+    DISPATCH_G(g->G, (mapk::k_transpose<GG><<<grid_for(g, n, GG), 256, 0, s>>>(n, g->rowptr, g->colidx, g->queue,
+                                                                              g->rcol)));
     if ((rc = ck(cudaGetLastError(), "transpose")) || (rc = ck(cudaStreamSynchronize(s), "create sync"))) {
         free_graph(g);
         return rc;
@@ -327,132 +475,111 @@ int map_run(map_graph *g, const map_opts *opts_in, map_result *res, uint32_t *ma
     if (opts_in) opts = *opts_in;
     if (opts.sched > MAP_SCHED_ASYNC) return fail(MAP_ERR_ARG, "map_run: unknown schedule %u", opts.sched);
     const bool sync_sched = opts.sched == MAP_SCHED_SYNC;
-    const uint64_t max_inner = opts.max_inner ? opts.max_inner : (uint64_t)g->n + 1;
     const bool profile = (opts.flags & MAP_FLAG_PROFILE) != 0;
+    // the CUDA-graph driver runs the whole loop on the device; per-iteration
+    // traces and per-kernel timing need the host-stepped driver (same kernels)
+    const bool stepped = opts.trace != nullptr || profile;
     memset(res, 0, sizeof *res);
-    res->verdict = MAP_NO_CYCLE;
-    res->witness = MAP_NONE;
-    res->inner_canonical = sync_sched ? 1 : 0;
     cudaStream_t s = g->stream;
     const uint32_t n = g->n;
-    const uint32_t W = g->words;
-    const int G = g->G;
+    const bool out_dev = map_out && is_device_ptr(map_out);
 
-    g->export_launches = 0;
-    CK(cudaEventRecord(g->ev[0], s));
-    CK(cudaMemcpyAsync(g->acc, g->acc0, (size_t)W * 4, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemsetAsync(g->fbits, 0, (size_t)2 * W * 4, s));
-    uint64_t nacc = g->nacc0;
-    uint32_t outer = 0;
-    int status = MAP_OK;
+    // run parameters into the control block (the kernels reset the rest)
+    Ctl init;
+    memset(&init, 0, sizeof init);
+    init.max_outer = opts.max_outer;
+    init.max_inner = opts.max_inner ? opts.max_inner : (n + 1 > n ? n + 1 : n);
+    init.hist_cap = g->hist_cap;
+    init.m = g->m;
+    init.nacc0 = g->nacc0;
+    init.rounds_hist = g->hist;
+    init.out = out_dev ? map_out : g->chv;
+    init.use_graph = stepped ? 0 : 1;
+    init.timeout_ns = (uint64_t)(opts.timeout_ms ? opts.timeout_ms : 120000u) * 1000000ull;
+    init.witness = mapk::NONE;
+
+    int rc = MAP_OK;
     float dense_ms = 0.f;
-    bool ran = false;
-
-    while (nacc > 0) {
-        if (opts.max_outer && outer >= opts.max_outer) {
-            status = fail(MAP_ERR_LIMIT, "map_run: max_outer = %u reached", opts.max_outer);
-            break;
-        }
-        outer++;
-        ran = true;
-        Ctl init;
-        memset(&init, 0, sizeof init);
-        init.witness = MAP_NONE;
+    if (!stepped) {
+        if ((rc = build_run_graph(g, opts.sched))) return rc;
         *g->h_ctl = init;
+        CK(cudaEventRecord(g->ev[0], s));
         CK(cudaMemcpyAsync(g->ctl, g->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
-
-        // round 1: every row
-        if (profile) CK(cudaEventRecord(g->ev[2], s));
-        DISPATCH_G(G, (mapk::k_dense<GG><<<grid_for(g, n, GG), 256, 0, s>>>(
-                          n, g->rowptr, g->colidx, g->acc, g->mval, g->rrowptr, g->rcol, g->fbits, g->queue, g->ctl,
-                          &g->ctl->qcnt[0])));
-        CK(cudaGetLastError());
-        res->launches++;
-        if (profile) CK(cudaEventRecord(g->ev[3], s));
-        res->relaxations += g->m;
-        uint64_t k = 1;
-        int rc = read_ctl(g);
-        if (rc) return rc;
-        if (profile) {
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, g->ev[2], g->ev[3]));
-            dense_ms += ms;
-            res->dense_launches++;
-        }
-        uint32_t changed = g->h_ctl->ccnt;
-        while (changed) {
-            k++;
-            if (k > max_inner) {
-                status = fail(MAP_ERR_LIMIT, "map_run: max_inner = %llu reached", (unsigned long long)max_inner);
-                break;
-            }
-            const int p = (int)(k & 1), np = p ^ 1;
-            const uint32_t nfront = g->h_ctl->qcnt[p];
-            uint32_t *front = g->queue + (size_t)p * n, *next = g->queue + (size_t)np * n;
-            uint32_t *fb = g->fbits + (size_t)p * W, *nb = g->fbits + (size_t)np * W;
-            CK(cudaMemsetAsync(&g->ctl->ccnt, 0, 4, s));
-            CK(cudaMemsetAsync(&g->ctl->qcnt[np], 0, 4, s));
-            if (nfront) {
-                if (sync_sched) {
-                    DISPATCH_G(G, (mapk::k_sync_compute<GG><<<grid_for(g, nfront, GG), 256, 0, s>>>(
-                                      front, nfront, g->rowptr, g->colidx, g->acc, g->mval, fb, g->chv, g->chval,
-                                      g->ctl)));
-                    DISPATCH_G(G, (mapk::k_sync_apply<GG><<<grid_for(g, nfront, GG), 256, 0, s>>>(
-                                      g->chv, g->chval, g->ctl, g->mval, g->rrowptr, g->rcol, nb, next,
-                                      &g->ctl->qcnt[np])));
-                } else {
-                    DISPATCH_G(G, (mapk::k_async_sweep<GG><<<grid_for(g, nfront, GG), 256, 0, s>>>(
-                                      front, nfront, g->rowptr, g->colidx, g->acc, g->mval, fb, g->rrowptr,
-                                      g->rcol, nb, next, &g->ctl->qcnt[np], g->ctl)));
-                }
-                CK(cudaGetLastError());
-                res->launches += sync_sched ? 2 : 1;
-            }
-            if ((rc = read_ctl(g))) return rc;
-            changed = g->h_ctl->ccnt;
-        }
-        if (opts.rounds_out && outer - 1 < opts.rounds_cap) opts.rounds_out[outer - 1] = (uint32_t)k;
-        res->inner_iters += k;
-        if (status != MAP_OK) break;
-        if (opts.trace) {
-            if ((rc = export_map(g, g->h_stage, false))) return rc;
-            opts.trace(opts.user, outer, g->h_stage, n, (uint32_t)k);
-        }
-
-        mapk::k_check_eliminate<<<grid_for(g, n, 1), 256, 0, s>>>(n, g->mval, g->acc, g->ctl);
-        CK(cudaGetLastError());
-        res->launches++;
+        CK(cudaGraphLaunch(g->exec[opts.sched], s));
+        CK(cudaEventRecord(g->ev[1], s));
         if ((rc = read_ctl(g))) return rc;
-        res->relaxations += g->h_ctl->relax;
-        if (g->h_ctl->witness != MAP_NONE) {
-            res->verdict = MAP_CYCLE;
-            res->witness = g->h_ctl->witness;
-            break;
+        res->launches = 0; // filled below from the counts
+    } else {
+        const mapk::Handles none{};
+        *g->h_ctl = init;
+        CK(cudaEventRecord(g->ev[0], s));
+        CK(cudaMemcpyAsync(g->ctl, g->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+        if ((rc = launch_reset(g, s))) return rc;
+        mapk::k_run_begin<<<1, 32, 0, s>>>(g->ctl, none);
+        CK(cudaGetLastError());
+        if ((rc = read_ctl(g))) return rc;
+        while (g->h_ctl->outer_go) {
+            if (profile) CK(cudaEventRecord(g->ev[2], s));
+            if ((rc = launch_dense(g, s, none))) return rc;
+            if (profile) CK(cudaEventRecord(g->ev[3], s));
+            if ((rc = read_ctl(g))) return rc;
+            if (profile) {
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, g->ev[2], g->ev[3]));
+                dense_ms += ms;
+                res->dense_launches++;
+            }
+            while (g->h_ctl->inner_go) {
+                if ((rc = launch_round(g, s, sync_sched, none))) return rc;
+                if ((rc = read_ctl(g))) return rc;
+            }
+            if (opts.trace) {
+                const uint32_t outer = g->h_ctl->outer, k = g->h_ctl->k;
+                if ((rc = launch_export(g, s, g->chval))) return rc; // chval is free between rounds
+                CK(cudaMemcpyAsync(g->h_stage, g->chval, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                opts.trace(opts.user, outer, g->h_stage, n, k);
+            }
+            if ((rc = launch_check(g, s, none))) return rc;
+            if ((rc = read_ctl(g))) return rc;
         }
-        if (!g->h_ctl->nonzero) break; // nothing reaches a remaining accepting vertex
-        nacc -= g->h_ctl->elim;
+        if ((rc = launch_export(g, s, nullptr))) return rc;
+        CK(cudaEventRecord(g->ev[1], s));
+        if ((rc = read_ctl(g))) return rc;
     }
-    CK(cudaEventRecord(g->ev[1], s));
     CK(cudaEventSynchronize(g->ev[1]));
     float total_ms = 0.f;
     CK(cudaEventElapsedTime(&total_ms, g->ev[0], g->ev[1]));
+    const Ctl &c = *g->h_ctl;
+    res->verdict = c.verdict ? MAP_CYCLE : MAP_NO_CYCLE;
+    res->witness = c.verdict ? c.witness : MAP_NONE;
+    res->outer_iters = c.outer;
+    res->inner_canonical = sync_sched ? 1 : 0;
+    res->inner_iters = c.inner_total;
+    res->relaxations = c.relax;
+    res->edges_total = g->m * (uint64_t)c.outer;
     res->device_ms = total_ms;
     res->dense_ms = dense_ms;
-    res->outer_iters = outer;
-    res->edges_total = g->m * (uint64_t)outer;
-    res->accepting_left = (uint32_t)nacc;
-
-    if (map_out) {
-        const bool dev = is_device_ptr(map_out);
-        if (!ran) {
-            CK(cudaMemsetAsync(g->mval, 0, (size_t)n * 4, s)); // no iteration: no value anywhere
-        }
-        int rc = export_map(g, map_out, dev);
-        if (rc) return rc;
-        if (dev) CK(cudaStreamSynchronize(s));
+    res->accepting_left = c.nacc;
+    // launches: reset (memcpy + memset are not kernels), run_begin, export, and per outer
+    // iteration dense + check, per round 2 (SYNC) or 1 (ASYNC)
+    const uint64_t rounds_after_first = c.inner_total >= c.outer ? c.inner_total - c.outer : 0;
+    res->launches = 2 + 2ull * c.outer + (sync_sched ? 2 : 1) * rounds_after_first;
+    const uint32_t nh = std::min<uint32_t>(c.outer, g->hist_cap);
+    if (opts.rounds_out && nh) {
+        CK(cudaMemcpyAsync(g->h_hist, g->hist, (size_t)nh * 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        memcpy(opts.rounds_out, g->h_hist, (size_t)std::min(nh, opts.rounds_cap) * 4);
     }
-    res->launches += g->export_launches;
-    return status;
+    if (map_out && !out_dev) {
+        CK(cudaMemcpyAsync(g->h_stage, g->chv, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        memcpy(map_out, g->h_stage, (size_t)n * 4);
+    }
+    if (c.status == mapk::ST_LIMIT) return fail(MAP_ERR_LIMIT, "map_run: max_outer or max_inner reached");
+    if (c.status == mapk::ST_TIMEOUT)
+        return fail(MAP_ERR_TIMEOUT, "map_run: stopped after timeout_ms = %u", opts.timeout_ms ? opts.timeout_ms : 120000u);
+    return MAP_OK;
 }
 
 } // extern "C"

@@ -40,6 +40,8 @@ def digest(vec):
 
 
 def gpu_run(pkg, g, sched=0, on_device=False, keep_trace=True, hash_trace=None, **kw):
+    """One map_run through the C ABI.  With a trace the library steps the loop from the host
+    (same kernels); without one the whole run is a single CUDA-graph launch."""
     if on_device:
         rp = torch.from_numpy(g.rowptr.view(np.int32)).cuda()
         ci = torch.from_numpy(g.colidx.view(np.int32) if g.m else np.zeros(1, np.int32)).cuda()
@@ -60,8 +62,28 @@ def gpu_run(pkg, g, sched=0, on_device=False, keep_trace=True, hash_trace=None, 
     return r, final
 
 
-def assert_parity(pkg, g, sched=0, on_device=False, hashed=False):
+def assert_graph_path(pkg, g, want, sched, on_device, per_outer):
+    """The CUDA-graph driver (no trace): same verdict, counts and final map; with per_outer,
+    the map of every outer iteration k from a run stopped by max_outer = k."""
+    got, final = gpu_run(pkg, g, sched, on_device, keep_trace=False)
+    assert got.status == pkg.MAP_OK
+    assert (got.verdict, got.witness, got.outer) == (want.verdict, want.witness, want.outer)
+    assert np.array_equal(final, want.map)
+    if sched == pkg.MAP_SCHED_SYNC:
+        assert (got.rounds, got.relaxations, got.inner_iters) == (want.rounds, want.relaxations, want.inner_total)
+    if per_outer:
+        for k in range(1, want.outer):
+            r, fk = gpu_run(pkg, g, sched, on_device, keep_trace=False, max_outer=k, allow_limit=True)
+            assert r.status == pkg.MAP_ERR_LIMIT and r.outer == k
+            tr = want.trace[k - 1][1]
+            assert (fk == tr).all() if not isinstance(tr, str) else digest(fk) == tr
+
+
+def assert_parity(pkg, g, sched=0, on_device=False, hashed=False, per_outer=None):
     want = oracle.run_graph(g, keep_trace=not hashed, hash_trace=digest if hashed else None)
+    if per_outer is None:
+        per_outer = g.n <= 5000 and want.outer <= 20
+    assert_graph_path(pkg, g, want, sched, on_device, per_outer)
     got, final = gpu_run(pkg, g, sched, on_device, keep_trace=not hashed, hash_trace=digest if hashed else None)
     assert got.status == pkg.MAP_OK
     assert (got.verdict, got.witness, got.outer) == (want.verdict, want.witness, want.outer)
