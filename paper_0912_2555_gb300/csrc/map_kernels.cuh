@@ -548,11 +548,11 @@ __global__ void __launch_bounds__(256) k_check_eliminate(uint32_t n, const uint3
     if (last_block(ctl)) epilogue_check(ctl, hd);
 }
 
-// External encoding into ctl->out (or `fallback`): MAP_NONE for no value, else
+// External encoding into `dst` (NULL: ctl->out): MAP_NONE for no value, else
 // the vertex id; all MAP_NONE when no outer iteration ran.
-__global__ void k_export(uint32_t n, const uint32_t *__restrict__ mval, const Ctl *ctl, uint32_t *fallback)
+__global__ void k_export(uint32_t n, const uint32_t *__restrict__ mval, const Ctl *ctl, uint32_t *dst)
 {
-    uint32_t *out = ctl->out ? ctl->out : fallback;
+    uint32_t *out = dst ? dst : ctl->out;
     const bool none = ctl->outer == 0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
