@@ -171,7 +171,7 @@ int read_ctl(map_graph *g)
 
 int launch_dense(map_graph *g, cudaStream_t s, mapk::Handles hd)
 {
-    mapk::k_dense<<<g->dense_grid, mapk::DT_THREADS, 0, s>>>(g->n, g->rowptr, g->colidx, g->acc, g->mval,
+    mapk::k_dense<<<g->dense_grid, mapk::DT_THREADS, mapk::DT_SMEM, s>>>(g->n, g->rowptr, g->colidx, g->acc, g->mval,
                                                               g->rrowptr, g->rcol, g->fbits, g->queue, g->ctl, hd);
     CK(cudaGetLastError());
     return MAP_OK;
@@ -358,11 +358,12 @@ int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const
     cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev);
     if (g->sms <= 0) g->sms = 1;
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mapk::k_dense, mapk::DT_THREADS, 0);
+    cudaFuncSetAttribute(mapk::k_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mapk::DT_SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mapk::k_dense, mapk::DT_THREADS, mapk::DT_SMEM);
     if (occ <= 0) occ = 1;
     const uint64_t ntiles = ((uint64_t)n + mapk::DT_ROWS - 1) / mapk::DT_ROWS;
     g->dense_grid = (int)std::min<uint64_t>(ntiles, (uint64_t)g->sms * occ);
-    g->sparse_grid = (int)std::min<uint64_t>(((uint64_t)n * g->G + 255) / 256 + 1, (uint64_t)g->sms * 4);
+    g->sparse_grid = (int)std::min<uint64_t>(((uint64_t)n * g->G + 255) / 256 + 1, (uint64_t)g->sms * 6);
     g->check_grid = (int)std::min<uint64_t>(((uint64_t)n / 4 + 255) / 256 + 1, (uint64_t)g->sms * 4);
     g->hist_cap = 1u << 16;
 

@@ -153,6 +153,7 @@ __device__ void epilogue_dense(Ctl *c, Handles hd)
         v->status = ST_LIMIT;
         go = 0;
     }
+    if (v->status != ST_OK) go = 0;
     v->inner_go = go;
     __threadfence();
     set_cond(c, hd.inner, go);
@@ -273,84 +274,243 @@ __device__ __forceinline__ void mark_readers(uint32_t u, unsigned glane, const u
 //
 // Round 1 of an outer iteration relaxes every row from "no value" everywhere,
 // so the value u offers is u + 1 if u is accepting and 0 otherwise: only the
-// accepting bitmap is gathered.  One block owns a tile of DT_ROWS consecutive
-// rows at a time: their rowptr slice goes to shared memory, the edge span of
-// the tile is streamed with 128-bit loads (DT_UNROLL independent loads per
-// thread, then 4 * DT_UNROLL independent bitmap gathers), and an edge that
-// offers a value finds its row by binary search in the rowptr slice and does a
-// shared-memory atomicMax.  The tile's values are written out coalesced (this
-// also resets the previous iteration's values), and the readers of every row
-// that got a value are marked into the round-2 frontier.
+// accepting bitmap is gathered.
+//
+// A block walks its tiles of DT_ROWS consecutive rows.  For each tile, thread 0
+// stages the rowptr slice and the tile's whole colidx span into shared memory
+// with bulk asynchronous copies (cp.async.bulk, completion on an mbarrier):
+// rowptr slices run two tiles ahead (3-slot ring), colidx spans one tile ahead
+// (2-slot ring), so the copies of the next tiles are in flight while the block
+// gathers accepting bits for the current one.  A tile whose span exceeds
+// DT_CAP words reads its edges straight from global memory instead.  An edge
+// that offers a value finds its row by binary search in the rowptr slice and
+// does a shared-memory atomicMax; the tile's values are then written out
+// coalesced (this also resets the previous iteration's values), and the
+// readers of every row that got a value are marked into the round-2 frontier.
+//
+// Every mbarrier wait is bounded; a wait that gives up sets ctl->status to
+// ST_TIMEOUT, waits (bounded) for the copies this block has in flight, and the
+// block leaves its tile loop.
 constexpr int DT_THREADS = 256;
-constexpr int DT_ROWS = 2048;
-constexpr int DT_UNROLL = 4;
-constexpr int DT_CHUNK = DT_THREADS * 4 * DT_UNROLL; // edges per pass
+constexpr int DT_ROWS = 1024;
+constexpr int DT_RPW = DT_ROWS + 4; // rowptr slice words (16-byte multiple)
+constexpr int DT_CAP = 8192;        // colidx words a tile may stage
+constexpr int DT_UNROLL = 4;        // 128-bit words per thread per pass
 
-__global__ void __launch_bounds__(DT_THREADS) k_dense(uint32_t n, const uint32_t *__restrict__ rowptr,
+struct DenseSmem {
+    uint32_t rp[3][DT_RPW];
+    uint32_t col[2][DT_CAP];
+    uint32_t best[DT_ROWS];
+    unsigned long long bar_rp[3];
+    unsigned long long bar_col[2];
+    uint32_t e0[2], e1[2], staged[2]; // per colidx slot: the tile's edge span and how it is read
+    uint32_t failed;
+};
+constexpr size_t DT_SMEM = sizeof(DenseSmem);
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// arrive (the single expected arrival) and announce `bytes` of asynchronous transfer
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// bounded wait for the phase with the given parity to complete
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity)
+{
+    for (uint32_t it = 0; it < (1u << 22); ++it) {
+        uint32_t ok;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(ok)
+                     : "r"(smem_u32(bar)), "r"(parity)
+                     : "memory");
+        if (ok) return true;
+        if (it > 64) __nanosleep(64);
+    }
+    return false;
+}
+
+// global -> shared bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// thread 0: stage the rowptr slice of tile t into slot `slot`
+__device__ __forceinline__ void issue_rp(DenseSmem &S, int slot, uint32_t t, uint32_t n,
+                                         const uint32_t *__restrict__ rowptr)
+{
+    const uint32_t r0 = t * DT_ROWS;
+    const uint32_t rows = min((uint32_t)DT_ROWS, n - r0);
+    const uint32_t words = (rows + 1 + 3) & ~3u; // the allocation has 4 words of slack past rowptr[n]
+    fence_proxy_async();
+    mbar_arrive_tx(&S.bar_rp[slot], words * 4);
+    bulk_g2s(S.rp[slot], rowptr + r0, words * 4, &S.bar_rp[slot]);
+}
+
+// thread 0, once the rowptr slice of tile t is in slot rslot: stage its colidx
+// span into colidx slot cslot (or mark it to be read from global memory)
+__device__ __forceinline__ void issue_col(DenseSmem &S, int cslot, int rslot, uint32_t t, uint32_t n,
+                                          const uint32_t *__restrict__ colidx)
+{
+    const uint32_t r0 = t * DT_ROWS;
+    const uint32_t rows = min((uint32_t)DT_ROWS, n - r0);
+    const uint32_t E0 = S.rp[rslot][0], E1 = S.rp[rslot][rows];
+    const uint32_t a0 = E0 & ~3u, a1 = (E1 + 3) & ~3u; // slack of 4 words past colidx[m]
+    S.e0[cslot] = E0;
+    S.e1[cslot] = E1;
+    if (E1 > E0 && a1 - a0 <= (uint32_t)DT_CAP) {
+        S.staged[cslot] = 1;
+        fence_proxy_async();
+        mbar_arrive_tx(&S.bar_col[cslot], (a1 - a0) * 4);
+        bulk_g2s(S.col[cslot], colidx + a0, (a1 - a0) * 4, &S.bar_col[cslot]);
+    } else {
+        S.staged[cslot] = 0;
+        mbar_arrive(&S.bar_col[cslot]); // complete the phase without a copy
+    }
+}
+
+// the edges [E0, E1) of a tile: gather accepting bits, find rows, atomicMax into best
+template <bool STAGED>
+__device__ __forceinline__ void dense_edges(DenseSmem &S, const uint32_t *__restrict__ src, uint32_t E0, uint32_t E1,
+                                            const uint32_t *__restrict__ rp, uint32_t rows,
+                                            const uint32_t *__restrict__ acc)
+{
+    const uint32_t a0 = E0 & ~3u;
+    const uint32_t nq = ((E1 + 3) & ~3u) - a0 >> 2; // 128-bit words in the span
+    for (uint32_t q0 = 0; q0 < nq; q0 += DT_THREADS * DT_UNROLL) {
+        uint4 w[DT_UNROLL];
+#pragma unroll
+        for (int j = 0; j < DT_UNROLL; ++j) {
+            const uint32_t q = q0 + j * DT_THREADS + threadIdx.x;
+            if (q < nq) {
+                if (STAGED) w[j] = reinterpret_cast<const uint4 *>(src)[q];
+                else w[j] = __ldg(reinterpret_cast<const uint4 *>(src + a0) + q);
+            } else {
+                w[j] = make_uint4(0, 0, 0, 0);
+            }
+        }
+        uint32_t aw[DT_UNROLL][4];
+#pragma unroll
+        for (int j = 0; j < DT_UNROLL; ++j) {
+            aw[j][0] = __ldg(acc + (w[j].x >> 5));
+            aw[j][1] = __ldg(acc + (w[j].y >> 5));
+            aw[j][2] = __ldg(acc + (w[j].z >> 5));
+            aw[j][3] = __ldg(acc + (w[j].w >> 5));
+        }
+#pragma unroll
+        for (int j = 0; j < DT_UNROLL; ++j) {
+            const uint32_t ebase = a0 + (q0 + j * DT_THREADS + threadIdx.x) * 4;
+            const uint32_t us[4] = {w[j].x, w[j].y, w[j].z, w[j].w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t e = ebase + k;
+                const uint32_t u = us[k];
+                if (e >= E0 && e < E1 && ((aw[j][k] >> (u & 31u)) & 1u)) {
+                    uint32_t lo = 0, hi = rows; // rp[lo] <= e < rp[hi]: the row of e is the last such lo
+                    while (hi - lo > 1) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (rp[mid] <= e) lo = mid;
+                        else hi = mid;
+                    }
+                    atomicMax(&S.best[lo], u + 1);
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(DT_THREADS, 2) k_dense(uint32_t n, const uint32_t *__restrict__ rowptr,
                                                       const uint32_t *__restrict__ colidx,
                                                       const uint32_t *__restrict__ acc, uint32_t *__restrict__ mval,
                                                       const uint32_t *__restrict__ rrowptr,
                                                       const uint32_t *__restrict__ rcol, uint32_t *bits,
                                                       uint32_t *queue, Ctl *ctl, Handles hd)
 {
-    __shared__ uint32_t srp[DT_ROWS + 1];
-    __shared__ uint32_t sbest[DT_ROWS];
+    extern __shared__ __align__(128) unsigned char dense_smem[];
+    DenseSmem &S = *reinterpret_cast<DenseSmem *>(dense_smem);
     default_stop(ctl, hd.outer);
     const uint32_t ntiles = (n + DT_ROWS - 1) / DT_ROWS;
+    const uint32_t my = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     unsigned changed = 0;
-    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const uint32_t r0 = tile * DT_ROWS;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 3; ++i) mbar_init(&S.bar_rp[i]);
+        for (int i = 0; i < 2; ++i) mbar_init(&S.bar_col[i]);
+        S.failed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    for (uint32_t i = threadIdx.x; i < DT_ROWS; i += DT_THREADS) S.best[i] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0 && my > 0) {
+        issue_rp(S, 0, blockIdx.x, n, rowptr);
+        if (my > 1) issue_rp(S, 1, blockIdx.x + gridDim.x, n, rowptr);
+        if (mbar_wait(&S.bar_rp[0], 0)) issue_col(S, 0, 0, blockIdx.x, n, colidx);
+        else S.failed = 1;
+    }
+    __syncthreads();
+    for (uint32_t i = 0; i < my && !S.failed; ++i) {
+        const uint32_t t = blockIdx.x + i * gridDim.x;
+        const int rs = i % 3, cs = i & 1;
+        const uint32_t r0 = t * DT_ROWS;
         const uint32_t rows = min((uint32_t)DT_ROWS, n - r0);
-        for (uint32_t i = threadIdx.x; i <= rows; i += DT_THREADS) srp[i] = __ldg(rowptr + r0 + i);
-        for (uint32_t i = threadIdx.x; i < rows; i += DT_THREADS) sbest[i] = 0;
-        __syncthreads();
-        const uint32_t E0 = srp[0], E1 = srp[rows];
-        for (uint32_t cs = E0 & ~3u; cs < E1; cs += DT_CHUNK) {
-            uint4 w[DT_UNROLL];
-#pragma unroll
-            for (int j = 0; j < DT_UNROLL; ++j) {
-                const uint32_t idx = cs + (j * DT_THREADS + threadIdx.x) * 4;
-                w[j] = idx < E1 ? __ldg(reinterpret_cast<const uint4 *>(colidx + idx)) : make_uint4(0, 0, 0, 0);
-            }
-            uint32_t aw[DT_UNROLL][4];
-#pragma unroll
-            for (int j = 0; j < DT_UNROLL; ++j) {
-                aw[j][0] = __ldg(acc + (w[j].x >> 5));
-                aw[j][1] = __ldg(acc + (w[j].y >> 5));
-                aw[j][2] = __ldg(acc + (w[j].z >> 5));
-                aw[j][3] = __ldg(acc + (w[j].w >> 5));
-            }
-#pragma unroll
-            for (int j = 0; j < DT_UNROLL; ++j) {
-                const uint32_t idx = cs + (j * DT_THREADS + threadIdx.x) * 4;
-                const uint32_t us[4] = {w[j].x, w[j].y, w[j].z, w[j].w};
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const uint32_t e = idx + q;
-                    const uint32_t u = us[q];
-                    if (e >= E0 && e < E1 && ((aw[j][q] >> (u & 31u)) & 1u)) {
-                        // row of edge e: the last r with srp[r] <= e
-                        uint32_t lo = 0, hi = rows; // srp[lo] <= e < srp[hi]
-                        while (hi - lo > 1) {
-                            const uint32_t mid = (lo + hi) >> 1;
-                            if (srp[mid] <= e) lo = mid;
-                            else hi = mid;
-                        }
-                        atomicMax(&sbest[lo], u + 1);
-                    }
-                }
+        // thread 0: the copies of the next tiles
+        if (threadIdx.x == 0 && i + 1 < my) {
+            const int rs1 = (i + 1) % 3;
+            if (mbar_wait(&S.bar_rp[rs1], ((i + 1) / 3) & 1u)) {
+                issue_col(S, cs ^ 1, rs1, t + gridDim.x, n, colidx);
+                if (i + 2 < my) issue_rp(S, (i + 2) % 3, t + 2 * gridDim.x, n, rowptr);
+            } else {
+                S.failed = 1;
             }
         }
+        // everyone: this tile's rowptr slice (ready since the previous step) and colidx span
+        bool ok = mbar_wait(&S.bar_rp[rs], (i / 3) & 1u) && mbar_wait(&S.bar_col[cs], (i >> 1) & 1u);
+        if (!ok) S.failed = 1;
+        if (ok) {
+            const uint32_t E0 = S.e0[cs], E1 = S.e1[cs];
+            if (S.staged[cs]) dense_edges<true>(S, S.col[cs], E0, E1, S.rp[rs], rows, acc);
+            else if (E1 > E0) dense_edges<false>(S, colidx, E0, E1, S.rp[rs], rows, acc);
+        }
         __syncthreads();
-        for (uint32_t i = threadIdx.x; i < rows; i += DT_THREADS) {
-            const uint32_t b = sbest[i];
-            mval[r0 + i] = b;
+        if (S.failed) break;
+        for (uint32_t r = threadIdx.x; r < rows; r += DT_THREADS) {
+            const uint32_t b = S.best[r];
+            mval[r0 + r] = b;
             if (b) {
+                S.best[r] = 0;
                 changed++;
-                mark_readers<1>(r0 + i, 0, rrowptr, rcol, bits, queue, &ctl->qcnt[0]);
+                mark_readers<1>(r0 + r, 0, rrowptr, rcol, bits, queue, &ctl->qcnt[0]);
             }
         }
         __syncthreads();
+    }
+    if (S.failed) {
+        // let this block's copies in flight land before the block exits (bounded)
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < 3; ++k) mbar_wait(&S.bar_rp[k], 0), mbar_wait(&S.bar_rp[k], 1);
+            for (int k = 0; k < 2; ++k) mbar_wait(&S.bar_col[k], 0), mbar_wait(&S.bar_col[k], 1);
+            atomicExch(&ctl->status, ST_TIMEOUT);
+        }
     }
     changed = __reduce_add_sync(0xFFFFFFFFu, changed);
     if (lane_id() == 0 && changed) atomicAdd(&ctl->ccnt, changed);
@@ -370,7 +530,7 @@ __global__ void __launch_bounds__(DT_THREADS) k_dense(uint32_t n, const uint32_t
 // the values of the previous round (mval is not written here).  Rows whose value
 // grows are appended to the change list.  Clears the frontier's bitmap.
 template <int G>
-__global__ void __launch_bounds__(256) k_sync_compute(const uint32_t *__restrict__ rowptr,
+__global__ void __launch_bounds__(256, 6) k_sync_compute(const uint32_t *__restrict__ rowptr,
                                                       const uint32_t *__restrict__ colidx,
                                                       const uint32_t *__restrict__ acc,
                                                       const uint32_t *__restrict__ mval, uint32_t *queue,
@@ -419,7 +579,7 @@ __global__ void __launch_bounds__(256) k_sync_compute(const uint32_t *__restrict
 // Synchronous round, apply half: write the new values and mark the readers of
 // every changed vertex into the frontier of the next round.
 template <int G>
-__global__ void __launch_bounds__(256) k_sync_apply(const uint32_t *__restrict__ chv,
+__global__ void __launch_bounds__(256, 8) k_sync_apply(const uint32_t *__restrict__ chv,
                                                     const uint32_t *__restrict__ chval, uint32_t *mval,
                                                     const uint32_t *__restrict__ rrowptr,
                                                     const uint32_t *__restrict__ rcol, uint32_t *queue, uint32_t *fbits,
@@ -448,7 +608,7 @@ __global__ void __launch_bounds__(256) k_sync_apply(const uint32_t *__restrict__
 // once (values only grow, so a racing reader sees the old or the new value and
 // the fix-point is the same), and its readers are marked at once.
 template <int G>
-__global__ void __launch_bounds__(256) k_async_sweep(const uint32_t *__restrict__ rowptr,
+__global__ void __launch_bounds__(256, 6) k_async_sweep(const uint32_t *__restrict__ rowptr,
                                                      const uint32_t *__restrict__ colidx,
                                                      const uint32_t *__restrict__ acc, uint32_t *mval,
                                                      const uint32_t *__restrict__ rrowptr,
