@@ -232,6 +232,9 @@ def main():
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s",
                 "share_of_step": (dense_ms / len(prof)) / (ms / args.steps) if ms else None,
                 "timing": "CUDA events around each dense launch in 2 extra host-stepped runs"}
+    phases = {"dense_ms_per_run": dense_ms / len(prof), "rounds_ms_per_run": sum(r.round_ms for r in prof) / len(prof),
+              "check_ms_per_run": sum(r.check_ms for r in prof) / len(prof),
+              "frontier_rows_per_run": prof[0].frontier_rows, "stepped_run_ms": prof[0].device_ms}
 
     # end to end through the C ABI from pinned host buffers
     hp = [torch.from_numpy(x.view(np.int32)).pin_memory() for x in (g.rowptr, g.colidx, pkg.pack_bits(g.acc))]
@@ -260,7 +263,7 @@ def main():
                            relaxations_per_run=r0.relaxations, verdict=r0.verdict,
                            l2="inputs larger than L2 (CSR 1.34 GB vs 129 MB L2); no flush",
                            parallelism="replicas" if ws > 1 else "single GPU"),
-            "roofline": roofline, "e2e": e2e, "gpu_launches": sum(r.launches for r in results),
+            "roofline": roofline, "phases": phases, "e2e": e2e, "gpu_launches": sum(r.launches for r in results),
             "clocks": clk.summary()}
     pkg.map_destroy(h)
     if rank == 0 and ws == 1 and not args.no_cpu:

@@ -69,7 +69,8 @@ enum { MAP_NO_CYCLE = 0, MAP_CYCLE = 1 };
 enum { MAP_SCHED_SYNC = 0, MAP_SCHED_ASYNC = 1 };
 
 /* opts.flags */
-#define MAP_FLAG_PROFILE 1u /* time the dense-round kernel with CUDA events (result.dense_ms) */
+#define MAP_FLAG_PROFILE 1u /* step the loop from the host and time each phase with CUDA events
+                               (result.dense_ms, round_ms, check_ms, frontier_rows) */
 
 /* Called after the fix-point of every outer iteration, before the cycle test
  * and the elimination: map[v] is map(v) of that iteration (MAP_NONE if none),
@@ -103,6 +104,9 @@ typedef struct {
     uint32_t dense_launches;  /* with MAP_FLAG_PROFILE: its launches */
     uint32_t accepting_left;  /* accepting vertices left at the end */
     uint64_t launches;        /* kernel launches issued by this run */
+    double round_ms;          /* with MAP_FLAG_PROFILE: summed time of the rounds after the first */
+    double check_ms;          /* with MAP_FLAG_PROFILE: summed time of the self-map test + elimination */
+    uint64_t frontier_rows;   /* with MAP_FLAG_PROFILE: frontier rows summed over the rounds after the first */
 } map_result;
 
 typedef struct map_graph map_graph; /* opaque: the device-resident graph and its work space */

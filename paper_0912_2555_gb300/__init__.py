@@ -65,6 +65,9 @@ class MapResult(ctypes.Structure):
         ("dense_launches", ctypes.c_uint32),
         ("accepting_left", ctypes.c_uint32),
         ("launches", ctypes.c_uint64),
+        ("round_ms", ctypes.c_double),
+        ("check_ms", ctypes.c_double),
+        ("frontier_rows", ctypes.c_uint64),
     ]
 
 
@@ -155,6 +158,9 @@ class RunResult:
     dense_launches: int
     accepting_left: int
     launches: int
+    round_ms: float
+    check_ms: float
+    frontier_rows: int
     trace: list
 
 
@@ -190,7 +196,8 @@ def map_run(handle, sched: int = MAP_SCHED_SYNC, max_outer: int = 0, max_inner: 
     return RunResult(rc, res.verdict, res.witness, res.outer_iters,
                      [int(x) for x in rounds[:min(res.outer_iters, rounds_cap)]], res.inner_iters,
                      bool(res.inner_canonical), res.relaxations, res.edges_total, res.device_ms, res.dense_ms,
-                     res.dense_launches, res.accepting_left, res.launches, tr)
+                     res.dense_launches, res.accepting_left, res.launches, res.round_ms, res.check_ms,
+                     res.frontier_rows, tr)
 
 
 def pack_bits(flags) -> np.ndarray:

@@ -90,7 +90,7 @@ struct map_graph {
     uint32_t *h_stage = nullptr; // pinned n words for traces / host output
     uint32_t *h_hist = nullptr;  // pinned mirror of hist
     uint32_t nacc0 = 0;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[8] = {};
     // the whole run as one CUDA graph, per schedule (built on first use)
     cudaGraph_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
@@ -358,11 +358,10 @@ int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const
     cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev);
     if (g->sms <= 0) g->sms = 1;
     int occ = 0;
-    cudaFuncSetAttribute(mapk::k_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mapk::DT_SMEM);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mapk::k_dense, mapk::DT_THREADS, mapk::DT_SMEM);
     if (occ <= 0) occ = 1;
-    const uint64_t ntiles = ((uint64_t)n + mapk::DT_ROWS - 1) / mapk::DT_ROWS;
-    g->dense_grid = (int)std::min<uint64_t>(ntiles, (uint64_t)g->sms * occ);
+    const uint64_t ntiles = ((uint64_t)n + mapk::WT_ROWS - 1) / mapk::WT_ROWS;
+    g->dense_grid = (int)std::min<uint64_t>((ntiles + mapk::WT_WARPS - 1) / mapk::WT_WARPS, (uint64_t)g->sms * occ);
     g->sparse_grid = (int)std::min<uint64_t>(((uint64_t)n * g->G + 255) / 256 + 1, (uint64_t)g->sms * 6);
     g->check_grid = (int)std::min<uint64_t>(((uint64_t)n / 4 + 255) / 256 + 1, (uint64_t)g->sms * 4);
     g->hist_cap = 1u << 16;
@@ -500,7 +499,7 @@ int map_run(map_graph *g, const map_opts *opts_in, map_result *res, uint32_t *ma
     init.witness = mapk::NONE;
 
     int rc = MAP_OK;
-    float dense_ms = 0.f;
+    float dense_ms = 0.f, round_ms = 0.f, check_ms = 0.f;
     if (!stepped) {
         if ((rc = build_run_graph(g, opts.sched))) return rc;
         *g->h_ctl = init;
@@ -531,8 +530,16 @@ int map_run(map_graph *g, const map_opts *opts_in, map_result *res, uint32_t *ma
                 res->dense_launches++;
             }
             while (g->h_ctl->inner_go) {
+                res->frontier_rows += g->h_ctl->qcnt[(g->h_ctl->k + 1) & 1];
+                if (profile) CK(cudaEventRecord(g->ev[4], s));
                 if ((rc = launch_round(g, s, sync_sched, none))) return rc;
+                if (profile) CK(cudaEventRecord(g->ev[5], s));
                 if ((rc = read_ctl(g))) return rc;
+                if (profile) {
+                    float ms = 0.f;
+                    CK(cudaEventElapsedTime(&ms, g->ev[4], g->ev[5]));
+                    round_ms += ms;
+                }
             }
             if (opts.trace) {
                 const uint32_t outer = g->h_ctl->outer, k = g->h_ctl->k;
@@ -541,8 +548,15 @@ int map_run(map_graph *g, const map_opts *opts_in, map_result *res, uint32_t *ma
                 CK(cudaStreamSynchronize(s));
                 opts.trace(opts.user, outer, g->h_stage, n, k);
             }
+            if (profile) CK(cudaEventRecord(g->ev[6], s));
             if ((rc = launch_check(g, s, none))) return rc;
+            if (profile) CK(cudaEventRecord(g->ev[7], s));
             if ((rc = read_ctl(g))) return rc;
+            if (profile) {
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, g->ev[6], g->ev[7]));
+                check_ms += ms;
+            }
         }
         if ((rc = launch_export(g, s, nullptr))) return rc;
         CK(cudaEventRecord(g->ev[1], s));
@@ -561,6 +575,8 @@ int map_run(map_graph *g, const map_opts *opts_in, map_result *res, uint32_t *ma
     res->edges_total = g->m * (uint64_t)c.outer;
     res->device_ms = total_ms;
     res->dense_ms = dense_ms;
+    res->round_ms = round_ms;
+    res->check_ms = check_ms;
     res->accepting_left = c.nacc;
     // launches: reset (memcpy + memset are not kernels), run_begin, export, and per outer
     // iteration dense + check, per round 2 (SYNC) or 1 (ASYNC)

@@ -276,244 +276,112 @@ __device__ __forceinline__ void mark_readers(uint32_t u, unsigned glane, const u
 // so the value u offers is u + 1 if u is accepting and 0 otherwise: only the
 // accepting bitmap is gathered.
 //
-// A block walks its tiles of DT_ROWS consecutive rows.  For each tile, thread 0
-// stages the rowptr slice and the tile's whole colidx span into shared memory
-// with bulk asynchronous copies (cp.async.bulk, completion on an mbarrier):
-// rowptr slices run two tiles ahead (3-slot ring), colidx spans one tile ahead
-// (2-slot ring), so the copies of the next tiles are in flight while the block
-// gathers accepting bits for the current one.  A tile whose span exceeds
-// DT_CAP words reads its edges straight from global memory instead.  An edge
-// that offers a value finds its row by binary search in the rowptr slice and
-// does a shared-memory atomicMax; the tile's values are then written out
-// coalesced (this also resets the previous iteration's values), and the
-// readers of every row that got a value are marked into the round-2 frontier.
-//
-// Every mbarrier wait is bounded; a wait that gives up sets ctl->status to
-// ST_TIMEOUT, waits (bounded) for the copies this block has in flight, and the
-// block leaves its tile loop.
+// Each warp owns tiles of WT_ROWS consecutive rows, with no block-wide phase:
+// the tile's rowptr slice (fetched one tile ahead into registers) goes to a
+// warp-private shared slice; the tile's edge span is streamed with 128-bit
+// loads (WT_UNROLL per lane, then 4 * WT_UNROLL independent bitmap gathers);
+// an edge that offers a value finds its row by binary search in the slice and
+// does a shared-memory atomicMax; the tile's values are written out coalesced
+// (this also resets the previous iteration's values) and the readers of every
+// row that got a value are marked into the round-2 frontier.
 constexpr int DT_THREADS = 256;
-constexpr int DT_ROWS = 1024;
-constexpr int DT_RPW = DT_ROWS + 4; // rowptr slice words (16-byte multiple)
-constexpr int DT_CAP = 8192;        // colidx words a tile may stage
-constexpr int DT_UNROLL = 4;        // 128-bit words per thread per pass
+constexpr int WT_WARPS = DT_THREADS / 32;
+constexpr int WT_ROWS = 128;
+constexpr int WT_UNROLL = 4;
+constexpr size_t DT_SMEM = 0; // static shared memory only
 
-struct DenseSmem {
-    uint32_t rp[3][DT_RPW];
-    uint32_t col[2][DT_CAP];
-    uint32_t best[DT_ROWS];
-    unsigned long long bar_rp[3];
-    unsigned long long bar_col[2];
-    uint32_t e0[2], e1[2], staged[2]; // per colidx slot: the tile's edge span and how it is read
-    uint32_t failed;
-};
-constexpr size_t DT_SMEM = sizeof(DenseSmem);
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long *bar)
+__global__ void __launch_bounds__(DT_THREADS, 4) k_dense(uint32_t n, const uint32_t *__restrict__ rowptr,
+                                                         const uint32_t *__restrict__ colidx,
+                                                         const uint32_t *__restrict__ acc,
+                                                         uint32_t *__restrict__ mval,
+                                                         const uint32_t *__restrict__ rrowptr,
+                                                         const uint32_t *__restrict__ rcol, uint32_t *bits,
+                                                         uint32_t *queue, Ctl *ctl, Handles hd)
 {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// arrive (the single expected arrival) and announce `bytes` of asynchronous transfer
-__device__ __forceinline__ void mbar_arrive_tx(unsigned long long *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// bounded wait for the phase with the given parity to complete
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity)
-{
-    for (uint32_t it = 0; it < (1u << 22); ++it) {
-        uint32_t ok;
-        asm volatile("{\n\t.reg .pred p;\n\t"
-                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}"
-                     : "=r"(ok)
-                     : "r"(smem_u32(bar)), "r"(parity)
-                     : "memory");
-        if (ok) return true;
-        if (it > 64) __nanosleep(64);
-    }
-    return false;
-}
-
-// global -> shared bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned)
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, unsigned long long *bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// thread 0: stage the rowptr slice of tile t into slot `slot`
-__device__ __forceinline__ void issue_rp(DenseSmem &S, int slot, uint32_t t, uint32_t n,
-                                         const uint32_t *__restrict__ rowptr)
-{
-    const uint32_t r0 = t * DT_ROWS;
-    const uint32_t rows = min((uint32_t)DT_ROWS, n - r0);
-    const uint32_t words = (rows + 1 + 3) & ~3u; // the allocation has 4 words of slack past rowptr[n]
-    fence_proxy_async();
-    mbar_arrive_tx(&S.bar_rp[slot], words * 4);
-    bulk_g2s(S.rp[slot], rowptr + r0, words * 4, &S.bar_rp[slot]);
-}
-
-// thread 0, once the rowptr slice of tile t is in slot rslot: stage its colidx
-// span into colidx slot cslot (or mark it to be read from global memory)
-__device__ __forceinline__ void issue_col(DenseSmem &S, int cslot, int rslot, uint32_t t, uint32_t n,
-                                          const uint32_t *__restrict__ colidx)
-{
-    const uint32_t r0 = t * DT_ROWS;
-    const uint32_t rows = min((uint32_t)DT_ROWS, n - r0);
-    const uint32_t E0 = S.rp[rslot][0], E1 = S.rp[rslot][rows];
-    const uint32_t a0 = E0 & ~3u, a1 = (E1 + 3) & ~3u; // slack of 4 words past colidx[m]
-    S.e0[cslot] = E0;
-    S.e1[cslot] = E1;
-    if (E1 > E0 && a1 - a0 <= (uint32_t)DT_CAP) {
-        S.staged[cslot] = 1;
-        fence_proxy_async();
-        mbar_arrive_tx(&S.bar_col[cslot], (a1 - a0) * 4);
-        bulk_g2s(S.col[cslot], colidx + a0, (a1 - a0) * 4, &S.bar_col[cslot]);
-    } else {
-        S.staged[cslot] = 0;
-        mbar_arrive(&S.bar_col[cslot]); // complete the phase without a copy
-    }
-}
-
-// the edges [E0, E1) of a tile: gather accepting bits, find rows, atomicMax into best
-template <bool STAGED>
-__device__ __forceinline__ void dense_edges(DenseSmem &S, const uint32_t *__restrict__ src, uint32_t E0, uint32_t E1,
-                                            const uint32_t *__restrict__ rp, uint32_t rows,
-                                            const uint32_t *__restrict__ acc)
-{
-    const uint32_t a0 = E0 & ~3u;
-    const uint32_t nq = ((E1 + 3) & ~3u) - a0 >> 2; // 128-bit words in the span
-    for (uint32_t q0 = 0; q0 < nq; q0 += DT_THREADS * DT_UNROLL) {
-        uint4 w[DT_UNROLL];
+    __shared__ __align__(16) uint32_t s_rp[WT_WARPS][WT_ROWS + 4];
+    __shared__ __align__(16) uint32_t s_best[WT_WARPS][WT_ROWS];
+    default_stop(ctl, hd.outer);
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    uint32_t *rp = s_rp[warp], *best = s_best[warp];
+    const uint32_t ntiles = (n + WT_ROWS - 1) / WT_ROWS;
+    const uint32_t nw = gridDim.x * WT_WARPS;
+    unsigned changed = 0;
 #pragma unroll
-        for (int j = 0; j < DT_UNROLL; ++j) {
-            const uint32_t q = q0 + j * DT_THREADS + threadIdx.x;
-            if (q < nq) {
-                if (STAGED) w[j] = reinterpret_cast<const uint4 *>(src)[q];
-                else w[j] = __ldg(reinterpret_cast<const uint4 *>(src + a0) + q);
-            } else {
-                w[j] = make_uint4(0, 0, 0, 0);
+    for (int k = 0; k < 4; ++k) best[lane * 4 + k] = 0;
+
+    // rowptr words r0 + 4 lane .. + 3 of tile t (only the words that exist: <= r0 + rows + 3)
+    auto load_rp = [&](uint32_t t, uint4 &q, uint32_t &last) {
+        const uint32_t r0 = t * WT_ROWS, rows = min((uint32_t)WT_ROWS, n - r0);
+        q = lane * 4 <= rows ? __ldg(reinterpret_cast<const uint4 *>(rowptr + r0) + lane) : make_uint4(0, 0, 0, 0);
+        last = (lane == 0 && rows == WT_ROWS) ? __ldg(rowptr + r0 + WT_ROWS) : 0;
+    };
+    uint32_t t = blockIdx.x * WT_WARPS + warp;
+    uint4 q = make_uint4(0, 0, 0, 0);
+    uint32_t qlast = 0;
+    if (t < ntiles) load_rp(t, q, qlast);
+    for (; t < ntiles; t += nw) {
+        const uint32_t r0 = t * WT_ROWS, rows = min((uint32_t)WT_ROWS, n - r0);
+        reinterpret_cast<uint4 *>(rp)[lane] = q;
+        if (lane == 0 && rows == WT_ROWS) rp[WT_ROWS] = qlast;
+        if (t + nw < ntiles) load_rp(t + nw, q, qlast); // next tile's slice, in flight meanwhile
+        __syncwarp();
+        const uint32_t E0 = rp[0], E1 = rp[rows];
+        for (uint32_t cs = E0 & ~3u; cs < E1; cs += 32 * 4 * WT_UNROLL) {
+            uint4 w[WT_UNROLL];
+#pragma unroll
+            for (int j = 0; j < WT_UNROLL; ++j) {
+                const uint32_t idx = cs + (j * 32 + lane) * 4;
+                w[j] = idx < E1 ? __ldg(reinterpret_cast<const uint4 *>(colidx + idx)) : make_uint4(0, 0, 0, 0);
             }
-        }
-        uint32_t aw[DT_UNROLL][4];
+            uint32_t aw[WT_UNROLL][4];
 #pragma unroll
-        for (int j = 0; j < DT_UNROLL; ++j) {
-            aw[j][0] = __ldg(acc + (w[j].x >> 5));
-            aw[j][1] = __ldg(acc + (w[j].y >> 5));
-            aw[j][2] = __ldg(acc + (w[j].z >> 5));
-            aw[j][3] = __ldg(acc + (w[j].w >> 5));
-        }
+            for (int j = 0; j < WT_UNROLL; ++j) {
+                aw[j][0] = __ldg(acc + (w[j].x >> 5));
+                aw[j][1] = __ldg(acc + (w[j].y >> 5));
+                aw[j][2] = __ldg(acc + (w[j].z >> 5));
+                aw[j][3] = __ldg(acc + (w[j].w >> 5));
+            }
 #pragma unroll
-        for (int j = 0; j < DT_UNROLL; ++j) {
-            const uint32_t ebase = a0 + (q0 + j * DT_THREADS + threadIdx.x) * 4;
-            const uint32_t us[4] = {w[j].x, w[j].y, w[j].z, w[j].w};
+            for (int j = 0; j < WT_UNROLL; ++j) {
+                const uint32_t ebase = cs + (j * 32 + lane) * 4;
+                const uint32_t us[4] = {w[j].x, w[j].y, w[j].z, w[j].w};
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const uint32_t e = ebase + k;
-                const uint32_t u = us[k];
-                if (e >= E0 && e < E1 && ((aw[j][k] >> (u & 31u)) & 1u)) {
-                    uint32_t lo = 0, hi = rows; // rp[lo] <= e < rp[hi]: the row of e is the last such lo
-                    while (hi - lo > 1) {
-                        const uint32_t mid = (lo + hi) >> 1;
-                        if (rp[mid] <= e) lo = mid;
-                        else hi = mid;
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t e = ebase + k, u = us[k];
+                    if (e >= E0 && e < E1 && ((aw[j][k] >> (u & 31u)) & 1u)) {
+                        uint32_t lo = 0, hi = rows; // rp[lo] <= e < rp[hi]: the row of e is the last such lo
+                        while (hi - lo > 1) {
+                            const uint32_t mid = (lo + hi) >> 1;
+                            if (rp[mid] <= e) lo = mid;
+                            else hi = mid;
+                        }
+                        atomicMax(&best[lo], u + 1);
                     }
-                    atomicMax(&S.best[lo], u + 1);
                 }
             }
         }
-    }
-}
-
-__global__ void __launch_bounds__(DT_THREADS, 2) k_dense(uint32_t n, const uint32_t *__restrict__ rowptr,
-                                                      const uint32_t *__restrict__ colidx,
-                                                      const uint32_t *__restrict__ acc, uint32_t *__restrict__ mval,
-                                                      const uint32_t *__restrict__ rrowptr,
-                                                      const uint32_t *__restrict__ rcol, uint32_t *bits,
-                                                      uint32_t *queue, Ctl *ctl, Handles hd)
-{
-    extern __shared__ __align__(128) unsigned char dense_smem[];
-    DenseSmem &S = *reinterpret_cast<DenseSmem *>(dense_smem);
-    default_stop(ctl, hd.outer);
-    const uint32_t ntiles = (n + DT_ROWS - 1) / DT_ROWS;
-    const uint32_t my = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    unsigned changed = 0;
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < 3; ++i) mbar_init(&S.bar_rp[i]);
-        for (int i = 0; i < 2; ++i) mbar_init(&S.bar_col[i]);
-        S.failed = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        fence_proxy_async();
-    }
-    for (uint32_t i = threadIdx.x; i < DT_ROWS; i += DT_THREADS) S.best[i] = 0;
-    __syncthreads();
-    if (threadIdx.x == 0 && my > 0) {
-        issue_rp(S, 0, blockIdx.x, n, rowptr);
-        if (my > 1) issue_rp(S, 1, blockIdx.x + gridDim.x, n, rowptr);
-        if (mbar_wait(&S.bar_rp[0], 0)) issue_col(S, 0, 0, blockIdx.x, n, colidx);
-        else S.failed = 1;
-    }
-    __syncthreads();
-    for (uint32_t i = 0; i < my && !S.failed; ++i) {
-        const uint32_t t = blockIdx.x + i * gridDim.x;
-        const int rs = i % 3, cs = i & 1;
-        const uint32_t r0 = t * DT_ROWS;
-        const uint32_t rows = min((uint32_t)DT_ROWS, n - r0);
-        // thread 0: the copies of the next tiles
-        if (threadIdx.x == 0 && i + 1 < my) {
-            const int rs1 = (i + 1) % 3;
-            if (mbar_wait(&S.bar_rp[rs1], ((i + 1) / 3) & 1u)) {
-                issue_col(S, cs ^ 1, rs1, t + gridDim.x, n, colidx);
-                if (i + 2 < my) issue_rp(S, (i + 2) % 3, t + 2 * gridDim.x, n, rowptr);
-            } else {
-                S.failed = 1;
-            }
+        __syncwarp();
+        const uint4 b4 = reinterpret_cast<const uint4 *>(best)[lane];
+        const uint32_t bs[4] = {b4.x, b4.y, b4.z, b4.w};
+        if (lane * 4 + 3 < rows) {
+            reinterpret_cast<uint4 *>(mval + r0)[lane] = b4;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (lane * 4 + k < rows) mval[r0 + lane * 4 + k] = bs[k];
         }
-        // everyone: this tile's rowptr slice (ready since the previous step) and colidx span
-        bool ok = mbar_wait(&S.bar_rp[rs], (i / 3) & 1u) && mbar_wait(&S.bar_col[cs], (i >> 1) & 1u);
-        if (!ok) S.failed = 1;
-        if (ok) {
-            const uint32_t E0 = S.e0[cs], E1 = S.e1[cs];
-            if (S.staged[cs]) dense_edges<true>(S, S.col[cs], E0, E1, S.rp[rs], rows, acc);
-            else if (E1 > E0) dense_edges<false>(S, colidx, E0, E1, S.rp[rs], rows, acc);
-        }
-        __syncthreads();
-        if (S.failed) break;
-        for (uint32_t r = threadIdx.x; r < rows; r += DT_THREADS) {
-            const uint32_t b = S.best[r];
-            mval[r0 + r] = b;
-            if (b) {
-                S.best[r] = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (bs[k] && lane * 4 + k < rows) {
+                best[lane * 4 + k] = 0;
                 changed++;
-                mark_readers<1>(r0 + r, 0, rrowptr, rcol, bits, queue, &ctl->qcnt[0]);
+                mark_readers<1>(r0 + lane * 4 + k, 0, rrowptr, rcol, bits, queue, &ctl->qcnt[0]);
             }
         }
-        __syncthreads();
-    }
-    if (S.failed) {
-        // let this block's copies in flight land before the block exits (bounded)
-        if (threadIdx.x == 0) {
-            for (int k = 0; k < 3; ++k) mbar_wait(&S.bar_rp[k], 0), mbar_wait(&S.bar_rp[k], 1);
-            for (int k = 0; k < 2; ++k) mbar_wait(&S.bar_col[k], 0), mbar_wait(&S.bar_col[k], 1);
-            atomicExch(&ctl->status, ST_TIMEOUT);
-        }
+        __syncwarp();
     }
     changed = __reduce_add_sync(0xFFFFFFFFu, changed);
-    if (lane_id() == 0 && changed) atomicAdd(&ctl->ccnt, changed);
+    if (lane == 0 && changed) atomicAdd(&ctl->ccnt, changed);
     if (last_block(ctl)) epilogue_dense(ctl, hd);
 }
 
