@@ -81,8 +81,13 @@ struct map_graph {
     int check_grid = 0;  // blocks of the self-map / elimination kernel
     cudaStream_t stream = nullptr;
     uint32_t *rowptr = nullptr, *colidx = nullptr, *rrowptr = nullptr, *rcol = nullptr;
-    uint32_t *acc0 = nullptr, *acc = nullptr, *mval = nullptr, *fbits = nullptr, *queue = nullptr;
-    uint32_t *chv = nullptr, *chval = nullptr;
+    uint32_t *acc0 = nullptr, *acc = nullptr, *mval = nullptr;
+    uint32_t *list = nullptr;  // 2n: vertices changed in a round, by parity
+    uint32_t *snap = nullptr;  // 2n: their values at the end of the round
+    uint32_t *flist = nullptr; // 2n: frontier rows of a round, by parity
+    uint32_t *bits = nullptr;  // 4W: cbit[2], fbit[2]
+    uint32_t *touched = nullptr, *xbuf = nullptr;
+    bool dirty = false; // a run stopped early: per-round state may be stale
     uint32_t *hist = nullptr; // rounds per outer iteration
     uint32_t hist_cap = 0;
     Ctl *ctl = nullptr;
@@ -106,8 +111,8 @@ void free_graph(map_graph *g)
         if (g->exec[i]) cudaGraphExecDestroy(g->exec[i]);
         if (g->graph[i]) cudaGraphDestroy(g->graph[i]);
     }
-    void *dev[] = {g->rowptr, g->colidx, g->rrowptr, g->rcol, g->acc0, g->acc,  g->mval,
-                   g->fbits,  g->queue,  g->chv,     g->chval, g->hist, g->ctl};
+    void *dev[] = {g->rowptr, g->colidx, g->rrowptr, g->rcol,    g->acc0, g->acc, g->mval, g->list,
+                   g->snap,   g->flist,  g->bits,    g->touched, g->xbuf, g->hist, g->ctl};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (g->h_ctl) cudaFreeHost(g->h_ctl);
@@ -169,28 +174,44 @@ int read_ctl(map_graph *g)
 
 // --- the steps of a run, issued on stream s (shared by both drivers) -------
 
+mapk::Dev dev_of(const map_graph *g)
+{
+    mapk::Dev d;
+    d.n = g->n;
+    d.words = g->words;
+    d.rowptr = g->rowptr;
+    d.colidx = g->colidx;
+    d.rrowptr = g->rrowptr;
+    d.rcol = g->rcol;
+    d.acc = g->acc;
+    d.mval = g->mval;
+    const size_t n = g->n, W = g->words;
+    for (int p = 0; p < 2; ++p) {
+        d.list[p] = g->list + p * n;
+        d.snap[p] = g->snap + p * n;
+        d.flist[p] = g->flist + p * n;
+        d.cbit[p] = g->bits + p * W;
+        d.fbit[p] = g->bits + (2 + p) * W;
+    }
+    d.touched = g->touched;
+    d.ctl = g->ctl;
+    return d;
+}
+
 int launch_dense(map_graph *g, cudaStream_t s, mapk::Handles hd)
 {
-    mapk::k_dense<<<g->dense_grid, mapk::DT_THREADS, mapk::DT_SMEM, s>>>(g->n, g->rowptr, g->colidx, g->acc, g->mval,
-                                                              g->rrowptr, g->rcol, g->fbits, g->queue, g->ctl, hd);
+    mapk::k_dense<<<g->dense_grid, mapk::DT_THREADS, mapk::DT_SMEM, s>>>(dev_of(g), hd);
     CK(cudaGetLastError());
     return MAP_OK;
 }
 
 int launch_round(map_graph *g, cudaStream_t s, bool sync_sched, mapk::Handles hd)
 {
-    const int G = g->G;
+    const mapk::Dev d = dev_of(g);
     if (sync_sched) {
-        DISPATCH_G(G, (mapk::k_sync_compute<GG><<<g->sparse_grid, 256, 0, s>>>(
-                          g->rowptr, g->colidx, g->acc, g->mval, g->queue, g->fbits, g->n, g->words, g->chv,
-                          g->chval, g->ctl, hd)));
-        DISPATCH_G(G, (mapk::k_sync_apply<GG><<<g->sparse_grid, 256, 0, s>>>(
-                          g->chv, g->chval, g->mval, g->rrowptr, g->rcol, g->queue, g->fbits, g->n, g->words,
-                          g->ctl, hd)));
+        DISPATCH_G(g->G, (mapk::k_push<GG, true><<<g->sparse_grid, 256, 0, s>>>(d, hd)));
     } else {
-        DISPATCH_G(G, (mapk::k_async_sweep<GG><<<g->sparse_grid, 256, 0, s>>>(
-                          g->rowptr, g->colidx, g->acc, g->mval, g->rrowptr, g->rcol, g->queue, g->fbits, g->n,
-                          g->words, g->ctl, hd)));
+        DISPATCH_G(g->G, (mapk::k_push<GG, false><<<g->sparse_grid, 256, 0, s>>>(d, hd)));
     }
     CK(cudaGetLastError());
     return MAP_OK;
@@ -198,15 +219,16 @@ int launch_round(map_graph *g, cudaStream_t s, bool sync_sched, mapk::Handles hd
 
 int launch_check(map_graph *g, cudaStream_t s, mapk::Handles hd)
 {
-    mapk::k_check_eliminate<<<g->check_grid, 256, 0, s>>>(g->n, g->mval, g->acc, g->ctl, hd);
+    mapk::k_check<<<g->check_grid, 256, 0, s>>>(dev_of(g), hd);
     CK(cudaGetLastError());
     return MAP_OK;
 }
 
+// per-run reset: the accepting set, the bitmaps (and the snapshots after a run that stopped early)
 int launch_reset(map_graph *g, cudaStream_t s)
 {
     CK(cudaMemcpyAsync(g->acc, g->acc0, (size_t)g->words * 4, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemsetAsync(g->fbits, 0, (size_t)2 * g->words * 4, s));
+    CK(cudaMemsetAsync(g->bits, 0, (size_t)4 * g->words * 4, s));
     return MAP_OK;
 }
 
@@ -363,7 +385,7 @@ int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const
     const uint64_t ntiles = ((uint64_t)n + mapk::WT_ROWS - 1) / mapk::WT_ROWS;
     g->dense_grid = (int)std::min<uint64_t>((ntiles + mapk::WT_WARPS - 1) / mapk::WT_WARPS, (uint64_t)g->sms * occ);
     g->sparse_grid = (int)std::min<uint64_t>(((uint64_t)n * g->G + 255) / 256 + 1, (uint64_t)g->sms * 6);
-    g->check_grid = (int)std::min<uint64_t>(((uint64_t)n / 4 + 255) / 256 + 1, (uint64_t)g->sms * 4);
+    g->check_grid = (int)std::min<uint64_t>(((uint64_t)n + 255) / 256, (uint64_t)g->sms * 4);
     g->hist_cap = 1u << 16;
 
     auto alloc = [&](uint32_t **p, uint64_t words) -> int {
@@ -374,8 +396,9 @@ int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const
     const uint64_t W = g->words;
     if ((rc = alloc(&g->rowptr, (uint64_t)n + 1)) || (rc = alloc(&g->colidx, m)) ||
         (rc = alloc(&g->rrowptr, (uint64_t)n + 1)) || (rc = alloc(&g->rcol, m)) || (rc = alloc(&g->acc0, W)) ||
-        (rc = alloc(&g->acc, W)) || (rc = alloc(&g->mval, n)) || (rc = alloc(&g->fbits, 2 * W)) ||
-        (rc = alloc(&g->queue, 2 * (uint64_t)n)) || (rc = alloc(&g->chv, n)) || (rc = alloc(&g->chval, n)) ||
+        (rc = alloc(&g->acc, W)) || (rc = alloc(&g->mval, n)) || (rc = alloc(&g->list, 2 * (uint64_t)n)) ||
+        (rc = alloc(&g->snap, 2 * (uint64_t)n)) || (rc = alloc(&g->flist, 2 * (uint64_t)n)) ||
+        (rc = alloc(&g->bits, 4 * W)) || (rc = alloc(&g->touched, n)) || (rc = alloc(&g->xbuf, n)) ||
         (rc = alloc(&g->hist, g->hist_cap))) {
         free_graph(g);
         return rc;
@@ -419,17 +442,18 @@ int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const
     if ((rc = ck(cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), s), "memset ctl")) ||
         (rc = ck(cudaMemsetAsync(g->colidx + m, 0, 16, s), "pad")) ||
         (rc = ck(cudaMemsetAsync(g->mval, 0, ((size_t)n + 4) * 4, s), "memset mval")) ||
-        (rc = ck(cudaMemsetAsync(g->fbits, 0, 2 * W * 4, s), "memset fbits"))) {
+        (rc = ck(cudaMemsetAsync(g->snap, 0, (2 * (size_t)n + 4) * 4, s), "memset snap")) ||
+        (rc = ck(cudaMemsetAsync(g->bits, 0, 4 * W * 4, s), "memset bits"))) {
         free_graph(g);
         return rc;
     }
-    mapk::k_validate<<<grid_for(g, m > n ? m : n, 1), 256, 0, s>>>(n, g->rowptr, m, g->colidx, &g->ctl->ccnt);
+    mapk::k_validate<<<grid_for(g, m > n ? m : n, 1), 256, 0, s>>>(n, g->rowptr, m, g->colidx, &g->ctl->bad);
     mapk::k_acc_init<<<grid_for(g, W, 1), 256, 0, s>>>(n, acc_in, g->acc0, &g->ctl->elim);
     if ((rc = ck(cudaGetLastError(), "validate")) || (rc = read_ctl(g))) {
         free_graph(g);
         return rc;
     }
-    if (g->h_ctl->ccnt) {
+    if (g->h_ctl->bad) {
         free_graph(g);
         return fail(MAP_ERR_CSR, "map_create: invalid CSR (decreasing rowptr or colidx >= n)");
     }
@@ -445,12 +469,12 @@ int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const
         free_graph(g);
         return rc;
     }
-    // cursor = rrowptr[0..n) (reuse the queue space)
-    if ((rc = ck(cudaMemcpyAsync(g->queue, g->rrowptr, (size_t)n * 4, cudaMemcpyDeviceToDevice, s), "cursor"))) {
+    // cursor = rrowptr[0..n) (reuse the list space)
+    if ((rc = ck(cudaMemcpyAsync(g->list, g->rrowptr, (size_t)n * 4, cudaMemcpyDeviceToDevice, s), "cursor"))) {
         free_graph(g);
         return rc;
     }
-    DISPATCH_G(g->G, (mapk::k_transpose<GG><<<grid_for(g, n, GG), 256, 0, s>>>(n, g->rowptr, g->colidx, g->queue,
+    DISPATCH_G(g->G, (mapk::k_transpose<GG><<<grid_for(g, n, GG), 256, 0, s>>>(n, g->rowptr, g->colidx, g->list,
                                                                               g->rcol)));
     if ((rc = ck(cudaGetLastError(), "transpose")) || (rc = ck(cudaStreamSynchronize(s), "create sync"))) {
         free_graph(g);
@@ -493,13 +517,17 @@ int map_run(map_graph *g, const map_opts *opts_in, map_result *res, uint32_t *ma
     init.m = g->m;
     init.nacc0 = g->nacc0;
     init.rounds_hist = g->hist;
-    init.out = out_dev ? map_out : g->chv;
+    init.out = out_dev ? map_out : g->xbuf;
     init.use_graph = stepped ? 0 : 1;
     init.timeout_ns = (uint64_t)(opts.timeout_ms ? opts.timeout_ms : 120000u) * 1000000ull;
     init.witness = mapk::NONE;
 
     int rc = MAP_OK;
     float dense_ms = 0.f, round_ms = 0.f, check_ms = 0.f;
+    if (g->dirty) { // the previous run stopped early: clear the snapshots it may have left
+        CK(cudaMemsetAsync(g->snap, 0, (2 * (size_t)n + 4) * 4, s));
+    }
+    g->dirty = true; // until this run completes normally
     if (!stepped) {
         if ((rc = build_run_graph(g, opts.sched))) return rc;
         *g->h_ctl = init;
@@ -530,11 +558,11 @@ int map_run(map_graph *g, const map_opts *opts_in, map_result *res, uint32_t *ma
                 res->dense_launches++;
             }
             while (g->h_ctl->inner_go) {
-                res->frontier_rows += g->h_ctl->qcnt[(g->h_ctl->k + 1) & 1];
                 if (profile) CK(cudaEventRecord(g->ev[4], s));
                 if ((rc = launch_round(g, s, sync_sched, none))) return rc;
                 if (profile) CK(cudaEventRecord(g->ev[5], s));
                 if ((rc = read_ctl(g))) return rc;
+                res->frontier_rows += g->h_ctl->fcnt[g->h_ctl->k & 1];
                 if (profile) {
                     float ms = 0.f;
                     CK(cudaEventElapsedTime(&ms, g->ev[4], g->ev[5]));
@@ -543,8 +571,8 @@ int map_run(map_graph *g, const map_opts *opts_in, map_result *res, uint32_t *ma
             }
             if (opts.trace) {
                 const uint32_t outer = g->h_ctl->outer, k = g->h_ctl->k;
-                if ((rc = launch_export(g, s, g->chval))) return rc; // chval is free between rounds
-                CK(cudaMemcpyAsync(g->h_stage, g->chval, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+                if ((rc = launch_export(g, s, g->xbuf))) return rc;
+                CK(cudaMemcpyAsync(g->h_stage, g->xbuf, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
                 CK(cudaStreamSynchronize(s));
                 opts.trace(opts.user, outer, g->h_stage, n, k);
             }
@@ -589,10 +617,11 @@ int map_run(map_graph *g, const map_opts *opts_in, map_result *res, uint32_t *ma
         memcpy(opts.rounds_out, g->h_hist, (size_t)std::min(nh, opts.rounds_cap) * 4);
     }
     if (map_out && !out_dev) {
-        CK(cudaMemcpyAsync(g->h_stage, g->chv, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(g->h_stage, g->xbuf, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         memcpy(map_out, g->h_stage, (size_t)n * 4);
     }
+    g->dirty = c.status != mapk::ST_OK;
     if (c.status == mapk::ST_LIMIT) return fail(MAP_ERR_LIMIT, "map_run: max_outer or max_inner reached");
     if (c.status == mapk::ST_TIMEOUT)
         return fail(MAP_ERR_TIMEOUT, "map_run: stopped after timeout_ms = %u", opts.timeout_ms ? opts.timeout_ms : 120000u);

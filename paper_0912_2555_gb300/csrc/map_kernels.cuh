@@ -1,21 +1,27 @@
 // map_kernels.cuh -- sm_103a kernels of the MAP hot path (Section 2 of the paper).
 //
 // Device layout of one graph (all u32 unless noted):
-//   rowptr[n+1], colidx[m]      the CSR handed in: row v = successors of v in G,
-//                               i.e. the pull matrix of the transposed graph;
-//   rrowptr[n+1], rcol[m]       its transpose: rcol[rrowptr[u] ..] are the
-//                               readers of u (the rows that contain u);
-//   acc[W], W = ceil(n/32)      the current accepting set, LSB-first bitmap;
-//   mval[n]                     enc(map(v)): 0 = no value, u + 1 = vertex u;
-//   fbits[2][W]                 frontier de-duplication, one bitmap per round parity;
-//   queue[2][n]                 frontier of a round, by round parity;
-//   chv[n], chval[n]            synchronous rounds: (vertex, new value) changes.
-//   Ctl                         the control block below (one per graph).
+//   rowptr[n+1], colidx[m]   the CSR handed in: row v = successors of v in G, i.e.
+//                            the pull matrix of the transposed graph;
+//   rrowptr[n+1], rcol[m]    its transpose: rcol[rrowptr[u] ..] are the readers
+//                            of u (the rows that contain u);
+//   acc[W], W = ceil(n/32)   the current accepting set, LSB-first bitmap;
+//   mval[n]                  enc(map(v)): 0 = no value, u + 1 = vertex u;
+//   list[2][n], cbit[2][W]   vertices whose value changed in a round (by round
+//                            parity) and the bitmap that keeps them unique;
+//   snap[2][n]               synchronous rounds: a listed vertex's value at the
+//                            end of its round (zero elsewhere);
+//   flist[2][n], fbit[2][W]  the frontier of a round (rows reading a vertex that
+//                            changed in the round before), for the relaxation count;
+//   touched[n]               vertices that got a value in this outer iteration;
+//   Ctl                      the control block below (one per graph).
 //
-// Every kernel that ends a step of the loop finishes with a last-block epilogue
-// (the last block to retire, found with an atomic ticket) that updates the
-// control block and, when the loop runs as a CUDA graph, sets the graph's
-// conditional WHILE handles.  There are no spin-waits anywhere.
+// One outer iteration: the dense round (every row, k_dense), then push rounds
+// (k_push) until a round changes nothing, then the self-map test and the
+// elimination over the touched vertices (k_check).  Every kernel that ends a
+// step of the loop finishes with a last-block epilogue (the last block to
+// retire, found with an atomic ticket) that updates the control block and, when
+// the loop runs as a CUDA graph, sets the graph's conditional WHILE handles.
 #pragma once
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
@@ -30,17 +36,17 @@ constexpr uint32_t ST_OK = 0, ST_TIMEOUT = 5, ST_LIMIT = 6; // map_status values
 
 struct Ctl {
     // fix-point loop
-    uint32_t qcnt[2];      // |frontier| by round parity
-    uint32_t ccnt;         // changes found in the current round
+    uint32_t lcnt[2];      // |list| by round parity
+    uint32_t fcnt[2];      // |flist| by round parity
+    uint32_t tcnt;         // |touched|
     uint32_t k;            // rounds completed in the current outer iteration
     // outer loop
     uint32_t outer;        // current outer iteration, 1-based (0: none ran)
     uint32_t inner_go;     // fix-point loop continues
     uint32_t outer_go;     // outer loop continues
-    uint32_t status;       // ST_OK or ST_LIMIT
+    uint32_t status;       // ST_OK, ST_LIMIT or ST_TIMEOUT
     uint32_t verdict;      // 1 = accepting cycle
     uint32_t witness;      // smallest self-mapped vertex of the last iteration
-    uint32_t nonzero;      // some map value is defined (eliminated set not empty)
     uint32_t elim;         // accepting vertices eliminated in this outer iteration
     uint32_t nacc;         // accepting vertices left
     uint32_t nacc0;        // accepting vertices at the start
@@ -48,21 +54,31 @@ struct Ctl {
     uint32_t max_outer;    // 0 = no limit
     uint32_t max_inner;    // rounds per outer iteration
     uint32_t hist_cap;     // entries of rounds_hist
+    uint32_t bad;          // set-up: validation failure
     uint64_t m;            // edges
-    uint64_t relax;        // edges examined
+    uint64_t relax;        // edges examined (canonical count of the synchronous schedule)
     uint64_t inner_total;  // rounds summed over outer iterations
     uint32_t *rounds_hist; // rounds of each outer iteration
-    uint32_t *out;         // map export destination (device); NULL: the work buffer chv
-    uint32_t use_graph;    // epilogues set the conditional handles
-    uint32_t pad0;
+    uint32_t *out;         // map export destination (device)
     uint64_t t0;           // %globaltimer at the start of the run (ns)
     uint64_t timeout_ns;   // the loop stops with ST_TIMEOUT past t0 + timeout_ns
-    uint32_t pad[4];
+    uint32_t use_graph;    // epilogues set the conditional handles
+    uint32_t pad[5];
 };
 
 struct Handles {
     unsigned long long inner; // cudaGraphConditionalHandle of the fix-point WHILE node
     unsigned long long outer; // ... of the outer WHILE node
+};
+
+// device pointers of one graph, passed by value to the loop kernels
+struct Dev {
+    uint32_t n, words;
+    const uint32_t *rowptr, *colidx, *rrowptr, *rcol;
+    uint32_t *acc, *mval;
+    uint32_t *list[2], *cbit[2], *snap[2], *flist[2], *fbit[2];
+    uint32_t *touched;
+    Ctl *ctl;
 };
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
@@ -81,12 +97,12 @@ __device__ __forceinline__ unsigned agg_inc(unsigned int *ctr)
     return g.shfl(base, 0) + g.thread_rank();
 }
 
-template <int G>
-__device__ __forceinline__ uint32_t group_max(uint32_t x)
+// set bit v of a bitmap; true for the one caller that flipped it from 0 to 1
+__device__ __forceinline__ bool test_and_set(uint32_t *bits, uint32_t v)
 {
-#pragma unroll
-    for (int off = G / 2; off > 0; off >>= 1) x = max(x, __shfl_xor_sync(0xFFFFFFFFu, x, off));
-    return x;
+    const uint32_t bit = 1u << (v & 31u);
+    if (*(volatile uint32_t *)(bits + (v >> 5)) & bit) return false; // read first: most calls stop here
+    return !(atomicOr(bits + (v >> 5), bit) & bit);
 }
 
 __device__ __forceinline__ unsigned long long warp_sum64(unsigned long long x)
@@ -140,12 +156,13 @@ __device__ __forceinline__ bool timed_out(volatile Ctl *v)
     return global_ns() - v->t0 > v->timeout_ns;
 }
 
-// After round 1 (the dense round) of an outer iteration.
+// After round 1 (the dense round) of an outer iteration: list[1] holds the
+// vertices that got a value, which are also the touched vertices so far.
 __device__ void epilogue_dense(Ctl *c, Handles hd)
 {
     volatile Ctl *v = c;
-    const uint32_t changed = v->ccnt;
-    v->ccnt = 0;
+    const uint32_t changed = v->lcnt[1];
+    v->tcnt = changed;
     v->k = 1;
     v->relax = v->relax + v->m;
     uint32_t go = changed ? 1u : 0u;
@@ -159,14 +176,15 @@ __device__ void epilogue_dense(Ctl *c, Handles hd)
     set_cond(c, hd.inner, go);
 }
 
-// After round k + 1 >= 2 (compute + apply, or one asynchronous sweep).
+// After push round k + 1 >= 2.
 __device__ void epilogue_round(Ctl *c, Handles hd)
 {
     volatile Ctl *v = c;
-    const uint32_t changed = v->ccnt;
-    const uint32_t k = v->k + 1;          // the round just finished
-    v->ccnt = 0;
-    v->qcnt[k & 1] = 0;                   // its frontier is consumed
+    const uint32_t k = v->k + 1;         // the round just finished
+    const uint32_t q = (k - 1) & 1u;     // parity of its input list (round k - 1)
+    const uint32_t changed = v->lcnt[q ^ 1u];
+    v->lcnt[q] = 0;                      // consumed
+    v->fcnt[q] = 0;                      // cleared by this round
     v->k = k;
     uint32_t go = changed ? 1u : 0u;
     if (go && k + 1 > v->max_inner) {
@@ -195,8 +213,8 @@ __device__ void epilogue_check(Ctl *c, Handles hd)
     } else if (v->witness != NONE) {
         v->verdict = 1;
         go = 0;
-    } else if (!v->nonzero) {
-        go = 0; // nothing reaches a remaining accepting vertex
+    } else if (v->tcnt == 0) {
+        go = 0; // no map value is defined: nothing reaches a remaining accepting vertex
     } else {
         const uint32_t left = v->nacc - v->elim;
         v->nacc = left;
@@ -214,9 +232,9 @@ __device__ void epilogue_check(Ctl *c, Handles hd)
     }
     if (go) {
         v->outer = outer + 1;
-        v->qcnt[0] = 0;
-        v->qcnt[1] = 0;
-        v->nonzero = 0;
+        v->lcnt[0] = v->lcnt[1] = 0;
+        v->fcnt[0] = v->fcnt[1] = 0;
+        v->tcnt = 0;
         v->elim = 0;
         v->k = 0;
     }
@@ -226,18 +244,18 @@ __device__ void epilogue_check(Ctl *c, Handles hd)
 }
 
 // Start of a run: fields written by the host (max_outer, max_inner, out,
-// hist_cap, m, nacc0, use_graph) are kept, the rest is reset.
+// hist_cap, m, nacc0, use_graph, timeout_ns) are kept, the rest is reset.
 __global__ void k_run_begin(Ctl *c, Handles hd)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     volatile Ctl *v = c;
-    v->qcnt[0] = v->qcnt[1] = 0;
-    v->ccnt = 0;
+    v->lcnt[0] = v->lcnt[1] = 0;
+    v->fcnt[0] = v->fcnt[1] = 0;
+    v->tcnt = 0;
     v->k = 0;
     v->status = ST_OK;
     v->verdict = 0;
     v->witness = NONE;
-    v->nonzero = 0;
     v->elim = 0;
     v->nacc = v->nacc0;
     v->done = 0;
@@ -252,24 +270,6 @@ __global__ void k_run_begin(Ctl *c, Handles hd)
     set_cond(c, hd.outer, go);
 }
 
-// Mark the readers of u for the next round: set their bit in `bits`; the lane
-// that flips a bit from 0 to 1 appends the reader to `queue`.  The G lanes of a
-// group split u's reader list.
-template <int G>
-__device__ __forceinline__ void mark_readers(uint32_t u, unsigned glane, const uint32_t *__restrict__ rrowptr,
-                                             const uint32_t *__restrict__ rcol, uint32_t *bits, uint32_t *queue,
-                                             unsigned int *qcnt)
-{
-    const uint32_t b = __ldg(rrowptr + u), e = __ldg(rrowptr + u + 1);
-    for (uint32_t i = b + glane; i < e; i += G) {
-        const uint32_t w = __ldg(rcol + i);
-        const uint32_t bit = 1u << (w & 31u);
-        if (*(volatile uint32_t *)(bits + (w >> 5)) & bit) continue; // read first: most re-marks stop here
-        const uint32_t old = atomicOr(bits + (w >> 5), bit);
-        if (!(old & bit)) queue[agg_inc(qcnt)] = w;
-    }
-}
-
 // ------------------------------------------------------------ dense round --
 //
 // Round 1 of an outer iteration relaxes every row from "no value" everywhere,
@@ -282,34 +282,32 @@ __device__ __forceinline__ void mark_readers(uint32_t u, unsigned glane, const u
 // loads (WT_UNROLL per lane, then 4 * WT_UNROLL independent bitmap gathers);
 // an edge that offers a value finds its row by binary search in the slice and
 // does a shared-memory atomicMax; the tile's values are written out coalesced
-// (this also resets the previous iteration's values) and the readers of every
-// row that got a value are marked into the round-2 frontier.
+// (this also resets the previous iteration's values).  Every row that got a
+// value goes to list[1] (with its value in snap[1]) and to the touched list.
 constexpr int DT_THREADS = 256;
 constexpr int WT_WARPS = DT_THREADS / 32;
 constexpr int WT_ROWS = 128;
 constexpr int WT_UNROLL = 4;
 constexpr size_t DT_SMEM = 0; // static shared memory only
 
-__global__ void __launch_bounds__(DT_THREADS, 4) k_dense(uint32_t n, const uint32_t *__restrict__ rowptr,
-                                                         const uint32_t *__restrict__ colidx,
-                                                         const uint32_t *__restrict__ acc,
-                                                         uint32_t *__restrict__ mval,
-                                                         const uint32_t *__restrict__ rrowptr,
-                                                         const uint32_t *__restrict__ rcol, uint32_t *bits,
-                                                         uint32_t *queue, Ctl *ctl, Handles hd)
+__global__ void __launch_bounds__(DT_THREADS, 4) k_dense(const Dev d, Handles hd)
 {
     __shared__ __align__(16) uint32_t s_rp[WT_WARPS][WT_ROWS + 4];
     __shared__ __align__(16) uint32_t s_best[WT_WARPS][WT_ROWS];
+    Ctl *ctl = d.ctl;
     default_stop(ctl, hd.outer);
+    const uint32_t n = d.n;
+    const uint32_t *__restrict__ rowptr = d.rowptr;
+    const uint32_t *__restrict__ colidx = d.colidx;
+    const uint32_t *__restrict__ acc = d.acc;
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
     uint32_t *rp = s_rp[warp], *best = s_best[warp];
     const uint32_t ntiles = (n + WT_ROWS - 1) / WT_ROWS;
     const uint32_t nw = gridDim.x * WT_WARPS;
-    unsigned changed = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) best[lane * 4 + k] = 0;
 
-    // rowptr words r0 + 4 lane .. + 3 of tile t (only the words that exist: <= r0 + rows + 3)
+    // rowptr words r0 + 4 lane .. + 3 of tile t (only words that exist: <= r0 + rows + 3)
     auto load_rp = [&](uint32_t t, uint4 &q, uint32_t &last) {
         const uint32_t r0 = t * WT_ROWS, rows = min((uint32_t)WT_ROWS, n - r0);
         q = lane * 4 <= rows ? __ldg(reinterpret_cast<const uint4 *>(rowptr + r0) + lane) : make_uint4(0, 0, 0, 0);
@@ -364,213 +362,143 @@ __global__ void __launch_bounds__(DT_THREADS, 4) k_dense(uint32_t n, const uint3
         const uint4 b4 = reinterpret_cast<const uint4 *>(best)[lane];
         const uint32_t bs[4] = {b4.x, b4.y, b4.z, b4.w};
         if (lane * 4 + 3 < rows) {
-            reinterpret_cast<uint4 *>(mval + r0)[lane] = b4;
+            reinterpret_cast<uint4 *>(d.mval + r0)[lane] = b4;
         } else {
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                if (lane * 4 + k < rows) mval[r0 + lane * 4 + k] = bs[k];
+                if (lane * 4 + k < rows) d.mval[r0 + lane * 4 + k] = bs[k];
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             if (bs[k] && lane * 4 + k < rows) {
+                const uint32_t v = r0 + lane * 4 + k;
                 best[lane * 4 + k] = 0;
-                changed++;
-                mark_readers<1>(r0 + lane * 4 + k, 0, rrowptr, rcol, bits, queue, &ctl->qcnt[0]);
+                d.snap[1][v] = bs[k];
+                const unsigned slot = agg_inc(&ctl->lcnt[1]);
+                d.list[1][slot] = v;
+                d.touched[slot] = v;
             }
         }
         __syncwarp();
     }
-    changed = __reduce_add_sync(0xFFFFFFFFu, changed);
-    if (lane == 0 && changed) atomicAdd(&ctl->ccnt, changed);
     if (last_block(ctl)) epilogue_dense(ctl, hd);
 }
 
-// ---------------------------------------------------------- frontier rounds --
+// ------------------------------------------------------------ push rounds --
 //
-// A frontier row is handled by a group of G consecutive lanes (G = 1 .. 32,
-// picked from the mean degree): each lane takes every G-th edge of the row and
-// the group reduces with xor-shuffles.  Loops run so that every lane of a warp
-// makes the same number of iterations (full-mask shuffles).  The round number
-// and the frontier size are read from the control block.
-
-// Synchronous round, compute half: for every frontier row v, the new value
-// max(mval[v], max over u in row v of max(u + 1 if u accepting, mval[u])) from
-// the values of the previous round (mval is not written here).  Rows whose value
-// grows are appended to the change list.  Clears the frontier's bitmap.
-template <int G>
-__global__ void __launch_bounds__(256, 6) k_sync_compute(const uint32_t *__restrict__ rowptr,
-                                                      const uint32_t *__restrict__ colidx,
-                                                      const uint32_t *__restrict__ acc,
-                                                      const uint32_t *__restrict__ mval, uint32_t *queue,
-                                                      uint32_t *fbits, uint32_t n, uint32_t words, uint32_t *chv,
-                                                      uint32_t *chval, Ctl *ctl, Handles hd)
+// Round k + 1 >= 2.  In the synchronous schedule a row's new value is
+//   m_{k+1}(w) = max(m_k(w), max over u in row w of offer_k(u)),
+//   offer_k(u) = max(u + 1 if u accepting, m_k(u)).
+// Every row already holds the offers of round k - 1 (round 1 relaxed every row),
+// and only the vertices changed in round k (list[q], q = k & 1) offer anything
+// new, so each of them pushes offer_k(u) -- taken from its snapshot snap[q][u],
+// the value it ended round k with -- to its readers with atomicMax.  A reader
+// that is raised joins list[q ^ 1] (once, via cbit) and raises its own
+// snapshot; a reader raised from "no value" joins the touched list (this
+// happens once per vertex and outer iteration).  Every reader is a frontier
+// row of round k + 1 in the pull formulation: the first time it is met its
+// row length is added to the relaxation count.
+//
+// The asynchronous schedule (SYNC = false) pushes the live value of u instead
+// of its snapshot; values may then travel several edges in one round.
+//
+// A listed vertex is handled by a group of G consecutive lanes that split its
+// reader list; the loop makes every lane of a warp run the same number of
+// iterations.  Also clears the previous round's frontier bitmap.
+template <int G, bool SYNC>
+__global__ void __launch_bounds__(256, 6) k_push(const Dev d, Handles hd)
 {
+    Ctl *ctl = d.ctl;
     default_stop(ctl, hd.inner);
-    const uint32_t p = (*(volatile uint32_t *)&ctl->k + 1) & 1u;
-    const uint32_t nfront = *(volatile uint32_t *)&ctl->qcnt[p];
-    const uint32_t *front = queue + (size_t)p * n;
-    uint32_t *front_bits = fbits + (size_t)p * words;
+    const uint32_t k = *(volatile uint32_t *)&ctl->k; // rounds completed; this is round k + 1
+    const uint32_t q = k & 1u, q2 = q ^ 1u;
+    const uint32_t nl = *(volatile uint32_t *)&ctl->lcnt[q];
+    const uint32_t nf = *(volatile uint32_t *)&ctl->fcnt[q];
+    const uint32_t *__restrict__ list = d.list[q];
+    uint32_t *snap_in = d.snap[q], *snap_out = d.snap[q2];
+    uint32_t *cbit_in = d.cbit[q], *cbit_out = d.cbit[q2];
+    uint32_t *fbit_out = d.fbit[q2], *flist_out = d.flist[q2];
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+    // the previous round's frontier bitmap: every bit in it belongs to flist[q]
+    for (uint64_t i = tid; i < nf; i += nthreads) d.fbit[q][d.flist[q][i] >> 5] = 0;
+
     const unsigned glane = threadIdx.x & (G - 1);
-    const uint64_t groups = (uint64_t)gridDim.x * blockDim.x / G;
-    const uint64_t gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-    const uint64_t warp_first = gid - (lane_id() / G);
+    const int leader = (int)(lane_id() & ~(unsigned)(G - 1));
+    const uint64_t groups = nthreads / G;
+    const uint64_t warp_first = tid / G - (lane_id() / G);
     unsigned long long relax = 0;
-    for (uint64_t base = warp_first; base < nfront; base += groups) {
+    for (uint64_t base = warp_first; base < nl; base += groups) {
         const uint64_t i = base + lane_id() / G;
-        uint32_t best = 0, own = 0, v = 0;
-        if (i < nfront) {
-            v = __ldg(front + i);
-            own = __ldg(mval + v);
-            const uint32_t b = __ldg(rowptr + v), e = __ldg(rowptr + v + 1);
-            if (glane == 0) {
-                relax += e - b;
-                front_bits[v >> 5] = 0; // every bit of this bitmap belongs to this frontier
-            }
-            for (uint32_t j = b + glane; j < e; j += G) {
-                const uint32_t u = __ldg(colidx + j);
-                uint32_t off = __ldg(mval + u);
-                if (acc_bit(acc, u)) off = max(off, u + 1);
-                best = max(best, off);
-            }
+        const bool valid = i < nl;
+        // the group's first lane reads the entry and consumes its snapshot and
+        // de-duplication bit (nothing else reads them in this round)
+        uint32_t u = 0, o = 0, b = 0, e = 0;
+        if (valid && glane == 0) {
+            u = __ldg(list + i);
+            const uint32_t mu = SYNC ? snap_in[u] : *(volatile uint32_t *)(d.mval + u);
+            o = acc_bit(d.acc, u) ? max(mu, u + 1) : mu;
+            b = __ldg(d.rrowptr + u);
+            e = __ldg(d.rrowptr + u + 1);
+            if (SYNC) snap_in[u] = 0;
+            cbit_in[u >> 5] = 0; // every bit in cbit[q] belongs to list[q]
         }
-        best = group_max<G>(best);
-        if (i < nfront && glane == 0 && best > own) {
-            const unsigned slot = agg_inc(&ctl->ccnt);
-            chv[slot] = v;
-            chval[slot] = best;
+        o = __shfl_sync(0xFFFFFFFFu, o, leader);
+        b = __shfl_sync(0xFFFFFFFFu, b, leader);
+        e = __shfl_sync(0xFFFFFFFFu, e, leader);
+        if (!valid) continue;
+        for (uint32_t j = b + glane; j < e; j += G) {
+            const uint32_t w = __ldg(d.rcol + j);
+            if (test_and_set(fbit_out, w)) {
+                flist_out[agg_inc(&ctl->fcnt[q2])] = w;
+                relax += __ldg(d.rowptr + w + 1) - __ldg(d.rowptr + w);
+            }
+            const uint32_t old = atomicMax(d.mval + w, o);
+            if (o > old) {
+                if (SYNC) atomicMax(snap_out + w, o);
+                if (old == 0) d.touched[agg_inc(&ctl->tcnt)] = w;
+                if (test_and_set(cbit_out, w)) d.list[q2][agg_inc(&ctl->lcnt[q2])] = w;
+            }
         }
     }
     relax = warp_sum64(relax);
     if (lane_id() == 0 && relax) atomicAdd((unsigned long long *)&ctl->relax, relax);
-}
-
-// Synchronous round, apply half: write the new values and mark the readers of
-// every changed vertex into the frontier of the next round.
-template <int G>
-__global__ void __launch_bounds__(256, 8) k_sync_apply(const uint32_t *__restrict__ chv,
-                                                    const uint32_t *__restrict__ chval, uint32_t *mval,
-                                                    const uint32_t *__restrict__ rrowptr,
-                                                    const uint32_t *__restrict__ rcol, uint32_t *queue, uint32_t *fbits,
-                                                    uint32_t n, uint32_t words, Ctl *ctl, Handles hd)
-{
-    const uint32_t np = *(volatile uint32_t *)&ctl->k & 1u; // parity of the round after this one
-    const uint32_t nch = *(volatile uint32_t *)&ctl->ccnt;
-    uint32_t *next = queue + (size_t)np * n;
-    uint32_t *nbits = fbits + (size_t)np * words;
-    const unsigned glane = threadIdx.x & (G - 1);
-    const uint64_t groups = (uint64_t)gridDim.x * blockDim.x / G;
-    const uint64_t gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-    const uint64_t warp_first = gid - (lane_id() / G);
-    for (uint64_t base = warp_first; base < nch; base += groups) {
-        const uint64_t i = base + lane_id() / G;
-        if (i < nch) {
-            const uint32_t v = chv[i];
-            if (glane == 0) mval[v] = chval[i];
-            mark_readers<G>(v, glane, rrowptr, rcol, nbits, next, &ctl->qcnt[np]);
-        }
-    }
-    if (last_block(ctl)) epilogue_round(ctl, hd);
-}
-
-// Asynchronous sweep: like a synchronous round, but a new value is written at
-// once (values only grow, so a racing reader sees the old or the new value and
-// the fix-point is the same), and its readers are marked at once.
-template <int G>
-__global__ void __launch_bounds__(256, 6) k_async_sweep(const uint32_t *__restrict__ rowptr,
-                                                     const uint32_t *__restrict__ colidx,
-                                                     const uint32_t *__restrict__ acc, uint32_t *mval,
-                                                     const uint32_t *__restrict__ rrowptr,
-                                                     const uint32_t *__restrict__ rcol, uint32_t *queue,
-                                                     uint32_t *fbits, uint32_t n, uint32_t words, Ctl *ctl,
-                                                     Handles hd)
-{
-    default_stop(ctl, hd.inner);
-    const uint32_t p = (*(volatile uint32_t *)&ctl->k + 1) & 1u, np = p ^ 1u;
-    const uint32_t nfront = *(volatile uint32_t *)&ctl->qcnt[p];
-    const uint32_t *front = queue + (size_t)p * n;
-    uint32_t *front_bits = fbits + (size_t)p * words;
-    uint32_t *next = queue + (size_t)np * n;
-    uint32_t *nbits = fbits + (size_t)np * words;
-    const unsigned glane = threadIdx.x & (G - 1);
-    const uint64_t groups = (uint64_t)gridDim.x * blockDim.x / G;
-    const uint64_t gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-    const uint64_t warp_first = gid - (lane_id() / G);
-    unsigned long long relax = 0;
-    unsigned changed = 0;
-    for (uint64_t base = warp_first; base < nfront; base += groups) {
-        const uint64_t i = base + lane_id() / G;
-        uint32_t best = 0, own = 0, v = 0;
-        if (i < nfront) {
-            v = __ldg(front + i);
-            own = *(volatile uint32_t *)(mval + v);
-            const uint32_t b = __ldg(rowptr + v), e = __ldg(rowptr + v + 1);
-            if (glane == 0) {
-                relax += e - b;
-                front_bits[v >> 5] = 0;
-            }
-            for (uint32_t j = b + glane; j < e; j += G) {
-                const uint32_t u = __ldg(colidx + j);
-                uint32_t off = *(volatile uint32_t *)(mval + u);
-                if (acc_bit(acc, u)) off = max(off, u + 1);
-                best = max(best, off);
-            }
-        }
-        best = group_max<G>(best);
-        if (i < nfront && best > own) {
-            if (glane == 0) {
-                atomicMax(mval + v, best);
-                changed++;
-            }
-            mark_readers<G>(v, glane, rrowptr, rcol, nbits, next, &ctl->qcnt[np]);
-        }
-    }
-    relax = warp_sum64(relax);
-    changed = __reduce_add_sync(0xFFFFFFFFu, changed);
-    if (lane_id() == 0) {
-        if (relax) atomicAdd((unsigned long long *)&ctl->relax, relax);
-        if (changed) atomicAdd(&ctl->ccnt, changed);
-    }
     if (last_block(ctl)) epilogue_round(ctl, hd);
 }
 
 // ------------------------------------------------- self-map test, elimination --
 //
-// One pass over the map vector (Section 2): witness = smallest v with
-// map(v) = v; every defined map value u is removed from the accepting set
-// (exact count of removals); nonzero = "some value is defined".  The map vector
-// is left intact (the next dense round overwrites it).  128-bit loads, four
-// words per thread per step.
-__global__ void __launch_bounds__(256) k_check_eliminate(uint32_t n, const uint32_t *__restrict__ mval,
-                                                         uint32_t *acc, Ctl *ctl, Handles hd)
+// Over the touched vertices (exactly the vertices with a defined map value),
+// Section 2: witness = smallest v with map(v) = v; every map value u is removed
+// from the accepting set (exact count of removals).  Also clears what is left
+// of the last round's frontier bitmap.  The map vector is left intact (the next
+// dense round overwrites it).
+__global__ void __launch_bounds__(256) k_check(const Dev d, Handles hd)
 {
-    const uint32_t n4 = (n + 3) / 4;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    unsigned elim = 0, any = 0;
+    Ctl *ctl = d.ctl;
+    const uint32_t nt = *(volatile uint32_t *)&ctl->tcnt;
+    const uint32_t nf0 = *(volatile uint32_t *)&ctl->fcnt[0], nf1 = *(volatile uint32_t *)&ctl->fcnt[1];
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = tid; i < nf0; i += nthreads) d.fbit[0][d.flist[0][i] >> 5] = 0;
+    for (uint64_t i = tid; i < nf1; i += nthreads) d.fbit[1][d.flist[1][i] >> 5] = 0;
+    unsigned elim = 0;
     uint32_t wit = NONE;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
-        const uint4 x4 = __ldg(reinterpret_cast<const uint4 *>(mval) + i);
-        const uint32_t xs[4] = {x4.x, x4.y, x4.z, x4.w};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const uint32_t v = i * 4 + q;
-            const uint32_t x = xs[q];
-            if (v >= n || !x) continue;
-            any = 1;
-            const uint32_t u = x - 1;
-            if (u == v) wit = min(wit, u);
-            const uint32_t bit = 1u << (u & 31u);
-            if (*(volatile uint32_t *)(acc + (u >> 5)) & bit) {
-                const uint32_t old = atomicAnd(acc + (u >> 5), ~bit);
-                elim += (old & bit) ? 1u : 0u;
-            }
+    for (uint64_t i = tid; i < nt; i += nthreads) {
+        const uint32_t v = __ldg(d.touched + i);
+        const uint32_t x = __ldg(d.mval + v);
+        const uint32_t u = x - 1; // x != 0 for a touched vertex
+        if (u == v) wit = min(wit, u);
+        const uint32_t bit = 1u << (u & 31u);
+        if (*(volatile uint32_t *)(d.acc + (u >> 5)) & bit) {
+            const uint32_t old = atomicAnd(d.acc + (u >> 5), ~bit);
+            elim += (old & bit) ? 1u : 0u;
         }
     }
     elim = __reduce_add_sync(0xFFFFFFFFu, elim);
-    any = __reduce_or_sync(0xFFFFFFFFu, any);
     wit = __reduce_min_sync(0xFFFFFFFFu, wit);
     if (lane_id() == 0) {
         if (elim) atomicAdd(&ctl->elim, elim);
-        if (any) atomicOr(&ctl->nonzero, 1u);
         if (wit != NONE) atomicMin(&ctl->witness, wit);
     }
     if (last_block(ctl)) epilogue_check(ctl, hd);
