@@ -208,11 +208,8 @@ int launch_dense(map_graph *g, cudaStream_t s, mapk::Handles hd)
 int launch_round(map_graph *g, cudaStream_t s, bool sync_sched, mapk::Handles hd)
 {
     const mapk::Dev d = dev_of(g);
-    if (sync_sched) {
-        DISPATCH_G(g->G, (mapk::k_push<GG, true><<<g->sparse_grid, 256, 0, s>>>(d, hd)));
-    } else {
-        DISPATCH_G(g->G, (mapk::k_push<GG, false><<<g->sparse_grid, 256, 0, s>>>(d, hd)));
-    }
+    if (sync_sched) mapk::k_push<true><<<g->sparse_grid, 256, 0, s>>>(d, hd);
+    else mapk::k_push<false><<<g->sparse_grid, 256, 0, s>>>(d, hd);
     CK(cudaGetLastError());
     return MAP_OK;
 }
@@ -384,7 +381,7 @@ int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const
     if (occ <= 0) occ = 1;
     const uint64_t ntiles = ((uint64_t)n + mapk::WT_ROWS - 1) / mapk::WT_ROWS;
     g->dense_grid = (int)std::min<uint64_t>((ntiles + mapk::WT_WARPS - 1) / mapk::WT_WARPS, (uint64_t)g->sms * occ);
-    g->sparse_grid = (int)std::min<uint64_t>(((uint64_t)n * g->G + 255) / 256 + 1, (uint64_t)g->sms * 6);
+    g->sparse_grid = (int)std::min<uint64_t>(((uint64_t)n + 255) / 256, (uint64_t)g->sms * 6);
     g->check_grid = (int)std::min<uint64_t>(((uint64_t)n + 255) / 256, (uint64_t)g->sms * 4);
     g->hist_cap = 1u << 16;
 

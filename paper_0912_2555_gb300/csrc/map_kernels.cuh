@@ -370,13 +370,23 @@ __global__ void __launch_bounds__(DT_THREADS, 4) k_dense(const Dev d, Handles hd
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            if (bs[k] && lane * 4 + k < rows) {
-                const uint32_t v = r0 + lane * 4 + k;
+            const bool got = bs[k] && lane * 4 + k < rows;
+            const uint32_t v = r0 + lane * 4 + k;
+            if (got) {
                 best[lane * 4 + k] = 0;
                 d.snap[1][v] = bs[k];
-                const unsigned slot = agg_inc(&ctl->lcnt[1]);
-                d.list[1][slot] = v;
-                d.touched[slot] = v;
+            }
+            // one reservation per warp, shared by list[1] and the touched list
+            const unsigned mask = __ballot_sync(0xFFFFFFFFu, got);
+            if (mask) {
+                const unsigned leader = __ffs(mask) - 1;
+                unsigned slot = 0;
+                if (lane == leader) slot = atomicAdd(&ctl->lcnt[1], (unsigned)__popc(mask));
+                slot = __shfl_sync(0xFFFFFFFFu, slot, leader) + __popc(mask & ((1u << lane) - 1u));
+                if (got) {
+                    d.list[1][slot] = v;
+                    d.touched[slot] = v;
+                }
             }
         }
         __syncwarp();
@@ -395,17 +405,44 @@ __global__ void __launch_bounds__(DT_THREADS, 4) k_dense(const Dev d, Handles hd
 // the value it ended round k with -- to its readers with atomicMax.  A reader
 // that is raised joins list[q ^ 1] (once, via cbit) and raises its own
 // snapshot; a reader raised from "no value" joins the touched list (this
-// happens once per vertex and outer iteration).  Every reader is a frontier
-// row of round k + 1 in the pull formulation: the first time it is met its
-// row length is added to the relaxation count.
+// happens once per vertex and outer iteration).  Every reader is a frontier row
+// of round k + 1 in the pull formulation; the frontier is kept (fbit, flist) and
+// its row lengths are added to the relaxation count when it is cleared, at the
+// start of the next round (or by k_check after the last one).
 //
 // The asynchronous schedule (SYNC = false) pushes the live value of u instead
 // of its snapshot; values may then travel several edges in one round.
 //
-// A listed vertex is handled by a group of G consecutive lanes that split its
-// reader list; the loop makes every lane of a warp run the same number of
-// iterations.  Also clears the previous round's frontier bitmap.
-template <int G, bool SYNC>
+// One thread per listed vertex; the reader loop runs warp-uniformly so that the
+// appends are aggregated with one atomic per warp and list.
+
+// append w (where flag) to arr, reserving space with one atomic per warp; all lanes call it
+__device__ __forceinline__ void warp_append(bool flag, uint32_t w, uint32_t *arr, unsigned int *ctr)
+{
+    const unsigned mask = __ballot_sync(0xFFFFFFFFu, flag);
+    if (!mask) return;
+    const unsigned lane = lane_id(), leader = __ffs(mask) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(ctr, (unsigned)__popc(mask));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    if (flag) arr[base + __popc(mask & ((1u << lane) - 1u))] = w;
+}
+
+// clear a frontier bitmap from its list and return the row lengths of the listed rows
+__device__ __forceinline__ unsigned long long clear_frontier(const uint32_t *__restrict__ flist, uint32_t nf,
+                                                             uint32_t *fbit, const uint32_t *__restrict__ rowptr)
+{
+    unsigned long long relax = 0;
+    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += nthreads) {
+        const uint32_t w = __ldg(flist + i);
+        fbit[w >> 5] = 0; // every bit in this bitmap belongs to this list
+        relax += __ldg(rowptr + w + 1) - __ldg(rowptr + w);
+    }
+    return relax;
+}
+
+template <bool SYNC>
 __global__ void __launch_bounds__(256, 6) k_push(const Dev d, Handles hd)
 {
     Ctl *ctl = d.ctl;
@@ -417,48 +454,44 @@ __global__ void __launch_bounds__(256, 6) k_push(const Dev d, Handles hd)
     const uint32_t *__restrict__ list = d.list[q];
     uint32_t *snap_in = d.snap[q], *snap_out = d.snap[q2];
     uint32_t *cbit_in = d.cbit[q], *cbit_out = d.cbit[q2];
-    uint32_t *fbit_out = d.fbit[q2], *flist_out = d.flist[q2];
-    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
-    // the previous round's frontier bitmap: every bit in it belongs to flist[q]
-    for (uint64_t i = tid; i < nf; i += nthreads) d.fbit[q][d.flist[q][i] >> 5] = 0;
+    uint32_t *fbit_out = d.fbit[q2];
+    // round k's frontier: clear its bitmap, count its relaxations
+    unsigned long long relax = clear_frontier(d.flist[q], nf, d.fbit[q], d.rowptr);
 
-    const unsigned glane = threadIdx.x & (G - 1);
-    const int leader = (int)(lane_id() & ~(unsigned)(G - 1));
-    const uint64_t groups = nthreads / G;
-    const uint64_t warp_first = tid / G - (lane_id() / G);
-    unsigned long long relax = 0;
-    for (uint64_t base = warp_first; base < nl; base += groups) {
-        const uint64_t i = base + lane_id() / G;
+    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t warp_first = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+    for (uint64_t base = warp_first; base < nl; base += nthreads) {
+        const uint64_t i = base + lane_id();
         const bool valid = i < nl;
-        // the group's first lane reads the entry and consumes its snapshot and
-        // de-duplication bit (nothing else reads them in this round)
-        uint32_t u = 0, o = 0, b = 0, e = 0;
-        if (valid && glane == 0) {
-            u = __ldg(list + i);
+        uint32_t o = 0, j = 0, e = 0;
+        if (valid) {
+            const uint32_t u = __ldg(list + i);
             const uint32_t mu = SYNC ? snap_in[u] : *(volatile uint32_t *)(d.mval + u);
             o = acc_bit(d.acc, u) ? max(mu, u + 1) : mu;
-            b = __ldg(d.rrowptr + u);
+            j = __ldg(d.rrowptr + u);
             e = __ldg(d.rrowptr + u + 1);
-            if (SYNC) snap_in[u] = 0;
-            cbit_in[u >> 5] = 0; // every bit in cbit[q] belongs to list[q]
+            if (SYNC) snap_in[u] = 0; // consumed (nothing else reads it in this round)
+            cbit_in[u >> 5] = 0;      // every bit in cbit[q] belongs to list[q]
         }
-        o = __shfl_sync(0xFFFFFFFFu, o, leader);
-        b = __shfl_sync(0xFFFFFFFFu, b, leader);
-        e = __shfl_sync(0xFFFFFFFFu, e, leader);
-        if (!valid) continue;
-        for (uint32_t j = b + glane; j < e; j += G) {
-            const uint32_t w = __ldg(d.rcol + j);
-            if (test_and_set(fbit_out, w)) {
-                flist_out[agg_inc(&ctl->fcnt[q2])] = w;
-                relax += __ldg(d.rowptr + w + 1) - __ldg(d.rowptr + w);
+        while (__any_sync(0xFFFFFFFFu, j < e)) {
+            const bool act = j < e;
+            uint32_t w = 0, bit = 0, fold = 0, mold = 0xFFFFFFFFu;
+            if (act) {
+                w = __ldg(d.rcol + j);
+                bit = 1u << (w & 31u);
+                fold = atomicOr(fbit_out + (w >> 5), bit); // both atomics in flight together
+                mold = atomicMax(d.mval + w, o);
             }
-            const uint32_t old = atomicMax(d.mval + w, o);
-            if (o > old) {
+            const bool raised = act && o > mold;
+            uint32_t cold = bit;
+            if (raised) {
                 if (SYNC) atomicMax(snap_out + w, o);
-                if (old == 0) d.touched[agg_inc(&ctl->tcnt)] = w;
-                if (test_and_set(cbit_out, w)) d.list[q2][agg_inc(&ctl->lcnt[q2])] = w;
+                cold = atomicOr(cbit_out + (w >> 5), bit);
             }
+            warp_append(act && !(fold & bit), w, d.flist[q2], &ctl->fcnt[q2]);
+            warp_append(raised && !(cold & bit), w, d.list[q2], &ctl->lcnt[q2]);
+            warp_append(raised && mold == 0, w, d.touched, &ctl->tcnt);
+            ++j;
         }
     }
     relax = warp_sum64(relax);
@@ -480,8 +513,9 @@ __global__ void __launch_bounds__(256) k_check(const Dev d, Handles hd)
     const uint32_t nf0 = *(volatile uint32_t *)&ctl->fcnt[0], nf1 = *(volatile uint32_t *)&ctl->fcnt[1];
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = tid; i < nf0; i += nthreads) d.fbit[0][d.flist[0][i] >> 5] = 0;
-    for (uint64_t i = tid; i < nf1; i += nthreads) d.fbit[1][d.flist[1][i] >> 5] = 0;
+    // the last round's frontier: clear its bitmap, count its relaxations
+    unsigned long long relax = clear_frontier(d.flist[0], nf0, d.fbit[0], d.rowptr);
+    relax += clear_frontier(d.flist[1], nf1, d.fbit[1], d.rowptr);
     unsigned elim = 0;
     uint32_t wit = NONE;
     for (uint64_t i = tid; i < nt; i += nthreads) {
@@ -497,9 +531,11 @@ __global__ void __launch_bounds__(256) k_check(const Dev d, Handles hd)
     }
     elim = __reduce_add_sync(0xFFFFFFFFu, elim);
     wit = __reduce_min_sync(0xFFFFFFFFu, wit);
+    relax = warp_sum64(relax);
     if (lane_id() == 0) {
         if (elim) atomicAdd(&ctl->elim, elim);
         if (wit != NONE) atomicMin(&ctl->witness, wit);
+        if (relax) atomicAdd((unsigned long long *)&ctl->relax, relax);
     }
     if (last_block(ctl)) epilogue_check(ctl, hd);
 }
