@@ -112,6 +112,77 @@ __device__ __forceinline__ unsigned long long warp_sum64(unsigned long long x)
     return x;
 }
 
+// ---- append staging -------------------------------------------------------
+//
+// Kernels append vertex ids to global lists.  Instead of one atomic on the
+// list's counter per append (or per warp and append step), each warp stages its
+// appends in shared memory and the block reserves global space once per list
+// when it finishes (a warp whose buffer fills up flushes it on its own).
+constexpr int SB_ENTRIES = 128; // staged entries per warp and list
+
+template <int NL>
+struct Stage {
+    uint32_t *buf;   // this warp's NL x SB_ENTRIES shared buffer
+    uint32_t cnt[NL]; // warp-uniform fill counts
+};
+
+// append w to list l where flag holds; every lane of the warp calls it.
+// dst[l][0..1]: global arrays the entry goes to (dst[l][1] may be NULL), ctr[l]: their counter.
+template <int NL>
+__device__ __forceinline__ void stage_append(Stage<NL> &st, int l, bool flag, uint32_t w, uint32_t *const (*dst)[2],
+                                             unsigned int *const *ctr)
+{
+    const unsigned mask = __ballot_sync(0xFFFFFFFFu, flag);
+    if (!mask) return;
+    const unsigned lane = lane_id();
+    uint32_t *b = st.buf + l * SB_ENTRIES;
+    if (st.cnt[l] + 32 > (uint32_t)SB_ENTRIES) { // full: this warp flushes on its own
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(ctr[l], st.cnt[l]);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        __syncwarp();
+        for (uint32_t i = lane; i < st.cnt[l]; i += 32) {
+            dst[l][0][base + i] = b[i];
+            if (dst[l][1]) dst[l][1][base + i] = b[i];
+        }
+        __syncwarp();
+        st.cnt[l] = 0;
+    }
+    if (flag) b[st.cnt[l] + __popc(mask & ((1u << lane) - 1u))] = w;
+    st.cnt[l] += __popc(mask);
+    __syncwarp();
+}
+
+// end of a kernel: every thread of the block calls it (it contains __syncthreads);
+// one global atomic per list and block.  s_cnt: shared [warps][NL], s_base: shared [NL].
+template <int NL>
+__device__ __forceinline__ void stage_flush_block(Stage<NL> &st, uint32_t (*s_cnt)[NL], uint32_t *s_base,
+                                                  uint32_t *const (*dst)[2], unsigned int *const *ctr)
+{
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    if (lane == 0) {
+#pragma unroll
+        for (int l = 0; l < NL; ++l) s_cnt[warp][l] = st.cnt[l];
+    }
+    __syncthreads();
+    if (threadIdx.x < (unsigned)NL) {
+        uint32_t tot = 0;
+        for (unsigned w = 0; w < nwarps; ++w) tot += s_cnt[w][threadIdx.x];
+        s_base[threadIdx.x] = tot ? atomicAdd(ctr[threadIdx.x], tot) : 0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        uint32_t off = s_base[l];
+        for (unsigned w = 0; w < warp; ++w) off += s_cnt[w][l];
+        const uint32_t *b = st.buf + l * SB_ENTRIES;
+        for (uint32_t i = lane; i < st.cnt[l]; i += 32) {
+            dst[l][0][off + i] = b[i];
+            if (dst[l][1]) dst[l][1][off + i] = b[i];
+        }
+    }
+}
+
 // True in exactly one thread of the grid: thread 0 of the last block to get here.
 // Every thread of every block must call it (it contains __syncthreads).
 __device__ __forceinline__ bool last_block(Ctl *ctl)
@@ -294,7 +365,15 @@ __global__ void __launch_bounds__(DT_THREADS, 4) k_dense(const Dev d, Handles hd
 {
     __shared__ __align__(16) uint32_t s_rp[WT_WARPS][WT_ROWS + 4];
     __shared__ __align__(16) uint32_t s_best[WT_WARPS][WT_ROWS];
+    __shared__ uint32_t s_stage[WT_WARPS][SB_ENTRIES];
+    __shared__ uint32_t s_cnt[WT_WARPS][1], s_base[1];
     Ctl *ctl = d.ctl;
+    // the rows that get a value go to list[1] and to the touched list
+    uint32_t *const dst[1][2] = {{d.list[1], d.touched}};
+    unsigned int *const ctr[1] = {&ctl->lcnt[1]};
+    Stage<1> st;
+    st.buf = s_stage[threadIdx.x >> 5];
+    st.cnt[0] = 0;
     default_stop(ctl, hd.outer);
     const uint32_t n = d.n;
     const uint32_t *__restrict__ rowptr = d.rowptr;
@@ -376,21 +455,11 @@ __global__ void __launch_bounds__(DT_THREADS, 4) k_dense(const Dev d, Handles hd
                 best[lane * 4 + k] = 0;
                 d.snap[1][v] = bs[k];
             }
-            // one reservation per warp, shared by list[1] and the touched list
-            const unsigned mask = __ballot_sync(0xFFFFFFFFu, got);
-            if (mask) {
-                const unsigned leader = __ffs(mask) - 1;
-                unsigned slot = 0;
-                if (lane == leader) slot = atomicAdd(&ctl->lcnt[1], (unsigned)__popc(mask));
-                slot = __shfl_sync(0xFFFFFFFFu, slot, leader) + __popc(mask & ((1u << lane) - 1u));
-                if (got) {
-                    d.list[1][slot] = v;
-                    d.touched[slot] = v;
-                }
-            }
+            stage_append<1>(st, 0, got, v, dst, ctr);
         }
         __syncwarp();
     }
+    stage_flush_block<1>(st, s_cnt, s_base, dst, ctr);
     if (last_block(ctl)) epilogue_dense(ctl, hd);
 }
 
@@ -442,9 +511,22 @@ __device__ __forceinline__ unsigned long long clear_frontier(const uint32_t *__r
     return relax;
 }
 
-template <bool SYNC>
-__global__ void __launch_bounds__(256, 6) k_push(const Dev d, Handles hd)
+// exclusive-free inclusive warp scan
+__device__ __forceinline__ uint32_t warp_inclusive_scan(uint32_t x)
 {
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, x, off);
+        if (lane_id() >= (unsigned)off) x += t;
+    }
+    return x;
+}
+
+template <bool SYNC>
+__global__ void __launch_bounds__(256, 5) k_push(const Dev d, Handles hd)
+{
+    __shared__ uint32_t s_stage[8][3 * SB_ENTRIES];
+    __shared__ uint32_t s_cnt[8][3], s_base[3];
     Ctl *ctl = d.ctl;
     default_stop(ctl, hd.inner);
     const uint32_t k = *(volatile uint32_t *)&ctl->k; // rounds completed; this is round k + 1
@@ -455,47 +537,67 @@ __global__ void __launch_bounds__(256, 6) k_push(const Dev d, Handles hd)
     uint32_t *snap_in = d.snap[q], *snap_out = d.snap[q2];
     uint32_t *cbit_in = d.cbit[q], *cbit_out = d.cbit[q2];
     uint32_t *fbit_out = d.fbit[q2];
+    // appends: 0 = this round's frontier, 1 = changed vertices, 2 = newly touched vertices
+    uint32_t *const dst[3][2] = {{d.flist[q2], nullptr}, {d.list[q2], nullptr}, {d.touched, nullptr}};
+    unsigned int *const ctr[3] = {&ctl->fcnt[q2], &ctl->lcnt[q2], &ctl->tcnt};
+    Stage<3> st;
+    st.buf = s_stage[threadIdx.x >> 5];
+    st.cnt[0] = st.cnt[1] = st.cnt[2] = 0;
     // round k's frontier: clear its bitmap, count its relaxations
     unsigned long long relax = clear_frontier(d.flist[q], nf, d.fbit[q], d.rowptr);
 
+    const unsigned lane = lane_id();
     const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t warp_first = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
     for (uint64_t base = warp_first; base < nl; base += nthreads) {
-        const uint64_t i = base + lane_id();
-        const bool valid = i < nl;
-        uint32_t o = 0, j = 0, e = 0;
-        if (valid) {
+        // 32 listed vertices per warp: each lane reads one and consumes its
+        // snapshot and de-duplication bit (nothing else reads them in this round)
+        const uint64_t i = base + lane;
+        uint32_t o = 0, b = 0, len = 0;
+        if (i < nl) {
             const uint32_t u = __ldg(list + i);
             const uint32_t mu = SYNC ? snap_in[u] : *(volatile uint32_t *)(d.mval + u);
             o = acc_bit(d.acc, u) ? max(mu, u + 1) : mu;
-            j = __ldg(d.rrowptr + u);
-            e = __ldg(d.rrowptr + u + 1);
-            if (SYNC) snap_in[u] = 0; // consumed (nothing else reads it in this round)
-            cbit_in[u >> 5] = 0;      // every bit in cbit[q] belongs to list[q]
+            b = __ldg(d.rrowptr + u);
+            len = __ldg(d.rrowptr + u + 1) - b;
+            if (SYNC) snap_in[u] = 0;
+            cbit_in[u >> 5] = 0; // every bit in cbit[q] belongs to list[q]
         }
-        while (__any_sync(0xFFFFFFFFu, j < e)) {
-            const bool act = j < e;
+        // their (vertex, reader) pairs, spread evenly over the lanes
+        const uint32_t incl = warp_inclusive_scan(len);
+        const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        const uint32_t excl = incl - len;
+        for (uint32_t p0 = 0; p0 < total; p0 += 32) {
+            const uint32_t p = p0 + lane;
+            uint32_t src = 0; // the lane whose list entry owns pair p: the number of lanes with incl <= p
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (__shfl_sync(0xFFFFFFFFu, incl, src + step - 1) <= p) src += step;
+            const uint32_t ob = __shfl_sync(0xFFFFFFFFu, o, src);
+            const uint32_t bb = __shfl_sync(0xFFFFFFFFu, b, src);
+            const uint32_t eb = __shfl_sync(0xFFFFFFFFu, excl, src);
+            const bool act = p < total;
             uint32_t w = 0, bit = 0, fold = 0, mold = 0xFFFFFFFFu;
             if (act) {
-                w = __ldg(d.rcol + j);
+                w = __ldg(d.rcol + bb + (p - eb));
                 bit = 1u << (w & 31u);
                 fold = atomicOr(fbit_out + (w >> 5), bit); // both atomics in flight together
-                mold = atomicMax(d.mval + w, o);
+                mold = atomicMax(d.mval + w, ob);
             }
-            const bool raised = act && o > mold;
+            const bool raised = act && ob > mold;
             uint32_t cold = bit;
             if (raised) {
-                if (SYNC) atomicMax(snap_out + w, o);
+                if (SYNC) atomicMax(snap_out + w, ob);
                 cold = atomicOr(cbit_out + (w >> 5), bit);
             }
-            warp_append(act && !(fold & bit), w, d.flist[q2], &ctl->fcnt[q2]);
-            warp_append(raised && !(cold & bit), w, d.list[q2], &ctl->lcnt[q2]);
-            warp_append(raised && mold == 0, w, d.touched, &ctl->tcnt);
-            ++j;
+            stage_append<3>(st, 0, act && !(fold & bit), w, dst, ctr);
+            stage_append<3>(st, 1, raised && !(cold & bit), w, dst, ctr);
+            stage_append<3>(st, 2, raised && mold == 0, w, dst, ctr);
         }
     }
+    stage_flush_block<3>(st, s_cnt, s_base, dst, ctr);
     relax = warp_sum64(relax);
-    if (lane_id() == 0 && relax) atomicAdd((unsigned long long *)&ctl->relax, relax);
+    if (lane == 0 && relax) atomicAdd((unsigned long long *)&ctl->relax, relax);
     if (last_block(ctl)) epilogue_round(ctl, hd);
 }
 
