@@ -83,9 +83,8 @@ struct map_graph {
     uint32_t *rowptr = nullptr, *colidx = nullptr, *rrowptr = nullptr, *rcol = nullptr;
     uint32_t *acc0 = nullptr, *acc = nullptr, *mval = nullptr;
     uint32_t *list = nullptr;  // 2n: vertices changed in a round, by parity
-    uint32_t *snap = nullptr;  // 2n: their values at the end of the round
     uint32_t *flist = nullptr; // 2n: frontier rows of a round, by parity
-    uint32_t *bits = nullptr;  // 4W: cbit[2], fbit[2]
+    uint4 *rec = nullptr;      // n: per-vertex round state (snapshots, list and frontier flags)
     uint32_t *touched = nullptr, *xbuf = nullptr;
     bool dirty = false; // a run stopped early: per-round state may be stale
     uint32_t *hist = nullptr; // rounds per outer iteration
@@ -111,8 +110,8 @@ void free_graph(map_graph *g)
         if (g->exec[i]) cudaGraphExecDestroy(g->exec[i]);
         if (g->graph[i]) cudaGraphDestroy(g->graph[i]);
     }
-    void *dev[] = {g->rowptr, g->colidx, g->rrowptr, g->rcol,    g->acc0, g->acc, g->mval, g->list,
-                   g->snap,   g->flist,  g->bits,    g->touched, g->xbuf, g->hist, g->ctl};
+    void *dev[] = {g->rowptr, g->colidx, g->rrowptr, g->rcol, g->acc0, g->acc,  g->mval,
+                   g->list,   g->flist,  g->rec,     g->touched, g->xbuf, g->hist, g->ctl};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (g->h_ctl) cudaFreeHost(g->h_ctl);
@@ -185,14 +184,12 @@ mapk::Dev dev_of(const map_graph *g)
     d.rcol = g->rcol;
     d.acc = g->acc;
     d.mval = g->mval;
-    const size_t n = g->n, W = g->words;
+    const size_t n = g->n;
     for (int p = 0; p < 2; ++p) {
         d.list[p] = g->list + p * n;
-        d.snap[p] = g->snap + p * n;
         d.flist[p] = g->flist + p * n;
-        d.cbit[p] = g->bits + p * W;
-        d.fbit[p] = g->bits + (2 + p) * W;
     }
+    d.rec = g->rec;
     d.touched = g->touched;
     d.ctl = g->ctl;
     return d;
@@ -221,11 +218,11 @@ int launch_check(map_graph *g, cudaStream_t s, mapk::Handles hd)
     return MAP_OK;
 }
 
-// per-run reset: the accepting set, the bitmaps (and the snapshots after a run that stopped early)
+// per-run reset: the accepting set (the round state is clean after every run
+// that completes; map_run clears it after one that stopped early)
 int launch_reset(map_graph *g, cudaStream_t s)
 {
     CK(cudaMemcpyAsync(g->acc, g->acc0, (size_t)g->words * 4, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemsetAsync(g->bits, 0, (size_t)4 * g->words * 4, s));
     return MAP_OK;
 }
 
@@ -394,8 +391,8 @@ int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const
     if ((rc = alloc(&g->rowptr, (uint64_t)n + 1)) || (rc = alloc(&g->colidx, m)) ||
         (rc = alloc(&g->rrowptr, (uint64_t)n + 1)) || (rc = alloc(&g->rcol, m)) || (rc = alloc(&g->acc0, W)) ||
         (rc = alloc(&g->acc, W)) || (rc = alloc(&g->mval, n)) || (rc = alloc(&g->list, 2 * (uint64_t)n)) ||
-        (rc = alloc(&g->snap, 2 * (uint64_t)n)) || (rc = alloc(&g->flist, 2 * (uint64_t)n)) ||
-        (rc = alloc(&g->bits, 4 * W)) || (rc = alloc(&g->touched, n)) || (rc = alloc(&g->xbuf, n)) ||
+        (rc = alloc(&g->flist, 2 * (uint64_t)n)) || (rc = alloc((uint32_t **)&g->rec, 4 * (uint64_t)n)) ||
+        (rc = alloc(&g->touched, n)) || (rc = alloc(&g->xbuf, n)) ||
         (rc = alloc(&g->hist, g->hist_cap))) {
         free_graph(g);
         return rc;
@@ -439,8 +436,7 @@ int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const
     if ((rc = ck(cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), s), "memset ctl")) ||
         (rc = ck(cudaMemsetAsync(g->colidx + m, 0, 16, s), "pad")) ||
         (rc = ck(cudaMemsetAsync(g->mval, 0, ((size_t)n + 4) * 4, s), "memset mval")) ||
-        (rc = ck(cudaMemsetAsync(g->snap, 0, (2 * (size_t)n + 4) * 4, s), "memset snap")) ||
-        (rc = ck(cudaMemsetAsync(g->bits, 0, 4 * W * 4, s), "memset bits"))) {
+        (rc = ck(cudaMemsetAsync(g->rec, 0, (size_t)n * 16, s), "memset rec"))) {
         free_graph(g);
         return rc;
     }
@@ -521,8 +517,8 @@ int map_run(map_graph *g, const map_opts *opts_in, map_result *res, uint32_t *ma
 
     int rc = MAP_OK;
     float dense_ms = 0.f, round_ms = 0.f, check_ms = 0.f;
-    if (g->dirty) { // the previous run stopped early: clear the snapshots it may have left
-        CK(cudaMemsetAsync(g->snap, 0, (2 * (size_t)n + 4) * 4, s));
+    if (g->dirty) { // the previous run stopped early: clear the round state it may have left
+        CK(cudaMemsetAsync(g->rec, 0, (size_t)n * 16, s));
     }
     g->dirty = true; // until this run completes normally
     if (!stepped) {

@@ -7,12 +7,14 @@
 //                            of u (the rows that contain u);
 //   acc[W], W = ceil(n/32)   the current accepting set, LSB-first bitmap;
 //   mval[n]                  enc(map(v)): 0 = no value, u + 1 = vertex u;
-//   list[2][n], cbit[2][W]   vertices whose value changed in a round (by round
-//                            parity) and the bitmap that keeps them unique;
-//   snap[2][n]               synchronous rounds: a listed vertex's value at the
-//                            end of its round (zero elsewhere);
-//   flist[2][n], fbit[2][W]  the frontier of a round (rows reading a vertex that
+//   list[2][n]               vertices whose value changed in a round, by round parity;
+//   flist[2][n]              the frontier of a round (rows reading a vertex that
 //                            changed in the round before), for the relaxation count;
+//   rec[n] (16 bytes)        per-vertex round state, in one sector so that a push
+//                            touches two sectors (mval and rec): snap[0..1], the
+//                            value a listed vertex ended its round with
+//                            (synchronous rounds), and flags: CB(p) = "in list[p]",
+//                            FB(p) = "in flist[p]";
 //   touched[n]               vertices that got a value in this outer iteration;
 //   Ctl                      the control block below (one per graph).
 //
@@ -76,10 +78,16 @@ struct Dev {
     uint32_t n, words;
     const uint32_t *rowptr, *colidx, *rrowptr, *rcol;
     uint32_t *acc, *mval;
-    uint32_t *list[2], *cbit[2], *snap[2], *flist[2], *fbit[2];
+    uint32_t *list[2], *flist[2];
+    uint4 *rec; // .x / .y: snap[0] / snap[1]; .z: flags
     uint32_t *touched;
     Ctl *ctl;
 };
+
+__device__ __forceinline__ uint32_t CB(uint32_t p) { return 1u << p; }       // in list[p]
+__device__ __forceinline__ uint32_t FB(uint32_t p) { return 4u << p; }       // in flist[p]
+__device__ __forceinline__ uint32_t *rec_snap(uint4 *r, uint32_t p) { return p ? &r->y : &r->x; }
+__device__ __forceinline__ uint32_t *rec_flags(uint4 *r) { return &r->z; }
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
@@ -453,7 +461,7 @@ __global__ void __launch_bounds__(DT_THREADS, 4) k_dense(const Dev d, Handles hd
             const uint32_t v = r0 + lane * 4 + k;
             if (got) {
                 best[lane * 4 + k] = 0;
-                d.snap[1][v] = bs[k];
+                *rec_snap(d.rec + v, 1) = bs[k];
             }
             stage_append<1>(st, 0, got, v, dst, ctr);
         }
@@ -497,21 +505,22 @@ __device__ __forceinline__ void warp_append(bool flag, uint32_t w, uint32_t *arr
     if (flag) arr[base + __popc(mask & ((1u << lane) - 1u))] = w;
 }
 
-// clear a frontier bitmap from its list and return the row lengths of the listed rows
+// clear the frontier flag FB(p) of the rows in flist[p] and return their row lengths
 __device__ __forceinline__ unsigned long long clear_frontier(const uint32_t *__restrict__ flist, uint32_t nf,
-                                                             uint32_t *fbit, const uint32_t *__restrict__ rowptr)
+                                                             uint32_t p, uint4 *rec,
+                                                             const uint32_t *__restrict__ rowptr)
 {
     unsigned long long relax = 0;
     const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += nthreads) {
         const uint32_t w = __ldg(flist + i);
-        fbit[w >> 5] = 0; // every bit in this bitmap belongs to this list
+        atomicAnd(rec_flags(rec + w), ~FB(p));
         relax += __ldg(rowptr + w + 1) - __ldg(rowptr + w);
     }
     return relax;
 }
 
-// exclusive-free inclusive warp scan
+// inclusive warp scan
 __device__ __forceinline__ uint32_t warp_inclusive_scan(uint32_t x)
 {
 #pragma unroll
@@ -533,35 +542,38 @@ __global__ void __launch_bounds__(256, 5) k_push(const Dev d, Handles hd)
     const uint32_t q = k & 1u, q2 = q ^ 1u;
     const uint32_t nl = *(volatile uint32_t *)&ctl->lcnt[q];
     const uint32_t nf = *(volatile uint32_t *)&ctl->fcnt[q];
-    const uint32_t *__restrict__ list = d.list[q];
-    uint32_t *snap_in = d.snap[q], *snap_out = d.snap[q2];
-    uint32_t *cbit_in = d.cbit[q], *cbit_out = d.cbit[q2];
-    uint32_t *fbit_out = d.fbit[q2];
+    // (parity-indexed pointers picked with selects: a dynamic index into the
+    // parameter struct would move it to local memory)
+    const uint32_t *__restrict__ list = q ? d.list[1] : d.list[0];
+    uint32_t *const list_out = q ? d.list[0] : d.list[1];
+    uint32_t *const flist_in = q ? d.flist[1] : d.flist[0];
+    uint32_t *const flist_out = q ? d.flist[0] : d.flist[1];
     // appends: 0 = this round's frontier, 1 = changed vertices, 2 = newly touched vertices
-    uint32_t *const dst[3][2] = {{d.flist[q2], nullptr}, {d.list[q2], nullptr}, {d.touched, nullptr}};
+    uint32_t *const dst[3][2] = {{flist_out, nullptr}, {list_out, nullptr}, {d.touched, nullptr}};
     unsigned int *const ctr[3] = {&ctl->fcnt[q2], &ctl->lcnt[q2], &ctl->tcnt};
     Stage<3> st;
     st.buf = s_stage[threadIdx.x >> 5];
     st.cnt[0] = st.cnt[1] = st.cnt[2] = 0;
     // round k's frontier: clear its bitmap, count its relaxations
-    unsigned long long relax = clear_frontier(d.flist[q], nf, d.fbit[q], d.rowptr);
+    unsigned long long relax = clear_frontier(flist_in, nf, q, d.rec, d.rowptr);
 
     const unsigned lane = lane_id();
     const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t warp_first = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
     for (uint64_t base = warp_first; base < nl; base += nthreads) {
         // 32 listed vertices per warp: each lane reads one and consumes its
-        // snapshot and de-duplication bit (nothing else reads them in this round)
+        // snapshot and list flag (nothing else reads them in this round)
         const uint64_t i = base + lane;
         uint32_t o = 0, b = 0, len = 0;
         if (i < nl) {
             const uint32_t u = __ldg(list + i);
-            const uint32_t mu = SYNC ? snap_in[u] : *(volatile uint32_t *)(d.mval + u);
+            const uint32_t mu = SYNC ? *(volatile uint32_t *)rec_snap(d.rec + u, q)
+                                     : *(volatile uint32_t *)(d.mval + u);
             o = acc_bit(d.acc, u) ? max(mu, u + 1) : mu;
             b = __ldg(d.rrowptr + u);
             len = __ldg(d.rrowptr + u + 1) - b;
-            if (SYNC) snap_in[u] = 0;
-            cbit_in[u >> 5] = 0; // every bit in cbit[q] belongs to list[q]
+            if (SYNC) *rec_snap(d.rec + u, q) = 0;
+            atomicAnd(rec_flags(d.rec + u), ~CB(q));
         }
         // their (vertex, reader) pairs, spread evenly over the lanes
         const uint32_t incl = warp_inclusive_scan(len);
@@ -577,21 +589,20 @@ __global__ void __launch_bounds__(256, 5) k_push(const Dev d, Handles hd)
             const uint32_t bb = __shfl_sync(0xFFFFFFFFu, b, src);
             const uint32_t eb = __shfl_sync(0xFFFFFFFFu, excl, src);
             const bool act = p < total;
-            uint32_t w = 0, bit = 0, fold = 0, mold = 0xFFFFFFFFu;
+            uint32_t w = 0, fold = FB(q2), mold = 0xFFFFFFFFu;
             if (act) {
                 w = __ldg(d.rcol + bb + (p - eb));
-                bit = 1u << (w & 31u);
-                fold = atomicOr(fbit_out + (w >> 5), bit); // both atomics in flight together
+                fold = atomicOr(rec_flags(d.rec + w), FB(q2)); // both atomics in flight together
                 mold = atomicMax(d.mval + w, ob);
             }
             const bool raised = act && ob > mold;
-            uint32_t cold = bit;
-            if (raised) {
-                if (SYNC) atomicMax(snap_out + w, ob);
-                cold = atomicOr(cbit_out + (w >> 5), bit);
+            uint32_t cold = CB(q2);
+            if (raised) { // the record's sector is in L2 by now
+                if (SYNC) atomicMax(rec_snap(d.rec + w, q2), ob);
+                cold = atomicOr(rec_flags(d.rec + w), CB(q2));
             }
-            stage_append<3>(st, 0, act && !(fold & bit), w, dst, ctr);
-            stage_append<3>(st, 1, raised && !(cold & bit), w, dst, ctr);
+            stage_append<3>(st, 0, act && !(fold & FB(q2)), w, dst, ctr);
+            stage_append<3>(st, 1, raised && !(cold & CB(q2)), w, dst, ctr);
             stage_append<3>(st, 2, raised && mold == 0, w, dst, ctr);
         }
     }
@@ -616,8 +627,8 @@ __global__ void __launch_bounds__(256) k_check(const Dev d, Handles hd)
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
     // the last round's frontier: clear its bitmap, count its relaxations
-    unsigned long long relax = clear_frontier(d.flist[0], nf0, d.fbit[0], d.rowptr);
-    relax += clear_frontier(d.flist[1], nf1, d.fbit[1], d.rowptr);
+    unsigned long long relax = clear_frontier(d.flist[0], nf0, 0, d.rec, d.rowptr);
+    relax += clear_frontier(d.flist[1], nf1, 1, d.rec, d.rowptr);
     unsigned elim = 0;
     uint32_t wit = NONE;
     for (uint64_t i = tid; i < nt; i += nthreads) {
