@@ -441,7 +441,7 @@ int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const
         return rc;
     }
     mapk::k_validate<<<grid_for(g, m > n ? m : n, 1), 256, 0, s>>>(n, g->rowptr, m, g->colidx, &g->ctl->bad);
-    mapk::k_acc_init<<<grid_for(g, W, 1), 256, 0, s>>>(n, acc_in, g->acc0, &g->ctl->elim);
+    mapk::k_acc_init<<<grid_for(g, W, 1), 256, 0, s>>>(n, acc_in, g->acc0, &g->ctl->elim.v);
     if ((rc = ck(cudaGetLastError(), "validate")) || (rc = read_ctl(g))) {
         free_graph(g);
         return rc;
@@ -450,7 +450,7 @@ int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const
         free_graph(g);
         return fail(MAP_ERR_CSR, "map_create: invalid CSR (decreasing rowptr or colidx >= n)");
     }
-    g->nacc0 = g->h_ctl->elim;
+    g->nacc0 = g->h_ctl->elim.v;
 
     // reverse CSR: in-degree histogram, scan, scatter
     if ((rc = ck(cudaMemsetAsync(g->rrowptr, 0, ((size_t)n + 1) * 4, s), "memset rrowptr"))) {
@@ -513,7 +513,7 @@ int map_run(map_graph *g, const map_opts *opts_in, map_result *res, uint32_t *ma
     init.out = out_dev ? map_out : g->xbuf;
     init.use_graph = stepped ? 0 : 1;
     init.timeout_ns = (uint64_t)(opts.timeout_ms ? opts.timeout_ms : 120000u) * 1000000ull;
-    init.witness = mapk::NONE;
+    init.witness.v = mapk::NONE;
 
     int rc = MAP_OK;
     float dense_ms = 0.f, round_ms = 0.f, check_ms = 0.f;
@@ -555,7 +555,7 @@ int map_run(map_graph *g, const map_opts *opts_in, map_result *res, uint32_t *ma
                 if ((rc = launch_round(g, s, sync_sched, none))) return rc;
                 if (profile) CK(cudaEventRecord(g->ev[5], s));
                 if ((rc = read_ctl(g))) return rc;
-                res->frontier_rows += g->h_ctl->fcnt[g->h_ctl->k & 1];
+                res->frontier_rows += g->h_ctl->fcnt[g->h_ctl->k & 1].v;
                 if (profile) {
                     float ms = 0.f;
                     CK(cudaEventElapsedTime(&ms, g->ev[4], g->ev[5]));
@@ -588,11 +588,11 @@ int map_run(map_graph *g, const map_opts *opts_in, map_result *res, uint32_t *ma
     CK(cudaEventElapsedTime(&total_ms, g->ev[0], g->ev[1]));
     const Ctl &c = *g->h_ctl;
     res->verdict = c.verdict ? MAP_CYCLE : MAP_NO_CYCLE;
-    res->witness = c.verdict ? c.witness : MAP_NONE;
+    res->witness = c.verdict ? c.witness.v : MAP_NONE;
     res->outer_iters = c.outer;
     res->inner_canonical = sync_sched ? 1 : 0;
     res->inner_iters = c.inner_total;
-    res->relaxations = c.relax;
+    res->relaxations = c.relax.v;
     res->edges_total = g->m * (uint64_t)c.outer;
     res->device_ms = total_ms;
     res->dense_ms = dense_ms;

@@ -36,11 +36,26 @@ namespace cg = cooperative_groups;
 constexpr uint32_t NONE = 0xFFFFFFFFu;
 constexpr uint32_t ST_OK = 0, ST_TIMEOUT = 5, ST_LIMIT = 6; // map_status values used on the device
 
+// Counters that many blocks update atomically each get a 128-byte line of their
+// own: atomics on one line are serialised, so sharing a line would make every
+// kernel wait on the others' updates.
+struct alignas(128) Cnt32 {
+    uint32_t v;
+};
+struct alignas(128) Cnt64 {
+    uint64_t v;
+};
+
 struct Ctl {
+    // hot counters
+    Cnt32 lcnt[2];         // |list| by round parity
+    Cnt32 fcnt[2];         // |flist| by round parity
+    Cnt32 tcnt;            // |touched|
+    Cnt32 done;            // last-block ticket
+    Cnt32 elim;            // accepting vertices eliminated in this outer iteration
+    Cnt32 witness;         // smallest self-mapped vertex of the last iteration
+    Cnt64 relax;           // edges examined (canonical count of the synchronous schedule)
     // fix-point loop
-    uint32_t lcnt[2];      // |list| by round parity
-    uint32_t fcnt[2];      // |flist| by round parity
-    uint32_t tcnt;         // |touched|
     uint32_t k;            // rounds completed in the current outer iteration
     // outer loop
     uint32_t outer;        // current outer iteration, 1-based (0: none ran)
@@ -48,17 +63,13 @@ struct Ctl {
     uint32_t outer_go;     // outer loop continues
     uint32_t status;       // ST_OK, ST_LIMIT or ST_TIMEOUT
     uint32_t verdict;      // 1 = accepting cycle
-    uint32_t witness;      // smallest self-mapped vertex of the last iteration
-    uint32_t elim;         // accepting vertices eliminated in this outer iteration
     uint32_t nacc;         // accepting vertices left
     uint32_t nacc0;        // accepting vertices at the start
-    uint32_t done;         // last-block ticket
     uint32_t max_outer;    // 0 = no limit
     uint32_t max_inner;    // rounds per outer iteration
     uint32_t hist_cap;     // entries of rounds_hist
     uint32_t bad;          // set-up: validation failure
     uint64_t m;            // edges
-    uint64_t relax;        // edges examined (canonical count of the synchronous schedule)
     uint64_t inner_total;  // rounds summed over outer iterations
     uint32_t *rounds_hist; // rounds of each outer iteration
     uint32_t *out;         // map export destination (device)
@@ -118,6 +129,42 @@ __device__ __forceinline__ unsigned long long warp_sum64(unsigned long long x)
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, off);
     return x;
+}
+
+// Block-wide sum (or min) of per-thread values, applied to a global counter with
+// one atomic per block.  Every thread of the block calls these (__syncthreads).
+__device__ __forceinline__ void block_add_u64(unsigned long long x, unsigned long long *dst)
+{
+    __shared__ unsigned long long part[32];
+    x = warp_sum64(x);
+    if (lane_id() == 0) part[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (unsigned w = 0; w < (blockDim.x >> 5); ++w) t += part[w];
+        if (t) atomicAdd(dst, t);
+    }
+}
+
+__device__ __forceinline__ void block_add_min_u32(uint32_t add, uint32_t mn, uint32_t *dst_add, uint32_t *dst_min)
+{
+    __shared__ uint32_t part_add[32], part_min[32];
+    add = __reduce_add_sync(0xFFFFFFFFu, add);
+    mn = __reduce_min_sync(0xFFFFFFFFu, mn);
+    if (lane_id() == 0) {
+        part_add[threadIdx.x >> 5] = add;
+        part_min[threadIdx.x >> 5] = mn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t a = 0, m = 0xFFFFFFFFu;
+        for (unsigned w = 0; w < (blockDim.x >> 5); ++w) {
+            a += part_add[w];
+            m = min(m, part_min[w]);
+        }
+        if (a) atomicAdd(dst_add, a);
+        if (m != 0xFFFFFFFFu) atomicMin(dst_min, m);
+    }
 }
 
 // ---- append staging -------------------------------------------------------
@@ -199,10 +246,10 @@ __device__ __forceinline__ bool last_block(Ctl *ctl)
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        const unsigned t = atomicAdd(&ctl->done, 1u);
+        const unsigned t = atomicAdd(&ctl->done.v, 1u);
         is_last = (t == gridDim.x - 1);
         if (is_last) {
-            ctl->done = 0;
+            ctl->done.v = 0;
             __threadfence();
         }
     }
@@ -240,10 +287,10 @@ __device__ __forceinline__ bool timed_out(volatile Ctl *v)
 __device__ void epilogue_dense(Ctl *c, Handles hd)
 {
     volatile Ctl *v = c;
-    const uint32_t changed = v->lcnt[1];
-    v->tcnt = changed;
+    const uint32_t changed = v->lcnt[1].v;
+    v->tcnt.v = changed;
     v->k = 1;
-    v->relax = v->relax + v->m;
+    v->relax.v = v->relax.v + v->m;
     uint32_t go = changed ? 1u : 0u;
     if (go && v->max_inner < 2) {
         v->status = ST_LIMIT;
@@ -261,9 +308,9 @@ __device__ void epilogue_round(Ctl *c, Handles hd)
     volatile Ctl *v = c;
     const uint32_t k = v->k + 1;         // the round just finished
     const uint32_t q = (k - 1) & 1u;     // parity of its input list (round k - 1)
-    const uint32_t changed = v->lcnt[q ^ 1u];
-    v->lcnt[q] = 0;                      // consumed
-    v->fcnt[q] = 0;                      // cleared by this round
+    const uint32_t changed = v->lcnt[q ^ 1u].v;
+    v->lcnt[q].v = 0;                      // consumed
+    v->fcnt[q].v = 0;                      // cleared by this round
     v->k = k;
     uint32_t go = changed ? 1u : 0u;
     if (go && k + 1 > v->max_inner) {
@@ -289,13 +336,13 @@ __device__ void epilogue_check(Ctl *c, Handles hd)
     uint32_t go = 1;
     if (v->status != ST_OK) {
         go = 0; // a limit was hit inside the fix-point loop
-    } else if (v->witness != NONE) {
+    } else if (v->witness.v != NONE) {
         v->verdict = 1;
         go = 0;
-    } else if (v->tcnt == 0) {
+    } else if (v->tcnt.v == 0) {
         go = 0; // no map value is defined: nothing reaches a remaining accepting vertex
     } else {
-        const uint32_t left = v->nacc - v->elim;
+        const uint32_t left = v->nacc - v->elim.v;
         v->nacc = left;
         if (left == 0) {
             go = 0;
@@ -311,10 +358,10 @@ __device__ void epilogue_check(Ctl *c, Handles hd)
     }
     if (go) {
         v->outer = outer + 1;
-        v->lcnt[0] = v->lcnt[1] = 0;
-        v->fcnt[0] = v->fcnt[1] = 0;
-        v->tcnt = 0;
-        v->elim = 0;
+        v->lcnt[0].v = v->lcnt[1].v = 0;
+        v->fcnt[0].v = v->fcnt[1].v = 0;
+        v->tcnt.v = 0;
+        v->elim.v = 0;
         v->k = 0;
     }
     v->outer_go = go;
@@ -328,17 +375,17 @@ __global__ void k_run_begin(Ctl *c, Handles hd)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     volatile Ctl *v = c;
-    v->lcnt[0] = v->lcnt[1] = 0;
-    v->fcnt[0] = v->fcnt[1] = 0;
-    v->tcnt = 0;
+    v->lcnt[0].v = v->lcnt[1].v = 0;
+    v->fcnt[0].v = v->fcnt[1].v = 0;
+    v->tcnt.v = 0;
     v->k = 0;
     v->status = ST_OK;
     v->verdict = 0;
-    v->witness = NONE;
-    v->elim = 0;
+    v->witness.v = NONE;
+    v->elim.v = 0;
     v->nacc = v->nacc0;
-    v->done = 0;
-    v->relax = 0;
+    v->done.v = 0;
+    v->relax.v = 0;
     v->inner_total = 0;
     v->t0 = global_ns();
     const uint32_t go = v->nacc0 ? 1u : 0u;
@@ -378,7 +425,7 @@ __global__ void __launch_bounds__(DT_THREADS, 4) k_dense(const Dev d, Handles hd
     Ctl *ctl = d.ctl;
     // the rows that get a value go to list[1] and to the touched list
     uint32_t *const dst[1][2] = {{d.list[1], d.touched}};
-    unsigned int *const ctr[1] = {&ctl->lcnt[1]};
+    unsigned int *const ctr[1] = {&ctl->lcnt[1].v};
     Stage<1> st;
     st.buf = s_stage[threadIdx.x >> 5];
     st.cnt[0] = 0;
@@ -540,8 +587,8 @@ __global__ void __launch_bounds__(256, 5) k_push(const Dev d, Handles hd)
     default_stop(ctl, hd.inner);
     const uint32_t k = *(volatile uint32_t *)&ctl->k; // rounds completed; this is round k + 1
     const uint32_t q = k & 1u, q2 = q ^ 1u;
-    const uint32_t nl = *(volatile uint32_t *)&ctl->lcnt[q];
-    const uint32_t nf = *(volatile uint32_t *)&ctl->fcnt[q];
+    const uint32_t nl = *(volatile uint32_t *)&ctl->lcnt[q].v;
+    const uint32_t nf = *(volatile uint32_t *)&ctl->fcnt[q].v;
     // (parity-indexed pointers picked with selects: a dynamic index into the
     // parameter struct would move it to local memory)
     const uint32_t *__restrict__ list = q ? d.list[1] : d.list[0];
@@ -550,7 +597,7 @@ __global__ void __launch_bounds__(256, 5) k_push(const Dev d, Handles hd)
     uint32_t *const flist_out = q ? d.flist[0] : d.flist[1];
     // appends: 0 = this round's frontier, 1 = changed vertices, 2 = newly touched vertices
     uint32_t *const dst[3][2] = {{flist_out, nullptr}, {list_out, nullptr}, {d.touched, nullptr}};
-    unsigned int *const ctr[3] = {&ctl->fcnt[q2], &ctl->lcnt[q2], &ctl->tcnt};
+    unsigned int *const ctr[3] = {&ctl->fcnt[q2].v, &ctl->lcnt[q2].v, &ctl->tcnt.v};
     Stage<3> st;
     st.buf = s_stage[threadIdx.x >> 5];
     st.cnt[0] = st.cnt[1] = st.cnt[2] = 0;
@@ -607,8 +654,7 @@ __global__ void __launch_bounds__(256, 5) k_push(const Dev d, Handles hd)
         }
     }
     stage_flush_block<3>(st, s_cnt, s_base, dst, ctr);
-    relax = warp_sum64(relax);
-    if (lane == 0 && relax) atomicAdd((unsigned long long *)&ctl->relax, relax);
+    block_add_u64(relax, (unsigned long long *)&ctl->relax.v);
     if (last_block(ctl)) epilogue_round(ctl, hd);
 }
 
@@ -622,8 +668,8 @@ __global__ void __launch_bounds__(256, 5) k_push(const Dev d, Handles hd)
 __global__ void __launch_bounds__(256) k_check(const Dev d, Handles hd)
 {
     Ctl *ctl = d.ctl;
-    const uint32_t nt = *(volatile uint32_t *)&ctl->tcnt;
-    const uint32_t nf0 = *(volatile uint32_t *)&ctl->fcnt[0], nf1 = *(volatile uint32_t *)&ctl->fcnt[1];
+    const uint32_t nt = *(volatile uint32_t *)&ctl->tcnt.v;
+    const uint32_t nf0 = *(volatile uint32_t *)&ctl->fcnt[0].v, nf1 = *(volatile uint32_t *)&ctl->fcnt[1].v;
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
     // the last round's frontier: clear its bitmap, count its relaxations
@@ -642,14 +688,8 @@ __global__ void __launch_bounds__(256) k_check(const Dev d, Handles hd)
             elim += (old & bit) ? 1u : 0u;
         }
     }
-    elim = __reduce_add_sync(0xFFFFFFFFu, elim);
-    wit = __reduce_min_sync(0xFFFFFFFFu, wit);
-    relax = warp_sum64(relax);
-    if (lane_id() == 0) {
-        if (elim) atomicAdd(&ctl->elim, elim);
-        if (wit != NONE) atomicMin(&ctl->witness, wit);
-        if (relax) atomicAdd((unsigned long long *)&ctl->relax, relax);
-    }
+    block_add_min_u32(elim, wit, &ctl->elim.v, &ctl->witness.v);
+    block_add_u64(relax, (unsigned long long *)&ctl->relax.v);
     if (last_block(ctl)) epilogue_check(ctl, hd);
 }
 
