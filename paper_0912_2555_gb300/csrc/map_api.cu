@@ -77,13 +77,13 @@ struct map_graph {
     int G = 4;
     int sms = 0;
     int dense_grid = 0;  // blocks of the dense-round kernel
-    int sparse_grid = 0; // blocks of the frontier-round kernels
+    int rounds_grid = 0; // blocks of the cooperative fix-point kernel (all resident)
     int check_grid = 0;  // blocks of the self-map / elimination kernel
     cudaStream_t stream = nullptr;
     uint32_t *rowptr = nullptr, *colidx = nullptr, *rrowptr = nullptr, *rcol = nullptr;
     uint32_t *acc0 = nullptr, *acc = nullptr, *mval = nullptr;
-    uint32_t *list = nullptr;  // 2n: vertices changed in a round, by parity
-    uint32_t *flist = nullptr; // 2n: frontier rows of a round, by parity
+    uint32_t *list = nullptr;  // 3n: vertices changed in a round, by round mod 3
+    uint32_t *flist = nullptr; // 3n: frontier rows of a round, by round mod 3
     uint4 *rec = nullptr;      // n: per-vertex round state (snapshots, list and frontier flags)
     uint32_t *touched = nullptr, *xbuf = nullptr;
     bool dirty = false; // a run stopped early: per-round state may be stale
@@ -185,7 +185,7 @@ mapk::Dev dev_of(const map_graph *g)
     d.acc = g->acc;
     d.mval = g->mval;
     const size_t n = g->n;
-    for (int p = 0; p < 2; ++p) {
+    for (int p = 0; p < 3; ++p) {
         d.list[p] = g->list + p * n;
         d.flist[p] = g->flist + p * n;
     }
@@ -202,12 +202,22 @@ int launch_dense(map_graph *g, cudaStream_t s, mapk::Handles hd)
     return MAP_OK;
 }
 
-int launch_round(map_graph *g, cudaStream_t s, bool sync_sched, mapk::Handles hd)
+// the fix-point loop: one cooperative launch (its grid barrier needs every block resident)
+int launch_rounds(map_graph *g, cudaStream_t s, bool sync_sched)
 {
     const mapk::Dev d = dev_of(g);
-    if (sync_sched) mapk::k_push<true><<<g->sparse_grid, 256, 0, s>>>(d, hd);
-    else mapk::k_push<false><<<g->sparse_grid, 256, 0, s>>>(d, hd);
-    CK(cudaGetLastError());
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)g->rounds_grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (sync_sched) CK(cudaLaunchKernelEx(&cfg, mapk::k_rounds<true>, d));
+    else CK(cudaLaunchKernelEx(&cfg, mapk::k_rounds<false>, d));
     return MAP_OK;
 }
 
@@ -233,7 +243,7 @@ int launch_export(map_graph *g, cudaStream_t s, uint32_t *override_dst)
     return MAP_OK;
 }
 
-// --- the run as a CUDA graph: outer WHILE { dense; WHILE { round }; check } --
+// --- the run as a CUDA graph: outer WHILE { dense; rounds; check } ---------
 
 int add_while(cudaStream_t cs, unsigned long long handle, cudaGraph_t *body)
 {
@@ -261,7 +271,7 @@ int build_run_graph(map_graph *g, int sched)
     cudaStream_t cs;
     CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     int rc = MAP_OK;
-    cudaGraph_t top = nullptr, outer_body = nullptr, inner_body = nullptr;
+    cudaGraph_t top = nullptr, outer_body = nullptr;
     mapk::Handles hd{};
     auto fin = [&](int code) {
         cudaStreamDestroy(cs);
@@ -292,21 +302,11 @@ int build_run_graph(map_graph *g, int sched)
         if (rc) return fin(rc);
         GK(e);
     }
-    // outer body: dense round, fix-point WHILE, self-map test + elimination
-    GK(cudaGraphConditionalHandleCreate(&hd.inner, outer_body, 0, cudaGraphCondAssignDefault));
+    // outer body: dense round, fix-point loop, self-map test + elimination
     GK(cudaStreamBeginCaptureToGraph(cs, outer_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     rc = launch_dense(g, cs, hd);
-    if (rc == MAP_OK) rc = add_while(cs, hd.inner, &inner_body);
+    if (rc == MAP_OK) rc = launch_rounds(g, cs, sync_sched);
     if (rc == MAP_OK) rc = launch_check(g, cs, hd);
-    {
-        cudaGraph_t got = nullptr;
-        cudaError_t e = cudaStreamEndCapture(cs, &got);
-        if (rc) return fin(rc);
-        GK(e);
-    }
-    // inner body: one round (compute + apply, or one sweep)
-    GK(cudaStreamBeginCaptureToGraph(cs, inner_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    rc = launch_round(g, cs, sync_sched, hd);
     {
         cudaGraph_t got = nullptr;
         cudaError_t e = cudaStreamEndCapture(cs, &got);
@@ -378,7 +378,11 @@ int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const
     if (occ <= 0) occ = 1;
     const uint64_t ntiles = ((uint64_t)n + mapk::WT_ROWS - 1) / mapk::WT_ROWS;
     g->dense_grid = (int)std::min<uint64_t>((ntiles + mapk::WT_WARPS - 1) / mapk::WT_WARPS, (uint64_t)g->sms * occ);
-    g->sparse_grid = (int)std::min<uint64_t>(((uint64_t)n + 255) / 256, (uint64_t)g->sms * 5);
+    int occ_r = 0, occ_a = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_r, mapk::k_rounds<true>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, mapk::k_rounds<false>, 256, 0);
+    occ_r = std::max(1, std::min(occ_r, occ_a));
+    g->rounds_grid = (int)std::min<uint64_t>(((uint64_t)n + 255) / 256, (uint64_t)g->sms * occ_r);
     g->check_grid = (int)std::min<uint64_t>(((uint64_t)n + 255) / 256, (uint64_t)g->sms * 4);
     g->hist_cap = 1u << 16;
 
@@ -390,8 +394,8 @@ int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const
     const uint64_t W = g->words;
     if ((rc = alloc(&g->rowptr, (uint64_t)n + 1)) || (rc = alloc(&g->colidx, m)) ||
         (rc = alloc(&g->rrowptr, (uint64_t)n + 1)) || (rc = alloc(&g->rcol, m)) || (rc = alloc(&g->acc0, W)) ||
-        (rc = alloc(&g->acc, W)) || (rc = alloc(&g->mval, n)) || (rc = alloc(&g->list, 2 * (uint64_t)n)) ||
-        (rc = alloc(&g->flist, 2 * (uint64_t)n)) || (rc = alloc((uint32_t **)&g->rec, 4 * (uint64_t)n)) ||
+        (rc = alloc(&g->acc, W)) || (rc = alloc(&g->mval, n)) || (rc = alloc(&g->list, 3 * (uint64_t)n)) ||
+        (rc = alloc(&g->flist, 3 * (uint64_t)n)) || (rc = alloc((uint32_t **)&g->rec, 4 * (uint64_t)n)) ||
         (rc = alloc(&g->touched, n)) || (rc = alloc(&g->xbuf, n)) ||
         (rc = alloc(&g->hist, g->hist_cap))) {
         free_graph(g);
@@ -550,17 +554,14 @@ int map_run(map_graph *g, const map_opts *opts_in, map_result *res, uint32_t *ma
                 dense_ms += ms;
                 res->dense_launches++;
             }
-            while (g->h_ctl->inner_go) {
-                if (profile) CK(cudaEventRecord(g->ev[4], s));
-                if ((rc = launch_round(g, s, sync_sched, none))) return rc;
-                if (profile) CK(cudaEventRecord(g->ev[5], s));
-                if ((rc = read_ctl(g))) return rc;
-                res->frontier_rows += g->h_ctl->fcnt[g->h_ctl->k & 1].v;
-                if (profile) {
-                    float ms = 0.f;
-                    CK(cudaEventElapsedTime(&ms, g->ev[4], g->ev[5]));
-                    round_ms += ms;
-                }
+            if (profile) CK(cudaEventRecord(g->ev[4], s));
+            if ((rc = launch_rounds(g, s, sync_sched))) return rc;
+            if (profile) CK(cudaEventRecord(g->ev[5], s));
+            if ((rc = read_ctl(g))) return rc;
+            if (profile) {
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, g->ev[4], g->ev[5]));
+                round_ms += ms;
             }
             if (opts.trace) {
                 const uint32_t outer = g->h_ctl->outer, k = g->h_ctl->k;
@@ -597,12 +598,11 @@ int map_run(map_graph *g, const map_opts *opts_in, map_result *res, uint32_t *ma
     res->device_ms = total_ms;
     res->dense_ms = dense_ms;
     res->round_ms = round_ms;
+    res->frontier_rows = c.frontier_rows.v;
     res->check_ms = check_ms;
     res->accepting_left = c.nacc;
-    // launches: reset (memcpy + memset are not kernels), run_begin, export, and per outer
-    // iteration dense + check, per round 2 (SYNC) or 1 (ASYNC)
-    const uint64_t rounds_after_first = c.inner_total >= c.outer ? c.inner_total - c.outer : 0;
-    res->launches = 2 + 2ull * c.outer + (sync_sched ? 2 : 1) * rounds_after_first;
+    // kernel launches: run_begin, export, and per outer iteration dense, rounds, check
+    res->launches = 2 + 3ull * c.outer;
     const uint32_t nh = std::min<uint32_t>(c.outer, g->hist_cap);
     if (opts.rounds_out && nh) {
         CK(cudaMemcpyAsync(g->h_hist, g->hist, (size_t)nh * 4, cudaMemcpyDeviceToHost, s));

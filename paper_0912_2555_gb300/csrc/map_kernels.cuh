@@ -7,11 +7,11 @@
 //                            of u (the rows that contain u);
 //   acc[W], W = ceil(n/32)   the current accepting set, LSB-first bitmap;
 //   mval[n]                  enc(map(v)): 0 = no value, u + 1 = vertex u;
-//   list[2][n]               vertices whose value changed in a round, by round parity;
-//   flist[2][n]              the frontier of a round (rows reading a vertex that
+//   list[3][n]               vertices whose value changed in a round, by round mod 3;
+//   flist[3][n]              the frontier of a round (rows reading a vertex that
 //                            changed in the round before), for the relaxation count;
 //   rec[n] (16 bytes)        per-vertex round state, in one sector so that a push
-//                            touches two sectors (mval and rec): snap[0..1], the
+//                            touches two sectors (mval and rec): snap[0..2], the
 //                            value a listed vertex ended its round with
 //                            (synchronous rounds), and flags: CB(p) = "in list[p]",
 //                            FB(p) = "in flist[p]";
@@ -19,7 +19,8 @@
 //   Ctl                      the control block below (one per graph).
 //
 // One outer iteration: the dense round (every row, k_dense), then push rounds
-// (k_push) until a round changes nothing, then the self-map test and the
+// until a round changes nothing (k_rounds, one persistent cooperative launch
+// with a grid barrier between rounds), then the self-map test and the
 // elimination over the touched vertices (k_check).  Every kernel that ends a
 // step of the loop finishes with a last-block epilogue (the last block to
 // retire, found with an atomic ticket) that updates the control block and, when
@@ -48,18 +49,21 @@ struct alignas(128) Cnt64 {
 
 struct Ctl {
     // hot counters
-    Cnt32 lcnt[2];         // |list| by round parity
-    Cnt32 fcnt[2];         // |flist| by round parity
+    Cnt32 lcnt[3];         // |list| by round mod 3
+    Cnt32 fcnt[3];         // |flist| by round mod 3
     Cnt32 tcnt;            // |touched|
     Cnt32 done;            // last-block ticket
     Cnt32 elim;            // accepting vertices eliminated in this outer iteration
     Cnt32 witness;         // smallest self-mapped vertex of the last iteration
     Cnt64 relax;           // edges examined (canonical count of the synchronous schedule)
+    Cnt64 frontier_rows;   // frontier rows summed over the push rounds
+    Cnt32 bar_count;       // grid barrier of k_rounds: arrivals
+    Cnt32 bar_gen;         // ... and generation
+    Cnt32 stop_req;        // k_rounds: block 0 asks every block to stop after the next barrier
     // fix-point loop
     uint32_t k;            // rounds completed in the current outer iteration
     // outer loop
     uint32_t outer;        // current outer iteration, 1-based (0: none ran)
-    uint32_t inner_go;     // fix-point loop continues
     uint32_t outer_go;     // outer loop continues
     uint32_t status;       // ST_OK, ST_LIMIT or ST_TIMEOUT
     uint32_t verdict;      // 1 = accepting cycle
@@ -80,8 +84,7 @@ struct Ctl {
 };
 
 struct Handles {
-    unsigned long long inner; // cudaGraphConditionalHandle of the fix-point WHILE node
-    unsigned long long outer; // ... of the outer WHILE node
+    unsigned long long outer; // cudaGraphConditionalHandle of the outer WHILE node
 };
 
 // device pointers of one graph, passed by value to the loop kernels
@@ -89,16 +92,22 @@ struct Dev {
     uint32_t n, words;
     const uint32_t *rowptr, *colidx, *rrowptr, *rcol;
     uint32_t *acc, *mval;
-    uint32_t *list[2], *flist[2];
-    uint4 *rec; // .x / .y: snap[0] / snap[1]; .z: flags
+    uint32_t *list[3], *flist[3];
+    uint4 *rec; // .x / .y / .z: snap[0..2]; .w: flags
     uint32_t *touched;
     Ctl *ctl;
 };
 
-__device__ __forceinline__ uint32_t CB(uint32_t p) { return 1u << p; }       // in list[p]
-__device__ __forceinline__ uint32_t FB(uint32_t p) { return 4u << p; }       // in flist[p]
-__device__ __forceinline__ uint32_t *rec_snap(uint4 *r, uint32_t p) { return p ? &r->y : &r->x; }
-__device__ __forceinline__ uint32_t *rec_flags(uint4 *r) { return &r->z; }
+__device__ __forceinline__ uint32_t CB(uint32_t p) { return 1u << p; } // in list[p]
+__device__ __forceinline__ uint32_t FB(uint32_t p) { return 8u << p; } // in flist[p]
+__device__ __forceinline__ uint32_t *rec_snap(uint4 *r, uint32_t p) { return p == 0 ? &r->x : p == 1 ? &r->y : &r->z; }
+__device__ __forceinline__ uint32_t *rec_flags(uint4 *r) { return &r->w; }
+// a parity-indexed pointer picked with selects (a dynamic index into the
+// parameter struct would move it to local memory)
+__device__ __forceinline__ uint32_t *pick3(uint32_t p, uint32_t *const (&a)[3])
+{
+    return p == 0 ? a[0] : p == 1 ? a[1] : a[2];
+}
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
@@ -284,46 +293,13 @@ __device__ __forceinline__ bool timed_out(volatile Ctl *v)
 
 // After round 1 (the dense round) of an outer iteration: list[1] holds the
 // vertices that got a value, which are also the touched vertices so far.
-__device__ void epilogue_dense(Ctl *c, Handles hd)
+__device__ void epilogue_dense(Ctl *c)
 {
     volatile Ctl *v = c;
-    const uint32_t changed = v->lcnt[1].v;
-    v->tcnt.v = changed;
+    v->tcnt.v = v->lcnt[1].v;
     v->k = 1;
     v->relax.v = v->relax.v + v->m;
-    uint32_t go = changed ? 1u : 0u;
-    if (go && v->max_inner < 2) {
-        v->status = ST_LIMIT;
-        go = 0;
-    }
-    if (v->status != ST_OK) go = 0;
-    v->inner_go = go;
     __threadfence();
-    set_cond(c, hd.inner, go);
-}
-
-// After push round k + 1 >= 2.
-__device__ void epilogue_round(Ctl *c, Handles hd)
-{
-    volatile Ctl *v = c;
-    const uint32_t k = v->k + 1;         // the round just finished
-    const uint32_t q = (k - 1) & 1u;     // parity of its input list (round k - 1)
-    const uint32_t changed = v->lcnt[q ^ 1u].v;
-    v->lcnt[q].v = 0;                      // consumed
-    v->fcnt[q].v = 0;                      // cleared by this round
-    v->k = k;
-    uint32_t go = changed ? 1u : 0u;
-    if (go && k + 1 > v->max_inner) {
-        v->status = ST_LIMIT;
-        go = 0;
-    }
-    if (go && timed_out(v)) {
-        v->status = ST_TIMEOUT;
-        go = 0;
-    }
-    v->inner_go = go;
-    __threadfence();
-    set_cond(c, hd.inner, go);
 }
 
 // After the self-map test and the elimination of an outer iteration.
@@ -358,8 +334,8 @@ __device__ void epilogue_check(Ctl *c, Handles hd)
     }
     if (go) {
         v->outer = outer + 1;
-        v->lcnt[0].v = v->lcnt[1].v = 0;
-        v->fcnt[0].v = v->fcnt[1].v = 0;
+        v->lcnt[0].v = v->lcnt[1].v = v->lcnt[2].v = 0;
+        v->fcnt[0].v = v->fcnt[1].v = v->fcnt[2].v = 0;
         v->tcnt.v = 0;
         v->elim.v = 0;
         v->k = 0;
@@ -375,9 +351,12 @@ __global__ void k_run_begin(Ctl *c, Handles hd)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     volatile Ctl *v = c;
-    v->lcnt[0].v = v->lcnt[1].v = 0;
-    v->fcnt[0].v = v->fcnt[1].v = 0;
+    v->lcnt[0].v = v->lcnt[1].v = v->lcnt[2].v = 0;
+    v->fcnt[0].v = v->fcnt[1].v = v->fcnt[2].v = 0;
     v->tcnt.v = 0;
+    v->frontier_rows.v = 0;
+    v->bar_count.v = 0;
+    v->stop_req.v = 0;
     v->k = 0;
     v->status = ST_OK;
     v->verdict = 0;
@@ -391,7 +370,6 @@ __global__ void k_run_begin(Ctl *c, Handles hd)
     const uint32_t go = v->nacc0 ? 1u : 0u;
     v->outer = go;
     v->outer_go = go;
-    v->inner_go = 0;
     __threadfence();
     set_cond(c, hd.outer, go);
 }
@@ -515,7 +493,7 @@ __global__ void __launch_bounds__(DT_THREADS, 4) k_dense(const Dev d, Handles hd
         __syncwarp();
     }
     stage_flush_block<1>(st, s_cnt, s_base, dst, ctr);
-    if (last_block(ctl)) epilogue_dense(ctl, hd);
+    if (last_block(ctl)) epilogue_dense(ctl);
 }
 
 // ------------------------------------------------------------ push rounds --
@@ -578,103 +556,159 @@ __device__ __forceinline__ uint32_t warp_inclusive_scan(uint32_t x)
     return x;
 }
 
+// Bounded grid-wide barrier of a cooperative launch (every block resident).
+// Returns false if the wait gave up (the caller then stops).
+constexpr uint32_t BAR_SPIN_LIMIT = 1u << 24;
+
+__device__ __forceinline__ bool grid_barrier(Ctl *ctl)
+{
+    __shared__ uint32_t s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t ok = 1;
+        const uint32_t gen = *(volatile uint32_t *)&ctl->bar_gen.v;
+        __threadfence();
+        if (atomicAdd(&ctl->bar_count.v, 1u) == gridDim.x - 1) {
+            atomicExch(&ctl->bar_count.v, 0u);
+            __threadfence();
+            atomicAdd(&ctl->bar_gen.v, 1u);
+        } else {
+            for (uint32_t it = 0; *(volatile uint32_t *)&ctl->bar_gen.v == gen; ++it) {
+                if (it > BAR_SPIN_LIMIT) {
+                    ok = 0;
+                    break;
+                }
+                if (it > 16) __nanosleep(32);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// The fix-point loop of one outer iteration: rounds 2, 3, ... until a round
+// changes nothing.  Round r reads list[(r-1) % 3] and appends to list[r % 3];
+// the counters of list[(r+1) % 3] (read in round r-1, appended again in round
+// r+1) are reset by block 0 during round r, so one barrier per round suffices.
 template <bool SYNC>
-__global__ void __launch_bounds__(256, 5) k_push(const Dev d, Handles hd)
+__global__ void __launch_bounds__(256, 4) k_rounds(const Dev d)
 {
     __shared__ uint32_t s_stage[8][3 * SB_ENTRIES];
     __shared__ uint32_t s_cnt[8][3], s_base[3];
     Ctl *ctl = d.ctl;
-    default_stop(ctl, hd.inner);
-    const uint32_t k = *(volatile uint32_t *)&ctl->k; // rounds completed; this is round k + 1
-    const uint32_t q = k & 1u, q2 = q ^ 1u;
-    const uint32_t nl = *(volatile uint32_t *)&ctl->lcnt[q].v;
-    const uint32_t nf = *(volatile uint32_t *)&ctl->fcnt[q].v;
-    // (parity-indexed pointers picked with selects: a dynamic index into the
-    // parameter struct would move it to local memory)
-    const uint32_t *__restrict__ list = q ? d.list[1] : d.list[0];
-    uint32_t *const list_out = q ? d.list[0] : d.list[1];
-    uint32_t *const flist_in = q ? d.flist[1] : d.flist[0];
-    uint32_t *const flist_out = q ? d.flist[0] : d.flist[1];
-    // appends: 0 = this round's frontier, 1 = changed vertices, 2 = newly touched vertices
-    uint32_t *const dst[3][2] = {{flist_out, nullptr}, {list_out, nullptr}, {d.touched, nullptr}};
-    unsigned int *const ctr[3] = {&ctl->fcnt[q2].v, &ctl->lcnt[q2].v, &ctl->tcnt.v};
-    Stage<3> st;
-    st.buf = s_stage[threadIdx.x >> 5];
-    st.cnt[0] = st.cnt[1] = st.cnt[2] = 0;
-    // round k's frontier: clear its bitmap, count its relaxations
-    unsigned long long relax = clear_frontier(flist_in, nf, q, d.rec, d.rowptr);
-
+    volatile Ctl *vc = ctl;
     const unsigned lane = lane_id();
     const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t warp_first = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
-    for (uint64_t base = warp_first; base < nl; base += nthreads) {
-        // 32 listed vertices per warp: each lane reads one and consumes its
-        // snapshot and list flag (nothing else reads them in this round)
-        const uint64_t i = base + lane;
-        uint32_t o = 0, b = 0, len = 0;
-        if (i < nl) {
-            const uint32_t u = __ldg(list + i);
-            const uint32_t mu = SYNC ? *(volatile uint32_t *)rec_snap(d.rec + u, q)
-                                     : *(volatile uint32_t *)(d.mval + u);
-            o = acc_bit(d.acc, u) ? max(mu, u + 1) : mu;
-            b = __ldg(d.rrowptr + u);
-            len = __ldg(d.rrowptr + u + 1) - b;
-            if (SYNC) *rec_snap(d.rec + u, q) = 0;
-            atomicAnd(rec_flags(d.rec + u), ~CB(q));
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    const uint32_t max_inner = vc->max_inner;
+    unsigned long long relax = 0, frows = 0;
+    uint32_t status = ST_OK;
+    uint32_t nl = vc->lcnt[1].v; // vertices that got a value in the dense round
+    uint32_t r = 1;              // rounds completed
+    if (nl && max_inner < 2) status = ST_LIMIT;
+    while (nl && status == ST_OK) {
+        const uint32_t rr = r + 1; // this round
+        const uint32_t p_in = (rr - 1) % 3, p_out = rr % 3, p_free = (rr + 1) % 3;
+        if (lead) {
+            vc->lcnt[p_free].v = 0;
+            vc->fcnt[p_free].v = 0;
         }
-        // their (vertex, reader) pairs, spread evenly over the lanes
-        const uint32_t incl = warp_inclusive_scan(len);
-        const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        const uint32_t excl = incl - len;
-        for (uint32_t p0 = 0; p0 < total; p0 += 32) {
-            const uint32_t p = p0 + lane;
-            uint32_t src = 0; // the lane whose list entry owns pair p: the number of lanes with incl <= p
+        const uint32_t *__restrict__ list = pick3(p_in, d.list);
+        uint32_t *const list_out = pick3(p_out, d.list);
+        uint32_t *const flist_out = pick3(p_out, d.flist);
+        // appends: 0 = this round's frontier, 1 = changed vertices, 2 = newly touched vertices
+        uint32_t *const dst[3][2] = {{flist_out, nullptr}, {list_out, nullptr}, {d.touched, nullptr}};
+        unsigned int *const ctr[3] = {&ctl->fcnt[p_out].v, &ctl->lcnt[p_out].v, &ctl->tcnt.v};
+        Stage<3> st;
+        st.buf = s_stage[threadIdx.x >> 5];
+        st.cnt[0] = st.cnt[1] = st.cnt[2] = 0;
+        // the previous round's frontier: clear its flags, count its relaxations
+        relax += clear_frontier(pick3(p_in, d.flist), vc->fcnt[p_in].v, p_in, d.rec, d.rowptr);
+
+        for (uint64_t base = warp_first; base < nl; base += nthreads) {
+            // 32 listed vertices per warp: each lane reads one and consumes its
+            // snapshot and list flag (nothing else reads them in this round)
+            const uint64_t i = base + lane;
+            uint32_t o = 0, b = 0, len = 0;
+            if (i < nl) {
+                const uint32_t u = __ldg(list + i);
+                const uint32_t mu = SYNC ? *(volatile uint32_t *)rec_snap(d.rec + u, p_in)
+                                         : *(volatile uint32_t *)(d.mval + u);
+                o = acc_bit(d.acc, u) ? max(mu, u + 1) : mu;
+                b = __ldg(d.rrowptr + u);
+                len = __ldg(d.rrowptr + u + 1) - b;
+                if (SYNC) *rec_snap(d.rec + u, p_in) = 0;
+                atomicAnd(rec_flags(d.rec + u), ~CB(p_in));
+            }
+            // their (vertex, reader) pairs, spread evenly over the lanes
+            const uint32_t incl = warp_inclusive_scan(len);
+            const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+            const uint32_t excl = incl - len;
+            for (uint32_t p0 = 0; p0 < total; p0 += 32) {
+                const uint32_t p = p0 + lane;
+                uint32_t src = 0; // the lane owning pair p: the number of lanes with incl <= p
 #pragma unroll
-            for (int step = 16; step > 0; step >>= 1)
-                if (__shfl_sync(0xFFFFFFFFu, incl, src + step - 1) <= p) src += step;
-            const uint32_t ob = __shfl_sync(0xFFFFFFFFu, o, src);
-            const uint32_t bb = __shfl_sync(0xFFFFFFFFu, b, src);
-            const uint32_t eb = __shfl_sync(0xFFFFFFFFu, excl, src);
-            const bool act = p < total;
-            uint32_t w = 0, fold = FB(q2), mold = 0xFFFFFFFFu;
-            if (act) {
-                w = __ldg(d.rcol + bb + (p - eb));
-                fold = atomicOr(rec_flags(d.rec + w), FB(q2)); // both atomics in flight together
-                mold = atomicMax(d.mval + w, ob);
+                for (int step = 16; step > 0; step >>= 1)
+                    if (__shfl_sync(0xFFFFFFFFu, incl, src + step - 1) <= p) src += step;
+                const uint32_t ob = __shfl_sync(0xFFFFFFFFu, o, src);
+                const uint32_t bb = __shfl_sync(0xFFFFFFFFu, b, src);
+                const uint32_t eb = __shfl_sync(0xFFFFFFFFu, excl, src);
+                const bool act = p < total;
+                uint32_t w = 0, fold = FB(p_out), mold = 0xFFFFFFFFu;
+                if (act) {
+                    w = __ldg(d.rcol + bb + (p - eb));
+                    fold = atomicOr(rec_flags(d.rec + w), FB(p_out)); // both atomics in flight together
+                    mold = atomicMax(d.mval + w, ob);
+                }
+                const bool raised = act && ob > mold;
+                uint32_t cold = CB(p_out);
+                if (raised) { // the record's sector is in L2 by now
+                    if (SYNC) atomicMax(rec_snap(d.rec + w, p_out), ob);
+                    cold = atomicOr(rec_flags(d.rec + w), CB(p_out));
+                }
+                stage_append<3>(st, 0, act && !(fold & FB(p_out)), w, dst, ctr);
+                stage_append<3>(st, 1, raised && !(cold & CB(p_out)), w, dst, ctr);
+                stage_append<3>(st, 2, raised && mold == 0, w, dst, ctr);
             }
-            const bool raised = act && ob > mold;
-            uint32_t cold = CB(q2);
-            if (raised) { // the record's sector is in L2 by now
-                if (SYNC) atomicMax(rec_snap(d.rec + w, q2), ob);
-                cold = atomicOr(rec_flags(d.rec + w), CB(q2));
-            }
-            stage_append<3>(st, 0, act && !(fold & FB(q2)), w, dst, ctr);
-            stage_append<3>(st, 1, raised && !(cold & CB(q2)), w, dst, ctr);
-            stage_append<3>(st, 2, raised && mold == 0, w, dst, ctr);
         }
+        stage_flush_block<3>(st, s_cnt, s_base, dst, ctr);
+        if (lead && timed_out(vc)) vc->stop_req.v = 1;
+        if (!grid_barrier(ctl)) {
+            status = ST_TIMEOUT;
+            break;
+        }
+        r = rr;
+        nl = vc->lcnt[p_out].v; // changed in this round
+        frows += vc->fcnt[p_out].v;
+        if (vc->stop_req.v) status = ST_TIMEOUT;
+        else if (nl && r + 1 > max_inner) status = ST_LIMIT;
     }
-    stage_flush_block<3>(st, s_cnt, s_base, dst, ctr);
+    // the last round's frontier: clear its flags, count its relaxations
+    if (r > 1) relax += clear_frontier(pick3(r % 3, d.flist), vc->fcnt[r % 3].v, r % 3, d.rec, d.rowptr);
     block_add_u64(relax, (unsigned long long *)&ctl->relax.v);
-    if (last_block(ctl)) epilogue_round(ctl, hd);
+    if (lead) {
+        vc->k = r;
+        vc->frontier_rows.v = vc->frontier_rows.v + frows;
+        if (status != ST_OK) vc->status = status;
+        __threadfence();
+    }
 }
 
 // ------------------------------------------------- self-map test, elimination --
 //
 // Over the touched vertices (exactly the vertices with a defined map value),
 // Section 2: witness = smallest v with map(v) = v; every map value u is removed
-// from the accepting set (exact count of removals).  Also clears what is left
-// of the last round's frontier bitmap.  The map vector is left intact (the next
-// dense round overwrites it).
+// from the accepting set (exact count of removals).  The map vector is left
+// intact (the next dense round overwrites it).
 __global__ void __launch_bounds__(256) k_check(const Dev d, Handles hd)
 {
     Ctl *ctl = d.ctl;
     const uint32_t nt = *(volatile uint32_t *)&ctl->tcnt.v;
-    const uint32_t nf0 = *(volatile uint32_t *)&ctl->fcnt[0].v, nf1 = *(volatile uint32_t *)&ctl->fcnt[1].v;
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
-    // the last round's frontier: clear its bitmap, count its relaxations
-    unsigned long long relax = clear_frontier(d.flist[0], nf0, 0, d.rec, d.rowptr);
-    relax += clear_frontier(d.flist[1], nf1, 1, d.rec, d.rowptr);
     unsigned elim = 0;
     uint32_t wit = NONE;
     for (uint64_t i = tid; i < nt; i += nthreads) {
@@ -689,7 +723,6 @@ __global__ void __launch_bounds__(256) k_check(const Dev d, Handles hd)
         }
     }
     block_add_min_u32(elim, wit, &ctl->elim.v, &ctl->witness.v);
-    block_add_u64(relax, (unsigned long long *)&ctl->relax.v);
     if (last_block(ctl)) epilogue_check(ctl, hd);
 }
 
