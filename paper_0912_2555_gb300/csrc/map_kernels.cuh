@@ -556,6 +556,26 @@ __device__ __forceinline__ uint32_t warp_inclusive_scan(uint32_t x)
     return x;
 }
 
+// inclusive scan over a 256-thread block (s_warp: 8 shared words)
+__device__ __forceinline__ uint32_t block_inclusive_scan(uint32_t x, uint32_t *s_warp)
+{
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    x = warp_inclusive_scan(x);
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t t = lane < 8 ? s_warp[lane] : 0;
+#pragma unroll
+        for (int off = 1; off < 8; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, t, off);
+            if (lane >= (unsigned)off) t += y;
+        }
+        if (lane < 8) s_warp[lane] = t;
+    }
+    __syncthreads();
+    return warp ? x + s_warp[warp - 1] : x;
+}
+
 // Bounded grid-wide barrier of a cooperative launch (every block resident).
 // Returns false if the wait gave up (the caller then stops).
 constexpr uint32_t BAR_SPIN_LIMIT = 1u << 24;
@@ -597,11 +617,10 @@ __global__ void __launch_bounds__(256, 4) k_rounds(const Dev d)
 {
     __shared__ uint32_t s_stage[8][3 * SB_ENTRIES];
     __shared__ uint32_t s_cnt[8][3], s_base[3];
+    __shared__ uint32_t s_incl[256], s_o[256], s_b[256], s_scan[8];
     Ctl *ctl = d.ctl;
     volatile Ctl *vc = ctl;
     const unsigned lane = lane_id();
-    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
-    const uint64_t warp_first = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
     const uint32_t max_inner = vc->max_inner;
     unsigned long long relax = 0, frows = 0;
@@ -628,10 +647,12 @@ __global__ void __launch_bounds__(256, 4) k_rounds(const Dev d)
         // the previous round's frontier: clear its flags, count its relaxations
         relax += clear_frontier(pick3(p_in, d.flist), vc->fcnt[p_in].v, p_in, d.rec, d.rowptr);
 
-        for (uint64_t base = warp_first; base < nl; base += nthreads) {
-            // 32 listed vertices per warp: each lane reads one and consumes its
-            // snapshot and list flag (nothing else reads them in this round)
-            const uint64_t i = base + lane;
+        // chunks of 256 listed vertices per block; their (vertex, reader) pairs
+        // are spread evenly over the block's threads
+        for (uint64_t c0 = (uint64_t)blockIdx.x * 256; c0 < nl; c0 += (uint64_t)gridDim.x * 256) {
+            // each thread reads one listed vertex and consumes its snapshot and
+            // list flag (nothing else reads them in this round)
+            const uint64_t i = c0 + threadIdx.x;
             uint32_t o = 0, b = 0, len = 0;
             if (i < nl) {
                 const uint32_t u = __ldg(list + i);
@@ -643,23 +664,25 @@ __global__ void __launch_bounds__(256, 4) k_rounds(const Dev d)
                 if (SYNC) *rec_snap(d.rec + u, p_in) = 0;
                 atomicAnd(rec_flags(d.rec + u), ~CB(p_in));
             }
-            // their (vertex, reader) pairs, spread evenly over the lanes
-            const uint32_t incl = warp_inclusive_scan(len);
-            const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-            const uint32_t excl = incl - len;
-            for (uint32_t p0 = 0; p0 < total; p0 += 32) {
-                const uint32_t p = p0 + lane;
-                uint32_t src = 0; // the lane owning pair p: the number of lanes with incl <= p
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1)
-                    if (__shfl_sync(0xFFFFFFFFu, incl, src + step - 1) <= p) src += step;
-                const uint32_t ob = __shfl_sync(0xFFFFFFFFu, o, src);
-                const uint32_t bb = __shfl_sync(0xFFFFFFFFu, b, src);
-                const uint32_t eb = __shfl_sync(0xFFFFFFFFu, excl, src);
+            const uint32_t incl = block_inclusive_scan(len, s_scan);
+            s_incl[threadIdx.x] = incl;
+            s_o[threadIdx.x] = o;
+            s_b[threadIdx.x] = b - (incl - len); // reader j of pair p is rcol[s_b[owner] + p]
+            __syncthreads();
+            const uint32_t total = s_incl[255];
+            for (uint32_t p0 = 0; p0 < total; p0 += 256) {
+                const uint32_t p = p0 + threadIdx.x;
                 const bool act = p < total;
-                uint32_t w = 0, fold = FB(p_out), mold = 0xFFFFFFFFu;
+                uint32_t w = 0, ob = 0, fold = FB(p_out), mold = 0xFFFFFFFFu;
                 if (act) {
-                    w = __ldg(d.rcol + bb + (p - eb));
+                    uint32_t lo = 0, hi = 255; // the owner: first entry with s_incl > p
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (s_incl[mid] > p) hi = mid;
+                        else lo = mid + 1;
+                    }
+                    ob = s_o[lo];
+                    w = __ldg(d.rcol + s_b[lo] + p);
                     fold = atomicOr(rec_flags(d.rec + w), FB(p_out)); // both atomics in flight together
                     mold = atomicMax(d.mval + w, ob);
                 }
@@ -673,6 +696,7 @@ __global__ void __launch_bounds__(256, 4) k_rounds(const Dev d)
                 stage_append<3>(st, 1, raised && !(cold & CB(p_out)), w, dst, ctr);
                 stage_append<3>(st, 2, raised && mold == 0, w, dst, ctr);
             }
+            __syncthreads(); // before the shared arrays are refilled
         }
         stage_flush_block<3>(st, s_cnt, s_base, dst, ctr);
         if (lead && timed_out(vc)) vc->stop_req.v = 1;
