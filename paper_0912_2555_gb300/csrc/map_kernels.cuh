@@ -682,7 +682,8 @@ __global__ void __launch_bounds__(256, 4) k_rounds(const Dev d)
                         else lo = mid + 1;
                     }
                     ob = s_o[lo];
-                    w = __ldg(d.rcol + s_b[lo] + p);
+                    const uint32_t j = s_b[lo] + p; // 32-bit wrap-around is intended: j = b + (p - excl)
+                    w = __ldg(d.rcol + j);
                     fold = atomicOr(rec_flags(d.rec + w), FB(p_out)); // both atomics in flight together
                     mold = atomicMax(d.mval + w, ob);
                 }
