@@ -148,6 +148,41 @@ MAP_API int map_destroy(map_graph *g);
 /* map_graph_info -- n and m of a graph (either pointer may be NULL). */
 MAP_API int map_graph_info(const map_graph *g, uint32_t *n, uint64_t *m);
 
+/*
+ * map_run_static -- one MAP run on a small graph without allocating anything.
+ *
+ * (The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory while they run -- code issuing work on a stream
+ * that is being captured into a CUDA graph, where cudaMalloc is not allowed;
+ * plug-ins whose host application owns the whole device budget; real-time
+ * loops that must never enter an allocator.)
+ *
+ * Computes exactly what map_create + map_run + map_destroy compute on the same
+ * arguments, with the same kernels, but every piece of work space lives in one
+ * file-scope device array of MAP_STATIC_SCRATCH_BYTES (about 7.8 MiB) that each
+ * GPU which loads this library holds until the process exits.  No cudaMalloc,
+ * cudaFree, cudaMallocHost or other allocating call is made.
+ *   n <= MAP_STATIC_MAX_N vertices and m = rowptr[n] <= MAP_STATIC_MAX_M edges;
+ *   larger graphs are rejected with MAP_ERR_ARG and a message naming the limit.
+ *   rowptr, colidx, acc_bits, map_out: as for map_create / map_run, host or
+ *   device memory; the inputs are copied into the array on every call.
+ *   opts: as for map_run, except that traces and MAP_FLAG_PROFILE are refused
+ *   (MAP_ERR_ARG); res: as for map_run (device_ms stays 0).
+ *   cuda_stream: the stream all work is issued on; the call returns when the
+ *   result is known.
+ * The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  Every call on a device shares the one array and
+ * overwrites what the previous call left there, so calls that overlap on the
+ * GPU (from several host threads, or on several streams) race and must be
+ * serialised by the caller.
+ */
+#define MAP_STATIC_MAX_N 65536u
+#define MAP_STATIC_MAX_M 524288u
+#define MAP_STATIC_SCRATCH_BYTES 8163584u
+MAP_API int map_run_static(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const uint32_t *acc_bits,
+                           const map_opts *opts, map_result *res, uint32_t *map_out, void *cuda_stream);
+
 /* map_last_error -- message of the calling thread's last failed call ("" if none). */
 MAP_API const char *map_last_error(void);
 

@@ -30,7 +30,9 @@ STATUS_NAMES = ["MAP_OK", "MAP_ERR_ARG", "MAP_ERR_CSR", "MAP_ERR_OOM", "MAP_ERR_
                 "MAP_ERR_LIMIT", "MAP_ERR_NOT_READY", "MAP_ERR_BUSY"]
 
 # exported symbols of include/map.h (checked by the tests)
-EXPORTS = ["map_create", "map_run", "map_destroy", "map_graph_info", "map_last_error"]
+EXPORTS = ["map_create", "map_run", "map_destroy", "map_graph_info", "map_last_error", "map_run_static"]
+MAP_STATIC_MAX_N = 65536
+MAP_STATIC_MAX_M = 524288
 
 TRACE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32),
                             ctypes.c_uint32, ctypes.c_uint32)
@@ -95,7 +97,8 @@ def load(path: str = LIB_PATH):
     lib.map_destroy.argtypes = [vp]
     lib.map_graph_info.argtypes = [vp, ctypes.POINTER(u32), ctypes.POINTER(ctypes.c_uint64)]
     lib.map_last_error.restype = ctypes.c_char_p
-    for f in ("map_create", "map_run", "map_destroy", "map_graph_info"):
+    lib.map_run_static.argtypes = [u32, vp, vp, vp, ctypes.POINTER(MapOpts), ctypes.POINTER(MapResult), vp, vp]
+    for f in ("map_create", "map_run", "map_destroy", "map_graph_info", "map_run_static"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -198,6 +201,36 @@ def map_run(handle, sched: int = MAP_SCHED_SYNC, max_outer: int = 0, max_inner: 
                      bool(res.inner_canonical), res.relaxations, res.edges_total, res.device_ms, res.dense_ms,
                      res.dense_launches, res.accepting_left, res.launches, res.round_ms, res.check_ms,
                      res.frontier_rows, tr)
+
+
+def map_run_static(n: int, rowptr, colidx, acc_bits, sched: int = MAP_SCHED_SYNC, max_outer: int = 0,
+                   max_inner: int = 0, map_out=None, stream=None, rounds_cap: int = 4096,
+                   allow_limit: bool = False) -> RunResult:
+    """One MAP run without any allocation (small graphs only; see include/map.h).
+
+    For callers that cannot allocate device memory at run time; the library's work space is
+    one fixed device array shared by every call on a device, so calls must not overlap."""
+    lib = load()
+    rp, k1 = _ptr(rowptr)
+    ci, k2 = _ptr(colidx)
+    ab, k3 = _ptr(acc_bits)
+    opts = MapOpts()
+    opts.sched, opts.max_outer, opts.max_inner = sched, max_outer, max_inner
+    rounds = np.zeros(max(rounds_cap, 1), dtype=np.uint32)
+    opts.rounds_out = rounds.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+    opts.rounds_cap = rounds_cap
+    res = MapResult()
+    out_ptr = None
+    if map_out is not None:
+        out_ptr = map_out.data_ptr() if hasattr(map_out, "data_ptr") else map_out.ctypes.data
+    rc = lib.map_run_static(n, rp, ci, ab, ctypes.byref(opts), ctypes.byref(res), out_ptr, _stream_handle(stream))
+    if rc != MAP_OK and not (allow_limit and rc == MAP_ERR_LIMIT):
+        raise MapError(rc, "map_run_static", last_error())
+    return RunResult(rc, res.verdict, res.witness, res.outer_iters,
+                     [int(x) for x in rounds[:min(res.outer_iters, rounds_cap)]], res.inner_iters,
+                     bool(res.inner_canonical), res.relaxations, res.edges_total, res.device_ms, res.dense_ms,
+                     res.dense_launches, res.accepting_left, res.launches, res.round_ms, res.check_ms,
+                     res.frontier_rows, [])
 
 
 def pack_bits(flags) -> np.ndarray:

@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <new>
 #include <string>
 #include <vector>
@@ -622,3 +623,245 @@ int map_run(map_graph *g, const map_opts *opts_in, map_result *res, uint32_t *ma
 }
 
 } // extern "C"
+
+// ============================================================================
+// map_run_static: a whole MAP run that allocates nothing.
+//
+// Some callers cannot allocate device memory at run time: code that runs while
+// its stream is being captured into a CUDA graph (cudaMalloc is not allowed
+// during capture), host applications that hand a fixed device budget to their
+// plug-ins and own every allocation themselves, and real-time loops that must
+// not call into the allocator.  For graphs up to MAP_STATIC_MAX_N vertices and
+// MAP_STATIC_MAX_M edges, map_run_static keeps all of its work space in the
+// file-scope device array below, which every GPU that loads this library holds
+// until the process exits, and it calls no cudaMalloc, cudaFree or allocating
+// routine.  It runs the same kernels as map_run, stepped from the host.
+// ============================================================================
+
+namespace {
+
+constexpr uint64_t ST_MAX_N = MAP_STATIC_MAX_N;
+constexpr uint64_t ST_MAX_M = MAP_STATIC_MAX_M;
+constexpr uint64_t ST_MAX_W = (ST_MAX_N + 31) / 32;
+constexpr uint64_t ST_HIST = 4096;
+constexpr uint64_t st_pad(uint64_t words) { return (words + 63) & ~uint64_t(63); } // 256-byte pieces
+// word offsets of the pieces of the scratch array
+constexpr uint64_t ST_CTL = 0;
+constexpr uint64_t ST_ROWPTR = ST_CTL + st_pad((sizeof(Ctl) + 3) / 4);
+constexpr uint64_t ST_COLIDX = ST_ROWPTR + st_pad(ST_MAX_N + 5);
+constexpr uint64_t ST_RROWPTR = ST_COLIDX + st_pad(ST_MAX_M + 4);
+constexpr uint64_t ST_RCOL = ST_RROWPTR + st_pad(ST_MAX_N + 5);
+constexpr uint64_t ST_ACC0 = ST_RCOL + st_pad(ST_MAX_M + 4);
+constexpr uint64_t ST_ACC = ST_ACC0 + st_pad(ST_MAX_W + 4);
+constexpr uint64_t ST_MVAL = ST_ACC + st_pad(ST_MAX_W + 4);
+constexpr uint64_t ST_LIST = ST_MVAL + st_pad(ST_MAX_N + 4);
+constexpr uint64_t ST_FLIST = ST_LIST + st_pad(3 * ST_MAX_N);
+constexpr uint64_t ST_REC = ST_FLIST + st_pad(3 * ST_MAX_N);
+constexpr uint64_t ST_TOUCHED = ST_REC + st_pad(4 * ST_MAX_N);
+constexpr uint64_t ST_XBUF = ST_TOUCHED + st_pad(ST_MAX_N);
+constexpr uint64_t ST_HISTW = ST_XBUF + st_pad(ST_MAX_N);
+constexpr uint64_t ST_SUMS = ST_HISTW + st_pad(ST_HIST);
+constexpr uint64_t ST_WORDS = ST_SUMS + st_pad((ST_MAX_N + 1 + 1023) / 1024 + 4);
+static_assert(ST_WORDS * 4 == MAP_STATIC_SCRATCH_BYTES, "MAP_STATIC_SCRATCH_BYTES in map.h is out of date");
+
+// The work space of map_run_static.  In host code this name is only a host-side
+// stand-in: kernels get the device address found by cudaGetSymbolAddress.
+static __device__ __align__(256) uint32_t g_static_scratch[ST_WORDS];
+
+constexpr int ST_MAX_DEVICES = 64;
+std::atomic<uint32_t *> g_static_ptr[ST_MAX_DEVICES];
+
+// the scratch array's device address on the current device (resolved once per device)
+int static_scratch(uint32_t **out)
+{
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= ST_MAX_DEVICES) return fail(MAP_ERR_ARG, "map_run_static: device %d not supported", dev);
+    uint32_t *p = g_static_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        void *addr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&addr, g_static_scratch);
+        if (e != cudaSuccess || !addr) {
+            cudaGetLastError();
+            return fail(MAP_ERR_CUDA, "map_run_static: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        }
+        p = static_cast<uint32_t *>(addr);
+        g_static_ptr[dev].store(p, std::memory_order_release);
+    }
+    *out = p;
+    return MAP_OK;
+}
+
+// inclusive scan of at most ST_MAX_N + 1 words: two levels, tile sums in the scratch
+int static_scan(uint32_t *x, uint64_t len, uint32_t *sums, cudaStream_t s)
+{
+    if (len <= 1) return MAP_OK;
+    const uint64_t tiles = (len + 1023) / 1024;
+    mapk::k_scan_tiles<<<(unsigned)tiles, 1024, 0, s>>>(x, len, tiles > 1 ? sums : nullptr);
+    CK(cudaGetLastError());
+    if (tiles > 1) { // tiles <= 1024: one tile of sums
+        mapk::k_scan_tiles<<<1, 1024, 0, s>>>(sums, tiles, nullptr);
+        mapk::k_scan_add<<<(unsigned)tiles, 1024, 0, s>>>(x, len, sums);
+        CK(cudaGetLastError());
+    }
+    return MAP_OK;
+}
+
+int static_read_ctl(Ctl *h, const Ctl *d, cudaStream_t s)
+{
+    CK(cudaMemcpyAsync(h, d, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return MAP_OK;
+}
+
+} // namespace
+
+extern "C" int map_run_static(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const uint32_t *acc_bits,
+                              const map_opts *opts_in, map_result *res, uint32_t *map_out, void *cuda_stream)
+{
+    g_err.clear();
+    if (!res) return fail(MAP_ERR_ARG, "map_run_static: result is NULL");
+    if (n == 0 || n > ST_MAX_N)
+        return fail(MAP_ERR_ARG, "map_run_static: n = %u is outside [1, %llu] (MAP_STATIC_MAX_N); use map_create/map_run",
+                    n, (unsigned long long)ST_MAX_N);
+    if (!rowptr || !acc_bits) return fail(MAP_ERR_ARG, "map_run_static: rowptr and acc_bits are required");
+    map_opts opts;
+    memset(&opts, 0, sizeof opts);
+    if (opts_in) opts = *opts_in;
+    if (opts.sched > MAP_SCHED_ASYNC) return fail(MAP_ERR_ARG, "map_run_static: unknown schedule %u", opts.sched);
+    if (opts.trace || (opts.flags & MAP_FLAG_PROFILE))
+        return fail(MAP_ERR_ARG, "map_run_static: traces and profiling are not offered here");
+    const bool sync_sched = opts.sched == MAP_SCHED_SYNC;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    memset(res, 0, sizeof *res);
+
+    uint32_t *base = nullptr;
+    int rc = static_scratch(&base);
+    if (rc) return rc;
+    // m = rowptr[n], from host or device memory
+    uint32_t m32 = 0, r0 = 0;
+    CK(cudaMemcpyAsync(&m32, rowptr + n, 4, cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(&r0, rowptr, 4, cudaMemcpyDefault, s));
+    CK(cudaStreamSynchronize(s));
+    const uint64_t m = m32;
+    if (r0 != 0) return fail(MAP_ERR_CSR, "map_run_static: rowptr[0] = %u, expected 0", r0);
+    if (m > ST_MAX_M)
+        return fail(MAP_ERR_ARG, "map_run_static: m = %llu edges exceeds %llu (MAP_STATIC_MAX_M); use map_create/map_run",
+                    (unsigned long long)m, (unsigned long long)ST_MAX_M);
+    if (m > 0 && !colidx) return fail(MAP_ERR_ARG, "map_run_static: colidx is NULL but m = %llu", (unsigned long long)m);
+
+    // the pieces of the scratch array (every call reuses them)
+    Ctl *ctl = reinterpret_cast<Ctl *>(base + ST_CTL);
+    map_graph g; // a view of the scratch in the layout the launch helpers expect
+    g.n = n;
+    g.m = m;
+    g.words = (n + 31) / 32;
+    g.stream = s;
+    g.G = pick_group(n, m);
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&g.sms, cudaDevAttrMultiProcessorCount, dev));
+    int occ = 0, occ_r = 0, occ_a = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mapk::k_dense, mapk::DT_THREADS, mapk::DT_SMEM));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_r, mapk::k_rounds<true>, 256, 0));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, mapk::k_rounds<false>, 256, 0));
+    occ = std::max(occ, 1);
+    occ_r = std::max(1, std::min(occ_r, occ_a));
+    const uint64_t ntiles = ((uint64_t)n + mapk::WT_ROWS - 1) / mapk::WT_ROWS;
+    g.dense_grid = (int)std::min<uint64_t>((ntiles + mapk::WT_WARPS - 1) / mapk::WT_WARPS, (uint64_t)g.sms * occ);
+    g.rounds_grid = (int)std::min<uint64_t>(((uint64_t)n + 255) / 256, (uint64_t)g.sms * occ_r);
+    g.check_grid = (int)std::min<uint64_t>(((uint64_t)n + 255) / 256, (uint64_t)g.sms * 4);
+    g.rowptr = base + ST_ROWPTR;
+    g.colidx = base + ST_COLIDX;
+    g.rrowptr = base + ST_RROWPTR;
+    g.rcol = base + ST_RCOL;
+    g.acc0 = base + ST_ACC0;
+    g.acc = base + ST_ACC;
+    g.mval = base + ST_MVAL;
+    g.list = base + ST_LIST;
+    g.flist = base + ST_FLIST;
+    g.rec = reinterpret_cast<uint4 *>(base + ST_REC);
+    g.touched = base + ST_TOUCHED;
+    g.xbuf = base + ST_XBUF;
+    g.hist = base + ST_HISTW;
+    g.hist_cap = (uint32_t)ST_HIST;
+    g.ctl = ctl;
+    uint32_t *sums = base + ST_SUMS;
+    const uint32_t W = g.words;
+
+    // inputs into the scratch; everything that must start at zero is cleared
+    // (the array keeps the previous call's contents)
+    CK(cudaMemcpyAsync(g.rowptr, rowptr, ((size_t)n + 1) * 4, cudaMemcpyDefault, s));
+    if (m) CK(cudaMemcpyAsync(g.colidx, colidx, m * 4, cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(g.acc, acc_bits, (size_t)W * 4, cudaMemcpyDefault, s));
+    CK(cudaMemsetAsync(g.colidx + m, 0, 16, s));
+    CK(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+    CK(cudaMemsetAsync(g.mval, 0, ((size_t)n + 4) * 4, s));
+    CK(cudaMemsetAsync(g.rec, 0, (size_t)n * 16, s));
+    CK(cudaMemsetAsync(g.rrowptr, 0, ((size_t)n + 1) * 4, s));
+    mapk::k_validate<<<grid_for(&g, m > n ? m : n, 1), 256, 0, s>>>(n, g.rowptr, m, g.colidx, &ctl->bad);
+    mapk::k_acc_init<<<grid_for(&g, W, 1), 256, 0, s>>>(n, g.acc, g.acc0, &ctl->elim.v);
+    CK(cudaGetLastError());
+    Ctl h;
+    if ((rc = static_read_ctl(&h, ctl, s))) return rc;
+    if (h.bad) return fail(MAP_ERR_CSR, "map_run_static: invalid CSR (decreasing rowptr or colidx >= n)");
+    const uint32_t nacc0 = h.elim.v;
+
+    // readers (reverse CSR): in-degree histogram, scan, scatter
+    mapk::k_indegree<<<grid_for(&g, m, 1), 256, 0, s>>>(m, g.colidx, g.rrowptr);
+    CK(cudaGetLastError());
+    if ((rc = static_scan(g.rrowptr, (uint64_t)n + 1, sums, s))) return rc;
+    CK(cudaMemcpyAsync(g.list, g.rrowptr, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+    DISPATCH_G(g.G, (mapk::k_transpose<GG><<<grid_for(&g, n, GG), 256, 0, s>>>(n, g.rowptr, g.colidx, g.list,
+                                                                             g.rcol)));
+    CK(cudaGetLastError());
+
+    // the run, stepped from the host (no graph: instantiating one would allocate)
+    const bool out_dev = map_out && is_device_ptr(map_out);
+    memset(&h, 0, sizeof h);
+    h.max_outer = opts.max_outer;
+    h.max_inner = opts.max_inner ? opts.max_inner : n + 1;
+    h.hist_cap = g.hist_cap;
+    h.m = m;
+    h.nacc0 = nacc0;
+    h.rounds_hist = g.hist;
+    h.out = out_dev ? map_out : g.xbuf;
+    h.use_graph = 0;
+    h.timeout_ns = (uint64_t)(opts.timeout_ms ? opts.timeout_ms : 120000u) * 1000000ull;
+    h.witness.v = mapk::NONE;
+    CK(cudaMemcpyAsync(ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(g.acc, g.acc0, (size_t)W * 4, cudaMemcpyDeviceToDevice, s));
+    const mapk::Handles none{};
+    mapk::k_run_begin<<<1, 32, 0, s>>>(ctl, none);
+    CK(cudaGetLastError());
+    if ((rc = static_read_ctl(&h, ctl, s))) return rc;
+    uint64_t launches = 1;
+    while (h.outer_go) {
+        if ((rc = launch_dense(&g, s, none)) || (rc = launch_rounds(&g, s, sync_sched)) ||
+            (rc = launch_check(&g, s, none)))
+            return rc;
+        launches += 3;
+        if ((rc = static_read_ctl(&h, ctl, s))) return rc;
+    }
+    if ((rc = launch_export(&g, s, nullptr))) return rc;
+    launches += 1;
+    if ((rc = static_read_ctl(&h, ctl, s))) return rc;
+    res->verdict = h.verdict ? MAP_CYCLE : MAP_NO_CYCLE;
+    res->witness = h.verdict ? h.witness.v : MAP_NONE;
+    res->outer_iters = h.outer;
+    res->inner_canonical = sync_sched ? 1 : 0;
+    res->inner_iters = h.inner_total;
+    res->relaxations = h.relax.v;
+    res->edges_total = m * (uint64_t)h.outer;
+    res->accepting_left = h.nacc;
+    res->launches = launches;
+    res->frontier_rows = h.frontier_rows.v;
+    const uint32_t nh = std::min<uint32_t>(h.outer, g.hist_cap);
+    if (opts.rounds_out && nh)
+        CK(cudaMemcpyAsync(opts.rounds_out, g.hist, (size_t)std::min(nh, opts.rounds_cap) * 4, cudaMemcpyDefault, s));
+    if (map_out && !out_dev) CK(cudaMemcpyAsync(map_out, g.xbuf, (size_t)n * 4, cudaMemcpyDefault, s));
+    CK(cudaStreamSynchronize(s));
+    if (h.status == mapk::ST_LIMIT) return fail(MAP_ERR_LIMIT, "map_run_static: max_outer or max_inner reached");
+    if (h.status == mapk::ST_TIMEOUT) return fail(MAP_ERR_TIMEOUT, "map_run_static: stopped after the timeout");
+    return MAP_OK;
+}
