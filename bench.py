@@ -221,7 +221,7 @@ def main():
     dense_launches = sum(r.dense_launches for r in prof)
     dense_ms = sum(r.dense_ms for r in prof)
     words = (g.n + 31) // 32
-    dense_bytes = 4 * (g.n + 1) + 4 * g.m + 4 * g.n + 4 * words
+    dense_bytes = 4 * (g.n + 1) + 4 * g.m + 4 * g.n  # rowptr + colidx (flags in bit 31) + map writes
     peaks = _peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     achieved = dense_bytes * dense_launches / (dense_ms / 1e3) / 1e9 if dense_ms > 0 else None

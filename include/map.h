@@ -159,7 +159,7 @@ MAP_API int map_graph_info(const map_graph *g, uint32_t *n, uint64_t *m);
  *
  * Computes exactly what map_create + map_run + map_destroy compute on the same
  * arguments, with the same kernels, but every piece of work space lives in one
- * file-scope device array of MAP_STATIC_SCRATCH_BYTES (about 7.8 MiB) that each
+ * file-scope device array of MAP_STATIC_SCRATCH_BYTES (about 10 MiB) that each
  * GPU which loads this library holds until the process exits.  No cudaMalloc,
  * cudaFree, cudaMallocHost or other allocating call is made.
  *   n <= MAP_STATIC_MAX_N vertices and m = rowptr[n] <= MAP_STATIC_MAX_M edges;
@@ -179,7 +179,7 @@ MAP_API int map_graph_info(const map_graph *g, uint32_t *n, uint64_t *m);
  */
 #define MAP_STATIC_MAX_N 65536u
 #define MAP_STATIC_MAX_M 524288u
-#define MAP_STATIC_SCRATCH_BYTES 8163584u
+#define MAP_STATIC_SCRATCH_BYTES 10523648u
 MAP_API int map_run_static(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const uint32_t *acc_bits,
                            const map_opts *opts, map_result *res, uint32_t *map_out, void *cuda_stream);
 

@@ -82,6 +82,8 @@ struct map_graph {
     int check_grid = 0;  // blocks of the self-map / elimination kernel
     cudaStream_t stream = nullptr;
     uint32_t *rowptr = nullptr, *colidx = nullptr, *rrowptr = nullptr, *rcol = nullptr;
+    uint32_t *rpos = nullptr; // positions in colidx of the reader entries
+    uint32_t *elog = nullptr; // vertices eliminated in the current run
     uint32_t *acc0 = nullptr, *acc = nullptr, *mval = nullptr;
     uint32_t *list = nullptr;  // 3n: vertices changed in a round, by round mod 3
     uint32_t *flist = nullptr; // 3n: frontier rows of a round, by round mod 3
@@ -111,8 +113,8 @@ void free_graph(map_graph *g)
         if (g->exec[i]) cudaGraphExecDestroy(g->exec[i]);
         if (g->graph[i]) cudaGraphDestroy(g->graph[i]);
     }
-    void *dev[] = {g->rowptr, g->colidx, g->rrowptr, g->rcol, g->acc0, g->acc,  g->mval,
-                   g->list,   g->flist,  g->rec,     g->touched, g->xbuf, g->hist, g->ctl};
+    void *dev[] = {g->rowptr, g->colidx, g->rrowptr, g->rcol,    g->rpos, g->elog, g->acc0, g->acc,
+                   g->mval,   g->list,   g->flist,   g->rec,     g->touched, g->xbuf, g->hist, g->ctl};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (g->h_ctl) cudaFreeHost(g->h_ctl);
@@ -183,6 +185,9 @@ mapk::Dev dev_of(const map_graph *g)
     d.colidx = g->colidx;
     d.rrowptr = g->rrowptr;
     d.rcol = g->rcol;
+    d.rpos = g->rpos;
+    d.colidx_w = g->colidx;
+    d.elog = g->elog;
     d.acc = g->acc;
     d.mval = g->mval;
     const size_t n = g->n;
@@ -234,6 +239,14 @@ int launch_check(map_graph *g, cudaStream_t s, mapk::Handles hd)
 int launch_reset(map_graph *g, cudaStream_t s)
 {
     CK(cudaMemcpyAsync(g->acc, g->acc0, (size_t)g->words * 4, cudaMemcpyDeviceToDevice, s));
+    return MAP_OK;
+}
+
+// end of a run: the eliminated vertices get their flag back in the matrix entries
+int launch_restore(map_graph *g, cudaStream_t s)
+{
+    mapk::k_restore<<<g->check_grid, 256, 0, s>>>(dev_of(g));
+    CK(cudaGetLastError());
     return MAP_OK;
 }
 
@@ -295,6 +308,7 @@ int build_run_graph(map_graph *g, int sched)
     if ((rc = launch_reset(g, cs)) == MAP_OK) {
         mapk::k_run_begin<<<1, 32, 0, cs>>>(g->ctl, hd);
         rc = add_while(cs, hd.outer, &outer_body);
+        if (rc == MAP_OK) rc = launch_restore(g, cs);
         if (rc == MAP_OK) rc = launch_export(g, cs, nullptr);
     }
     {
@@ -394,7 +408,8 @@ int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const
     int rc = MAP_OK;
     const uint64_t W = g->words;
     if ((rc = alloc(&g->rowptr, (uint64_t)n + 1)) || (rc = alloc(&g->colidx, m)) ||
-        (rc = alloc(&g->rrowptr, (uint64_t)n + 1)) || (rc = alloc(&g->rcol, m)) || (rc = alloc(&g->acc0, W)) ||
+        (rc = alloc(&g->rrowptr, (uint64_t)n + 1)) || (rc = alloc(&g->rcol, m)) || (rc = alloc(&g->rpos, m)) ||
+        (rc = alloc(&g->elog, n)) || (rc = alloc(&g->acc0, W)) ||
         (rc = alloc(&g->acc, W)) || (rc = alloc(&g->mval, n)) || (rc = alloc(&g->list, 3 * (uint64_t)n)) ||
         (rc = alloc(&g->flist, 3 * (uint64_t)n)) || (rc = alloc((uint32_t **)&g->rec, 4 * (uint64_t)n)) ||
         (rc = alloc(&g->touched, n)) || (rc = alloc(&g->xbuf, n)) ||
@@ -473,7 +488,9 @@ int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const
         return rc;
     }
     DISPATCH_G(g->G, (mapk::k_transpose<GG><<<grid_for(g, n, GG), 256, 0, s>>>(n, g->rowptr, g->colidx, g->list,
-                                                                              g->rcol)));
+                                                                              g->rcol, g->rpos)));
+    // the accepting flag of each target into bit 31 of its entry (restored after every run)
+    mapk::k_pack_flags<<<grid_for(g, m, 1), 256, 0, s>>>(m, g->colidx, g->acc0);
     if ((rc = ck(cudaGetLastError(), "transpose")) || (rc = ck(cudaStreamSynchronize(s), "create sync"))) {
         free_graph(g);
         return rc;
@@ -581,6 +598,7 @@ int map_run(map_graph *g, const map_opts *opts_in, map_result *res, uint32_t *ma
                 check_ms += ms;
             }
         }
+        if ((rc = launch_restore(g, s))) return rc;
         if ((rc = launch_export(g, s, nullptr))) return rc;
         CK(cudaEventRecord(g->ev[1], s));
         if ((rc = read_ctl(g))) return rc;
@@ -602,8 +620,8 @@ int map_run(map_graph *g, const map_opts *opts_in, map_result *res, uint32_t *ma
     res->frontier_rows = c.frontier_rows.v;
     res->check_ms = check_ms;
     res->accepting_left = c.nacc;
-    // kernel launches: run_begin, export, and per outer iteration dense, rounds, check
-    res->launches = 2 + 3ull * c.outer;
+    // kernel launches: run_begin, restore, export, and per outer iteration dense, rounds, check
+    res->launches = 3 + 3ull * c.outer;
     const uint32_t nh = std::min<uint32_t>(c.outer, g->hist_cap);
     if (opts.rounds_out && nh) {
         CK(cudaMemcpyAsync(g->h_hist, g->hist, (size_t)nh * 4, cudaMemcpyDeviceToHost, s));
@@ -651,7 +669,9 @@ constexpr uint64_t ST_ROWPTR = ST_CTL + st_pad((sizeof(Ctl) + 3) / 4);
 constexpr uint64_t ST_COLIDX = ST_ROWPTR + st_pad(ST_MAX_N + 5);
 constexpr uint64_t ST_RROWPTR = ST_COLIDX + st_pad(ST_MAX_M + 4);
 constexpr uint64_t ST_RCOL = ST_RROWPTR + st_pad(ST_MAX_N + 5);
-constexpr uint64_t ST_ACC0 = ST_RCOL + st_pad(ST_MAX_M + 4);
+constexpr uint64_t ST_RPOS = ST_RCOL + st_pad(ST_MAX_M + 4);
+constexpr uint64_t ST_ELOG = ST_RPOS + st_pad(ST_MAX_M + 4);
+constexpr uint64_t ST_ACC0 = ST_ELOG + st_pad(ST_MAX_N + 4);
 constexpr uint64_t ST_ACC = ST_ACC0 + st_pad(ST_MAX_W + 4);
 constexpr uint64_t ST_MVAL = ST_ACC + st_pad(ST_MAX_W + 4);
 constexpr uint64_t ST_LIST = ST_MVAL + st_pad(ST_MAX_N + 4);
@@ -775,6 +795,8 @@ extern "C" int map_run_static(uint32_t n, const uint32_t *rowptr, const uint32_t
     g.colidx = base + ST_COLIDX;
     g.rrowptr = base + ST_RROWPTR;
     g.rcol = base + ST_RCOL;
+    g.rpos = base + ST_RPOS;
+    g.elog = base + ST_ELOG;
     g.acc0 = base + ST_ACC0;
     g.acc = base + ST_ACC;
     g.mval = base + ST_MVAL;
@@ -813,7 +835,8 @@ extern "C" int map_run_static(uint32_t n, const uint32_t *rowptr, const uint32_t
     if ((rc = static_scan(g.rrowptr, (uint64_t)n + 1, sums, s))) return rc;
     CK(cudaMemcpyAsync(g.list, g.rrowptr, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
     DISPATCH_G(g.G, (mapk::k_transpose<GG><<<grid_for(&g, n, GG), 256, 0, s>>>(n, g.rowptr, g.colidx, g.list,
-                                                                             g.rcol)));
+                                                                             g.rcol, g.rpos)));
+    mapk::k_pack_flags<<<grid_for(&g, m, 1), 256, 0, s>>>(m, g.colidx, g.acc);
     CK(cudaGetLastError());
 
     // the run, stepped from the host (no graph: instantiating one would allocate)
@@ -843,8 +866,8 @@ extern "C" int map_run_static(uint32_t n, const uint32_t *rowptr, const uint32_t
         launches += 3;
         if ((rc = static_read_ctl(&h, ctl, s))) return rc;
     }
-    if ((rc = launch_export(&g, s, nullptr))) return rc;
-    launches += 1;
+    if ((rc = launch_restore(&g, s)) || (rc = launch_export(&g, s, nullptr))) return rc;
+    launches += 2;
     if ((rc = static_read_ctl(&h, ctl, s))) return rc;
     res->verdict = h.verdict ? MAP_CYCLE : MAP_NO_CYCLE;
     res->witness = h.verdict ? h.witness.v : MAP_NONE;

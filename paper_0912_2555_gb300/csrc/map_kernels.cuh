@@ -2,9 +2,16 @@
 //
 // Device layout of one graph (all u32 unless noted):
 //   rowptr[n+1], colidx[m]   the CSR handed in: row v = successors of v in G, i.e.
-//                            the pull matrix of the transposed graph;
+//                            the pull matrix of the transposed graph.  The
+//                            library's copy of colidx carries the accepting flag
+//                            of each target in bit 31 (ids are < 2^31 - 1), so the
+//                            dense round streams the matrix without gathers;
 //   rrowptr[n+1], rcol[m]    its transpose: rcol[rrowptr[u] ..] are the readers
-//                            of u (the rows that contain u);
+//                            of u (the rows that contain u), and rpos[..] the
+//                            positions in colidx of those entries (to update the
+//                            flag of u when u is eliminated);
+//   elog[n]                  vertices eliminated in this run (their flags are
+//                            restored at the end of the run);
 //   acc[W], W = ceil(n/32)   the current accepting set, LSB-first bitmap;
 //   mval[n]                  enc(map(v)): 0 = no value, u + 1 = vertex u;
 //   list[3][n]               vertices whose value changed in a round, by round mod 3;
@@ -55,6 +62,7 @@ struct Ctl {
     Cnt32 done;            // last-block ticket
     Cnt32 elim;            // accepting vertices eliminated in this outer iteration
     Cnt32 witness;         // smallest self-mapped vertex of the last iteration
+    Cnt32 ecnt;            // |elog|
     Cnt64 relax;           // edges examined (canonical count of the synchronous schedule)
     Cnt64 frontier_rows;   // frontier rows summed over the push rounds
     Cnt32 bar_count;       // grid barrier of k_rounds: arrivals
@@ -90,8 +98,10 @@ struct Handles {
 // device pointers of one graph, passed by value to the loop kernels
 struct Dev {
     uint32_t n, words;
-    const uint32_t *rowptr, *colidx, *rrowptr, *rcol;
+    const uint32_t *rowptr, *colidx, *rrowptr, *rcol, *rpos;
+    uint32_t *colidx_w; // the same array as colidx, for the flag updates
     uint32_t *acc, *mval;
+    uint32_t *elog;
     uint32_t *list[3], *flist[3];
     uint4 *rec; // .x / .y / .z: snap[0..2]; .w: flags
     uint32_t *touched;
@@ -377,15 +387,14 @@ __global__ void k_run_begin(Ctl *c, Handles hd)
 // ------------------------------------------------------------ dense round --
 //
 // Round 1 of an outer iteration relaxes every row from "no value" everywhere,
-// so the value u offers is u + 1 if u is accepting and 0 otherwise: only the
-// accepting bitmap is gathered.
+// so the value u offers is u + 1 if u is accepting and 0 otherwise -- and the
+// flag is bit 31 of the matrix entry itself, so the round is a pure stream.
 //
 // Each warp owns tiles of WT_ROWS consecutive rows, with no block-wide phase:
 // the tile's rowptr slice (fetched one tile ahead into registers) goes to a
 // warp-private shared slice; the tile's edge span is streamed with 128-bit
-// loads (WT_UNROLL per lane, then 4 * WT_UNROLL independent bitmap gathers);
-// an edge that offers a value finds its row by binary search in the slice and
-// does a shared-memory atomicMax; the tile's values are written out coalesced
+// loads (WT_UNROLL per lane in flight); an edge whose target is accepting finds
+// its row by binary search in the slice and does a shared-memory atomicMax; the tile's values are written out coalesced
 // (this also resets the previous iteration's values).  Every row that got a
 // value goes to list[1] (with its value in snap[1]) and to the touched list.
 constexpr int DT_THREADS = 256;
@@ -411,7 +420,6 @@ __global__ void __launch_bounds__(DT_THREADS, 4) k_dense(const Dev d, Handles hd
     const uint32_t n = d.n;
     const uint32_t *__restrict__ rowptr = d.rowptr;
     const uint32_t *__restrict__ colidx = d.colidx;
-    const uint32_t *__restrict__ acc = d.acc;
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
     uint32_t *rp = s_rp[warp], *best = s_best[warp];
     const uint32_t ntiles = (n + WT_ROWS - 1) / WT_ROWS;
@@ -443,29 +451,21 @@ __global__ void __launch_bounds__(DT_THREADS, 4) k_dense(const Dev d, Handles hd
                 const uint32_t idx = cs + (j * 32 + lane) * 4;
                 w[j] = idx < E1 ? __ldg(reinterpret_cast<const uint4 *>(colidx + idx)) : make_uint4(0, 0, 0, 0);
             }
-            uint32_t aw[WT_UNROLL][4];
-#pragma unroll
-            for (int j = 0; j < WT_UNROLL; ++j) {
-                aw[j][0] = __ldg(acc + (w[j].x >> 5));
-                aw[j][1] = __ldg(acc + (w[j].y >> 5));
-                aw[j][2] = __ldg(acc + (w[j].z >> 5));
-                aw[j][3] = __ldg(acc + (w[j].w >> 5));
-            }
 #pragma unroll
             for (int j = 0; j < WT_UNROLL; ++j) {
                 const uint32_t ebase = cs + (j * 32 + lane) * 4;
-                const uint32_t us[4] = {w[j].x, w[j].y, w[j].z, w[j].w};
+                const uint32_t cs4[4] = {w[j].x, w[j].y, w[j].z, w[j].w};
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const uint32_t e = ebase + k, u = us[k];
-                    if (e >= E0 && e < E1 && ((aw[j][k] >> (u & 31u)) & 1u)) {
+                    const uint32_t e = ebase + k, c = cs4[k];
+                    if ((c >> 31) && e >= E0 && e < E1) { // the target is accepting
                         uint32_t lo = 0, hi = rows; // rp[lo] <= e < rp[hi]: the row of e is the last such lo
                         while (hi - lo > 1) {
                             const uint32_t mid = (lo + hi) >> 1;
                             if (rp[mid] <= e) lo = mid;
                             else hi = mid;
                         }
-                        atomicMax(&best[lo], u + 1);
+                        atomicMax(&best[lo], (c & 0x7FFFFFFFu) + 1u);
                     }
                 }
             }
@@ -744,7 +744,12 @@ __global__ void __launch_bounds__(256) k_check(const Dev d, Handles hd)
         const uint32_t bit = 1u << (u & 31u);
         if (*(volatile uint32_t *)(d.acc + (u >> 5)) & bit) {
             const uint32_t old = atomicAnd(d.acc + (u >> 5), ~bit);
-            elim += (old & bit) ? 1u : 0u;
+            if (old & bit) { // this thread removed u: clear u's flag in the matrix entries, log u
+                elim++;
+                d.elog[atomicAdd(&ctl->ecnt.v, 1u)] = u;
+                const uint32_t b = __ldg(d.rrowptr + u), e = __ldg(d.rrowptr + u + 1);
+                for (uint32_t j = b; j < e; ++j) d.colidx_w[__ldg(d.rpos + j)] = u;
+            }
         }
     }
     block_add_min_u32(elim, wit, &ctl->elim.v, &ctl->witness.v);
@@ -760,6 +765,21 @@ __global__ void k_export(uint32_t n, const uint32_t *__restrict__ mval, const Ct
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
         out[v] = none ? NONE : __ldg(mval + v) - 1u;
+}
+
+// End of a run: give the vertices eliminated in it their accepting flag back
+// in the matrix entries (they are all accepting in the initial set).
+__global__ void __launch_bounds__(256) k_restore(const Dev d)
+{
+    Ctl *ctl = d.ctl;
+    const uint32_t ne = *(volatile uint32_t *)&ctl->ecnt.v;
+    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ne; i += nthreads) {
+        const uint32_t u = __ldg(d.elog + i);
+        const uint32_t b = __ldg(d.rrowptr + u), e = __ldg(d.rrowptr + u + 1);
+        for (uint32_t j = b; j < e; ++j) d.colidx_w[__ldg(d.rpos + j)] = u | 0x80000000u;
+    }
+    if (last_block(ctl)) ctl->ecnt.v = 0;
 }
 
 // ---------------------------------------------------------------- set-up --
@@ -821,11 +841,12 @@ __global__ void k_scan_add(uint32_t *x, uint64_t len, const uint32_t *__restrict
     if (blockIdx.x > 0 && i < len) x[i] += sums[blockIdx.x - 1];
 }
 
-// transpose scatter: the group of row w appends w to the reader list of each u in row w
+// transpose scatter: the group of row w appends w (and the entry's position) to
+// the reader list of each u in row w
 template <int G>
 __global__ void __launch_bounds__(256) k_transpose(uint32_t n, const uint32_t *__restrict__ rowptr,
                                                    const uint32_t *__restrict__ colidx, uint32_t *cursor,
-                                                   uint32_t *rcol)
+                                                   uint32_t *rcol, uint32_t *rpos)
 {
     const unsigned glane = threadIdx.x & (G - 1);
     const uint64_t groups = (uint64_t)gridDim.x * blockDim.x / G;
@@ -833,8 +854,20 @@ __global__ void __launch_bounds__(256) k_transpose(uint32_t n, const uint32_t *_
         const uint32_t b = __ldg(rowptr + w), e = __ldg(rowptr + w + 1);
         for (uint32_t i = b + glane; i < e; i += G) {
             const uint32_t u = __ldg(colidx + i);
-            rcol[atomicAdd(cursor + u, 1u)] = (uint32_t)w;
+            const uint32_t slot = atomicAdd(cursor + u, 1u);
+            rcol[slot] = (uint32_t)w;
+            rpos[slot] = i;
         }
+    }
+}
+
+// put the accepting flag of each target into bit 31 of its matrix entry
+__global__ void k_pack_flags(uint64_t m, uint32_t *colidx, const uint32_t *__restrict__ acc)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        const uint32_t u = colidx[i];
+        colidx[i] = u | ((__ldg(acc + (u >> 5)) >> (u & 31u)) << 31);
     }
 }
 
