@@ -106,7 +106,9 @@ typedef struct {
     uint64_t launches;        /* kernel launches issued by this run */
     double round_ms;          /* with MAP_FLAG_PROFILE: summed time of the rounds after the first */
     double check_ms;          /* with MAP_FLAG_PROFILE: summed time of the self-map test + elimination */
-    uint64_t frontier_rows;   /* with MAP_FLAG_PROFILE: frontier rows summed over the rounds after the first */
+    uint64_t frontier_rows;   /* frontier rows summed over the rounds after the first */
+    uint32_t status;          /* map_status of this graph's run (batched runs report one per graph) */
+    uint32_t reserved;
 } map_result;
 
 typedef struct map_graph map_graph; /* opaque: the device-resident graph and its work space */
@@ -144,6 +146,40 @@ MAP_API int map_run(map_graph *g, const map_opts *opts, map_result *res, uint32_
 
 /* map_destroy -- free the graph's device memory. NULL is accepted. */
 MAP_API int map_destroy(map_graph *g);
+
+/*
+ * Batched runs: many independent graphs solved together in one run.  The
+ * graphs are joined into one disjoint union on the device (each graph's ids
+ * are offset, which keeps its own order of accepting vertices), and one
+ * CUDA-graph launch runs MAP on all of them at once: every outer iteration is
+ * one outer iteration of each graph still running; a graph that has reached
+ * its verdict is frozen (the dense round skips its rows).  Every graph gets
+ * exactly the result it gets alone.
+ *
+ * map_batch_create -- count >= 1 graphs; graph c has ns[c] vertices, rowptrs[c]
+ *   (ns[c] + 1 entries), colidxs[c] (its own ids, < ns[c]), acc_bits[c] (as for
+ *   map_create).  Host or device pointers; the library copies them.  The union
+ *   must have < 2^31 - 1 vertices and < 2^32 edges.  Returns a handle for
+ *   map_batch_run and map_destroy (map_run refuses it).
+ */
+MAP_API int map_batch_create(uint32_t count, const uint32_t *ns, const uint32_t *const *rowptrs,
+                             const uint32_t *const *colidxs, const uint32_t *const *acc_bits, void *cuda_stream,
+                             map_graph **out);
+
+/*
+ * map_batch_run -- run all graphs of a batch.
+ *   results    count entries: graph c's result (witness in its own ids,
+ *              status = its map_status); device_ms and launches are the batch's.
+ *   map_out    optional, sum(ns) entries, host or device: the graphs' final map
+ *              vectors one after another, each in its own ids (MAP_NONE = none).
+ *   rounds_out optional host array of count * rounds_cap entries: round counts
+ *              of graph c's outer iterations at [c * rounds_cap + i] (at most
+ *              1024 per graph are kept).
+ * opts as for map_run (no trace).  Returns MAP_OK, or the first non-OK status
+ * of a graph (all results are filled in either case).
+ */
+MAP_API int map_batch_run(map_graph *g, const map_opts *opts, map_result *results, uint32_t *map_out,
+                          uint32_t *rounds_out, uint32_t rounds_cap);
 
 /* map_graph_info -- n and m of a graph (either pointer may be NULL). */
 MAP_API int map_graph_info(const map_graph *g, uint32_t *n, uint64_t *m);

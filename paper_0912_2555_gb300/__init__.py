@@ -30,7 +30,8 @@ STATUS_NAMES = ["MAP_OK", "MAP_ERR_ARG", "MAP_ERR_CSR", "MAP_ERR_OOM", "MAP_ERR_
                 "MAP_ERR_LIMIT", "MAP_ERR_NOT_READY", "MAP_ERR_BUSY"]
 
 # exported symbols of include/map.h (checked by the tests)
-EXPORTS = ["map_create", "map_run", "map_destroy", "map_graph_info", "map_last_error", "map_run_static"]
+EXPORTS = ["map_create", "map_run", "map_destroy", "map_graph_info", "map_last_error", "map_run_static",
+           "map_batch_create", "map_batch_run"]
 MAP_STATIC_MAX_N = 65536
 MAP_STATIC_MAX_M = 524288
 
@@ -70,6 +71,8 @@ class MapResult(ctypes.Structure):
         ("round_ms", ctypes.c_double),
         ("check_ms", ctypes.c_double),
         ("frontier_rows", ctypes.c_uint64),
+        ("status", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
     ]
 
 
@@ -98,7 +101,10 @@ def load(path: str = LIB_PATH):
     lib.map_graph_info.argtypes = [vp, ctypes.POINTER(u32), ctypes.POINTER(ctypes.c_uint64)]
     lib.map_last_error.restype = ctypes.c_char_p
     lib.map_run_static.argtypes = [u32, vp, vp, vp, ctypes.POINTER(MapOpts), ctypes.POINTER(MapResult), vp, vp]
-    for f in ("map_create", "map_run", "map_destroy", "map_graph_info", "map_run_static"):
+    lib.map_batch_create.argtypes = [u32, vp, vp, vp, vp, vp, ctypes.POINTER(vp)]
+    lib.map_batch_run.argtypes = [vp, ctypes.POINTER(MapOpts), ctypes.POINTER(MapResult), vp, vp, u32]
+    for f in ("map_create", "map_run", "map_destroy", "map_graph_info", "map_run_static", "map_batch_create",
+              "map_batch_run"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -231,6 +237,56 @@ def map_run_static(n: int, rowptr, colidx, acc_bits, sched: int = MAP_SCHED_SYNC
                      bool(res.inner_canonical), res.relaxations, res.edges_total, res.device_ms, res.dense_ms,
                      res.dense_launches, res.accepting_left, res.launches, res.round_ms, res.check_ms,
                      res.frontier_rows, [])
+
+
+def map_batch_create(graphs, stream=None):
+    """A batch handle for many graphs: ``graphs`` is a sequence of (n, rowptr, colidx, acc_bits)
+    with numpy arrays or CUDA tensors (see map_batch_create in include/map.h)."""
+    lib = load()
+    count = len(graphs)
+    keep = []
+    ns = np.array([int(gr[0]) for gr in graphs], dtype=np.uint32)
+    arrs = []
+    for col in (1, 2, 3):
+        ptrs = np.zeros(count, dtype=np.uint64)
+        for i, gr in enumerate(graphs):
+            p, k = _ptr(gr[col])
+            keep.append(k)
+            ptrs[i] = p or 0
+        arrs.append(ptrs)
+    h = ctypes.c_void_p()
+    rc = lib.map_batch_create(count, ns.ctypes.data, arrs[0].ctypes.data, arrs[1].ctypes.data, arrs[2].ctypes.data,
+                              _stream_handle(stream), ctypes.byref(h))
+    if rc != MAP_OK:
+        raise MapError(rc, "map_batch_create", last_error())
+    h.count = count
+    h.total_n = int(ns.sum(dtype=np.uint64))
+    return h
+
+
+def map_batch_run(handle, count: int, sched: int = MAP_SCHED_SYNC, max_outer: int = 0, max_inner: int = 0,
+                  flags: int = 0, map_out=None, rounds_cap: int = 256, allow_limit: bool = False):
+    """Run a batch; returns a list of RunResult (one per graph, ``rounds`` filled)."""
+    lib = load()
+    opts = MapOpts()
+    opts.sched, opts.max_outer, opts.max_inner, opts.flags = sched, max_outer, max_inner, flags
+    res = (MapResult * count)()
+    rounds = np.zeros(count * max(rounds_cap, 1), dtype=np.uint32)
+    out_ptr = None
+    if map_out is not None:
+        out_ptr = map_out.data_ptr() if hasattr(map_out, "data_ptr") else map_out.ctypes.data
+    rc = lib.map_batch_run(handle, ctypes.byref(opts), res, out_ptr, rounds.ctypes.data, rounds_cap)
+    if rc != MAP_OK and not (allow_limit and rc in (MAP_ERR_LIMIT, MAP_ERR_TIMEOUT)):
+        raise MapError(rc, "map_batch_run", last_error())
+    out = []
+    for c in range(count):
+        r = res[c]
+        rl = [int(x) for x in rounds[c * rounds_cap: c * rounds_cap + min(r.outer_iters, rounds_cap)]]
+        out.append(RunResult(r.status, r.verdict, r.witness, r.outer_iters, rl, r.inner_iters,
+                             bool(r.inner_canonical), r.relaxations, r.edges_total, r.device_ms, r.dense_ms,
+                             r.dense_launches, r.accepting_left, r.launches, r.round_ms, r.check_ms,
+                             r.frontier_rows, []))
+    return out
 
 
 def pack_bits(flags) -> np.ndarray:

@@ -98,6 +98,13 @@ struct map_graph {
     uint32_t *h_hist = nullptr;  // pinned mirror of hist
     uint32_t nacc0 = 0;
     cudaEvent_t ev[8] = {};
+    // batched graphs (disjoint union of several graphs; see map_batch_create)
+    uint32_t ncomp = 0;
+    uint32_t *comp = nullptr;        // graph of each union vertex
+    mapk::CompState *cs = nullptr;   // one record per graph
+    uint32_t *chist = nullptr;       // rounds per outer iteration, CH_CAP per graph
+    mapk::CompState *h_cs = nullptr; // pinned mirrors
+    uint32_t *h_chist = nullptr;
     // the whole run as one CUDA graph, per schedule (built on first use)
     cudaGraph_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
@@ -117,6 +124,11 @@ void free_graph(map_graph *g)
                    g->mval,   g->list,   g->flist,   g->rec,     g->touched, g->xbuf, g->hist, g->ctl};
     for (void *p : dev)
         if (p) cudaFree(p);
+    if (g->comp) cudaFree(g->comp);
+    if (g->cs) cudaFree(g->cs);
+    if (g->chist) cudaFree(g->chist);
+    if (g->h_cs) cudaFreeHost(g->h_cs);
+    if (g->h_chist) cudaFreeHost(g->h_chist);
     if (g->h_ctl) cudaFreeHost(g->h_ctl);
     if (g->h_stage) cudaFreeHost(g->h_stage);
     if (g->h_hist) cudaFreeHost(g->h_hist);
@@ -198,6 +210,10 @@ mapk::Dev dev_of(const map_graph *g)
     d.rec = g->rec;
     d.touched = g->touched;
     d.ctl = g->ctl;
+    d.comp = g->comp;
+    d.cs = g->cs;
+    d.chist = g->chist;
+    d.ncomp = g->ncomp;
     return d;
 }
 
@@ -252,7 +268,7 @@ int launch_restore(map_graph *g, cudaStream_t s)
 
 int launch_export(map_graph *g, cudaStream_t s, uint32_t *override_dst)
 {
-    mapk::k_export<<<g->check_grid, 256, 0, s>>>(g->n, g->mval, g->ctl, override_dst);
+    mapk::k_export<<<g->check_grid, 256, 0, s>>>(g->n, g->mval, g->ctl, override_dst, g->comp, g->cs);
     CK(cudaGetLastError());
     return MAP_OK;
 }
@@ -307,6 +323,7 @@ int build_run_graph(map_graph *g, int sched)
     GK(cudaStreamBeginCaptureToGraph(cs, top, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     if ((rc = launch_reset(g, cs)) == MAP_OK) {
         mapk::k_run_begin<<<1, 32, 0, cs>>>(g->ctl, hd);
+        if (g->comp) mapk::k_batch_begin<<<(g->ncomp + 255) / 256, 256, 0, cs>>>(dev_of(g));
         rc = add_while(cs, hd.outer, &outer_body);
         if (rc == MAP_OK) rc = launch_restore(g, cs);
         if (rc == MAP_OK) rc = launch_export(g, cs, nullptr);
@@ -352,33 +369,19 @@ int map_graph_info(const map_graph *g, uint32_t *n, uint64_t *m)
     return MAP_OK;
 }
 
-int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const uint32_t *acc_bits,
-               void *cuda_stream, map_graph **out)
+} // extern "C"
+
+namespace {
+
+// Allocate and prepare a graph of n vertices and m edges.  `upload(g, &acc)`
+// fills g->rowptr (n + 1 words) and g->colidx (m words) on stream s and sets acc
+// to a device bitmap of the accepting vertices; it may also set up the batch
+// fields.  Then: validation, accepting set, readers (reverse CSR), flags.
+template <class Upload>
+int create_graph(uint32_t n, uint64_t m, cudaStream_t s, const char *who, Upload upload, map_graph **out)
 {
-    g_err.clear();
-    if (!out) return fail(MAP_ERR_ARG, "map_create: out is NULL");
-    *out = nullptr;
-    if (n == 0 || n >= 0x7FFFFFFFu) return fail(MAP_ERR_ARG, "map_create: n = %u out of range [1, 2^31-1)", n);
-    if (!rowptr || !acc_bits) return fail(MAP_ERR_ARG, "map_create: rowptr and acc_bits are required");
-    cudaStream_t s = (cudaStream_t)cuda_stream;
-
-    // rowptr[0] and rowptr[n] (m) are needed on the host to size the copies
-    uint32_t ends[2];
-    const bool rp_dev = is_device_ptr(rowptr);
-    if (rp_dev) {
-        CK(cudaMemcpyAsync(&ends[0], rowptr, 4, cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(&ends[1], rowptr + n, 4, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-    } else {
-        ends[0] = rowptr[0];
-        ends[1] = rowptr[n];
-    }
-    if (ends[0] != 0) return fail(MAP_ERR_CSR, "map_create: rowptr[0] = %u, expected 0", ends[0]);
-    const uint64_t m = ends[1];
-    if (m > 0 && !colidx) return fail(MAP_ERR_ARG, "map_create: colidx is NULL but m = %llu", (unsigned long long)m);
-
     map_graph *g = new (std::nothrow) map_graph;
-    if (!g) return fail(MAP_ERR_OOM, "map_create: host allocation failed");
+    if (!g) return fail(MAP_ERR_OOM, "%s: host allocation failed", who);
     g->n = n;
     g->m = m;
     g->words = (n + 31) / 32;
@@ -420,7 +423,7 @@ int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const
     auto ck = [&](cudaError_t e, const char *what) -> int {
         if (e == cudaSuccess) return MAP_OK;
         cudaGetLastError();
-        return fail(e == cudaErrorMemoryAllocation ? MAP_ERR_OOM : MAP_ERR_CUDA, "map_create: %s: %s", what,
+        return fail(e == cudaErrorMemoryAllocation ? MAP_ERR_OOM : MAP_ERR_CUDA, "%s: %s: %s", who, what,
                     cudaGetErrorString(e));
     };
     if ((rc = ck(cudaMalloc((void **)&g->ctl, sizeof(Ctl)), "ctl")) ||
@@ -436,25 +439,13 @@ int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const
             return rc;
         }
 
-    // copies (host or device sources)
-    const auto kind = [](const void *p) { return is_device_ptr(p) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; };
-    if ((rc = ck(cudaMemcpyAsync(g->rowptr, rowptr, ((size_t)n + 1) * 4, kind(rowptr), s), "copy rowptr")) ||
-        (m && (rc = ck(cudaMemcpyAsync(g->colidx, colidx, m * 4, kind(colidx), s), "copy colidx")))) {
+    // inputs into g->rowptr, g->colidx and an accepting bitmap (host or device sources)
+    uint32_t *acc_in = nullptr;
+    if ((rc = ck(cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), s), "memset ctl")) || (rc = upload(g, &acc_in))) {
         free_graph(g);
         return rc;
     }
-    uint32_t *acc_in = nullptr;
-    if (is_device_ptr(acc_bits)) {
-        acc_in = const_cast<uint32_t *>(acc_bits);
-    } else {
-        acc_in = g->acc; // stage through the work bitmap
-        if ((rc = ck(cudaMemcpyAsync(acc_in, acc_bits, W * 4, cudaMemcpyHostToDevice, s), "copy acc"))) {
-            free_graph(g);
-            return rc;
-        }
-    }
-    if ((rc = ck(cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), s), "memset ctl")) ||
-        (rc = ck(cudaMemsetAsync(g->colidx + m, 0, 16, s), "pad")) ||
+    if ((rc = ck(cudaMemsetAsync(g->colidx + m, 0, 16, s), "pad")) ||
         (rc = ck(cudaMemsetAsync(g->mval, 0, ((size_t)n + 4) * 4, s), "memset mval")) ||
         (rc = ck(cudaMemsetAsync(g->rec, 0, (size_t)n * 16, s), "memset rec"))) {
         free_graph(g);
@@ -468,7 +459,7 @@ int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const
     }
     if (g->h_ctl->bad) {
         free_graph(g);
-        return fail(MAP_ERR_CSR, "map_create: invalid CSR (decreasing rowptr or colidx >= n)");
+        return fail(MAP_ERR_CSR, "%s: invalid CSR (decreasing rowptr or colidx out of range)", who);
     }
     g->nacc0 = g->h_ctl->elim.v;
 
@@ -499,15 +490,59 @@ int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const
     return MAP_OK;
 }
 
+} // namespace
+
+extern "C" {
+
+int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const uint32_t *acc_bits,
+               void *cuda_stream, map_graph **out)
+{
+    g_err.clear();
+    if (!out) return fail(MAP_ERR_ARG, "map_create: out is NULL");
+    *out = nullptr;
+    if (n == 0 || n >= 0x7FFFFFFFu) return fail(MAP_ERR_ARG, "map_create: n = %u out of range [1, 2^31-1)", n);
+    if (!rowptr || !acc_bits) return fail(MAP_ERR_ARG, "map_create: rowptr and acc_bits are required");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+
+    // rowptr[0] and rowptr[n] (m) are needed on the host to size the copies
+    uint32_t ends[2];
+    const bool rp_dev = is_device_ptr(rowptr);
+    if (rp_dev) {
+        CK(cudaMemcpyAsync(&ends[0], rowptr, 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&ends[1], rowptr + n, 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    } else {
+        ends[0] = rowptr[0];
+        ends[1] = rowptr[n];
+    }
+    if (ends[0] != 0) return fail(MAP_ERR_CSR, "map_create: rowptr[0] = %u, expected 0", ends[0]);
+    const uint64_t m = ends[1];
+    if (m > 0 && !colidx) return fail(MAP_ERR_ARG, "map_create: colidx is NULL but m = %llu", (unsigned long long)m);
+
+    const auto kind = [](const void *p) { return is_device_ptr(p) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; };
+    return create_graph(n, m, s, "map_create",
+                        [&](map_graph *g, uint32_t **acc) -> int {
+                            CK(cudaMemcpyAsync(g->rowptr, rowptr, ((size_t)n + 1) * 4, kind(rowptr), s));
+                            if (m) CK(cudaMemcpyAsync(g->colidx, colidx, m * 4, kind(colidx), s));
+                            if (is_device_ptr(acc_bits)) {
+                                *acc = const_cast<uint32_t *>(acc_bits);
+                            } else {
+                                *acc = g->acc; // stage through the work bitmap
+                                CK(cudaMemcpyAsync(g->acc, acc_bits, (size_t)g->words * 4, cudaMemcpyHostToDevice, s));
+                            }
+                            return MAP_OK;
+                        },
+                        out);
+}
+
 int map_destroy(map_graph *g)
 {
     free_graph(g);
     return MAP_OK;
 }
 
-int map_run(map_graph *g, const map_opts *opts_in, map_result *res, uint32_t *map_out)
+static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint32_t *map_out)
 {
-    g_err.clear();
     if (!g || !res) return fail(MAP_ERR_ARG, "map_run: NULL graph or result");
     map_opts opts;
     memset(&opts, 0, sizeof opts);
@@ -559,6 +594,7 @@ int map_run(map_graph *g, const map_opts *opts_in, map_result *res, uint32_t *ma
         CK(cudaMemcpyAsync(g->ctl, g->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
         if ((rc = launch_reset(g, s))) return rc;
         mapk::k_run_begin<<<1, 32, 0, s>>>(g->ctl, none);
+        if (g->comp) mapk::k_batch_begin<<<(g->ncomp + 255) / 256, 256, 0, s>>>(dev_of(g));
         CK(cudaGetLastError());
         if ((rc = read_ctl(g))) return rc;
         while (g->h_ctl->outer_go) {
@@ -637,6 +673,151 @@ int map_run(map_graph *g, const map_opts *opts_in, map_result *res, uint32_t *ma
     if (c.status == mapk::ST_LIMIT) return fail(MAP_ERR_LIMIT, "map_run: max_outer or max_inner reached");
     if (c.status == mapk::ST_TIMEOUT)
         return fail(MAP_ERR_TIMEOUT, "map_run: stopped after timeout_ms = %u", opts.timeout_ms ? opts.timeout_ms : 120000u);
+    return MAP_OK;
+}
+
+int map_run(map_graph *g, const map_opts *opts, map_result *res, uint32_t *map_out)
+{
+    g_err.clear();
+    if (!g || !res) return fail(MAP_ERR_ARG, "map_run: NULL graph or result");
+    if (g->comp) return fail(MAP_ERR_ARG, "map_run: this handle holds a batch; use map_batch_run");
+    const int rc = run_impl(g, opts, res, map_out);
+    res->status = (uint32_t)rc;
+    return rc;
+}
+
+int map_batch_create(uint32_t count, const uint32_t *ns, const uint32_t *const *rowptrs,
+                     const uint32_t *const *colidxs, const uint32_t *const *acc_bits, void *cuda_stream,
+                     map_graph **out)
+{
+    g_err.clear();
+    if (!out) return fail(MAP_ERR_ARG, "map_batch_create: out is NULL");
+    *out = nullptr;
+    if (count == 0 || !ns || !rowptrs || !colidxs || !acc_bits)
+        return fail(MAP_ERR_ARG, "map_batch_create: count = 0 or a NULL array");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    std::vector<uint32_t> off(count + 1), woff(count + 1), mc(count);
+    std::vector<uint64_t> eoff(count + 1);
+    off[0] = 0;
+    eoff[0] = 0;
+    woff[0] = 0;
+    for (uint32_t c = 0; c < count; ++c) {
+        if (ns[c] == 0 || !rowptrs[c] || !acc_bits[c])
+            return fail(MAP_ERR_ARG, "map_batch_create: graph %u: n = 0 or NULL rowptr / acc_bits", c);
+        uint32_t ends[2];
+        if (is_device_ptr(rowptrs[c])) {
+            CK(cudaMemcpyAsync(&ends[0], rowptrs[c], 4, cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(&ends[1], rowptrs[c] + ns[c], 4, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+        } else {
+            ends[0] = rowptrs[c][0];
+            ends[1] = rowptrs[c][ns[c]];
+        }
+        if (ends[0] != 0) return fail(MAP_ERR_CSR, "map_batch_create: graph %u: rowptr[0] = %u", c, ends[0]);
+        if (ends[1] > 0 && !colidxs[c]) return fail(MAP_ERR_ARG, "map_batch_create: graph %u: colidx is NULL", c);
+        mc[c] = ends[1];
+        const uint64_t n_next = (uint64_t)off[c] + ns[c];
+        if (n_next >= 0x7FFFFFFFu) return fail(MAP_ERR_ARG, "map_batch_create: the union has too many vertices");
+        off[c + 1] = (uint32_t)n_next;
+        eoff[c + 1] = eoff[c] + mc[c];
+        if (eoff[c + 1] > 0xFFFFFFFFull) return fail(MAP_ERR_ARG, "map_batch_create: the union has too many edges");
+        woff[c + 1] = woff[c] + (ns[c] + 31) / 32;
+    }
+    const uint32_t N = off[count];
+    const uint64_t M = eoff[count];
+    const auto kind = [](const void *p) { return is_device_ptr(p) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; };
+    int rc = create_graph(
+        N, M, s, "map_batch_create",
+        [&](map_graph *g, uint32_t **acc) -> int {
+            g->ncomp = count;
+            CK(cudaMalloc((void **)&g->comp, ((size_t)N + 4) * 4));
+            CK(cudaMalloc((void **)&g->cs, (size_t)count * sizeof(mapk::CompState)));
+            CK(cudaMalloc((void **)&g->chist, (size_t)count * mapk::CH_CAP * 4));
+            CK(cudaMallocHost((void **)&g->h_cs, (size_t)count * sizeof(mapk::CompState)));
+            CK(cudaMallocHost((void **)&g->h_chist, (size_t)count * mapk::CH_CAP * 4));
+            // graph by graph: its rows and edges into the union, checked in its own ids, then offset
+            uint32_t *staged = g->xbuf; // accepting bitmaps one after another (sum of words <= N)
+            for (uint32_t c = 0; c < count; ++c) {
+                const uint32_t n_c = ns[c];
+                CK(cudaMemcpyAsync(g->rowptr + off[c], rowptrs[c], ((size_t)n_c + 1) * 4, kind(rowptrs[c]), s));
+                if (mc[c]) CK(cudaMemcpyAsync(g->colidx + eoff[c], colidxs[c], (size_t)mc[c] * 4, kind(colidxs[c]), s));
+                CK(cudaMemcpyAsync(staged + woff[c], acc_bits[c], (size_t)(woff[c + 1] - woff[c]) * 4, kind(acc_bits[c]),
+                                   s));
+                mapk::k_validate<<<grid_for(g, std::max<uint64_t>(mc[c], n_c), 1), 256, 0, s>>>(
+                    n_c, g->rowptr + off[c], mc[c], g->colidx + eoff[c], &g->ctl->bad);
+                mapk::k_add<<<grid_for(g, (uint64_t)n_c + 1, 1), 256, 0, s>>>(g->rowptr + off[c], (uint64_t)n_c + 1,
+                                                                              (uint32_t)eoff[c]);
+                if (mc[c])
+                    mapk::k_add<<<grid_for(g, mc[c], 1), 256, 0, s>>>(g->colidx + eoff[c], mc[c], off[c]);
+                CK(cudaGetLastError());
+            }
+            // per-graph offsets (in the list space, free at this point), graph of each vertex, union bitmap
+            uint32_t *d_off = g->list, *d_woff = g->list + (count + 1);
+            CK(cudaMemcpyAsync(d_off, off.data(), (size_t)(count + 1) * 4, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(d_woff, woff.data(), (size_t)(count + 1) * 4, cudaMemcpyHostToDevice, s));
+            mapk::k_fill_comp<<<grid_for(g, N, 1), 256, 0, s>>>(N, d_off, count, g->comp);
+            mapk::k_gather_acc<<<grid_for(g, g->words, 1), 256, 0, s>>>(N, d_off, d_woff, staged, g->comp, g->acc);
+            // per-graph records: off, m (host), accepting count (device)
+            std::vector<mapk::CompState> init(count);
+            memset(init.data(), 0, init.size() * sizeof(mapk::CompState));
+            for (uint32_t c = 0; c < count; ++c) {
+                init[c].off = off[c];
+                init[c].m = mc[c];
+            }
+            CK(cudaMemcpyAsync(g->cs, init.data(), (size_t)count * sizeof(mapk::CompState), cudaMemcpyHostToDevice, s));
+            mapk::k_count_acc<<<grid_for(g, N, 1), 256, 0, s>>>(N, g->acc, g->comp, g->cs);
+            CK(cudaGetLastError());
+            CK(cudaStreamSynchronize(s)); // `init` and the offset vectors leave scope
+            *acc = g->acc;
+            return MAP_OK;
+        },
+        out);
+    return rc;
+}
+
+int map_batch_run(map_graph *g, const map_opts *opts, map_result *results, uint32_t *map_out, uint32_t *rounds_out,
+                  uint32_t rounds_cap)
+{
+    g_err.clear();
+    if (!g || !results) return fail(MAP_ERR_ARG, "map_batch_run: NULL handle or results");
+    if (!g->comp) return fail(MAP_ERR_ARG, "map_batch_run: this handle holds a single graph; use map_run");
+    if (opts && opts->trace) return fail(MAP_ERR_ARG, "map_batch_run: traces are not offered for batches");
+    map_opts o;
+    memset(&o, 0, sizeof o);
+    if (opts) o = *opts;
+    o.rounds_out = nullptr;
+    o.rounds_cap = 0;
+    map_result all;
+    const int rc = run_impl(g, &o, &all, map_out);
+    if (rc != MAP_OK && rc != MAP_ERR_LIMIT && rc != MAP_ERR_TIMEOUT) return rc;
+    const uint32_t count = g->ncomp;
+    CK(cudaMemcpyAsync(g->h_cs, g->cs, (size_t)count * sizeof(mapk::CompState), cudaMemcpyDeviceToHost, g->stream));
+    if (rounds_out && rounds_cap)
+        CK(cudaMemcpyAsync(g->h_chist, g->chist, (size_t)count * mapk::CH_CAP * 4, cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    int first = MAP_OK;
+    for (uint32_t c = 0; c < count; ++c) {
+        const mapk::CompState &S = g->h_cs[c];
+        map_result &r = results[c];
+        memset(&r, 0, sizeof r);
+        r.verdict = S.verdict ? MAP_CYCLE : MAP_NO_CYCLE;
+        r.witness = S.verdict ? S.witness - S.off : MAP_NONE;
+        r.outer_iters = S.outer;
+        r.inner_canonical = all.inner_canonical;
+        r.inner_iters = S.inner_total;
+        r.relaxations = S.relax;
+        r.edges_total = S.m * (uint64_t)S.outer;
+        r.device_ms = all.device_ms;
+        r.accepting_left = S.nacc;
+        r.launches = all.launches;
+        r.status = S.status == mapk::ST_LIMIT ? MAP_ERR_LIMIT : S.status == mapk::ST_TIMEOUT ? MAP_ERR_TIMEOUT : MAP_OK;
+        if (r.status != MAP_OK && first == MAP_OK) first = (int)r.status;
+        if (rounds_out && rounds_cap) {
+            const uint32_t k = std::min(std::min(S.outer, rounds_cap), mapk::CH_CAP);
+            memcpy(rounds_out + (size_t)c * rounds_cap, g->h_chist + (size_t)c * mapk::CH_CAP, (size_t)k * 4);
+        }
+    }
+    if (first != MAP_OK) return fail(first, "map_batch_run: a graph stopped at a limit or timeout");
     return MAP_OK;
 }
 

@@ -42,6 +42,7 @@ namespace mapk {
 namespace cg = cooperative_groups;
 
 constexpr uint32_t NONE = 0xFFFFFFFFu;
+constexpr uint32_t CH_CAP = 1024; // rounds recorded per graph in a batched run
 constexpr uint32_t ST_OK = 0, ST_TIMEOUT = 5, ST_LIMIT = 6; // map_status values used on the device
 
 // Counters that many blocks update atomically each get a 128-byte line of their
@@ -96,8 +97,36 @@ struct Handles {
 };
 
 // device pointers of one graph, passed by value to the loop kernels
+// Batched runs: several graphs as one disjoint union (ids offset per graph,
+// which keeps each graph's order), one state record per graph.  A graph whose
+// run has ended is frozen: the dense round skips its rows, so its last map
+// vector stays in place, and nothing else touches it.
+struct CompState {
+    uint32_t active;      // still running
+    uint32_t outer;       // its outer iterations so far (current one, 1-based)
+    uint32_t verdict;     // 1 = accepting cycle
+    uint32_t witness;     // smallest self-mapped vertex (union id) of the current iteration
+    uint32_t nacc;        // accepting vertices left
+    uint32_t nacc0;       // accepting vertices at the start
+    uint32_t elim;        // eliminated in the current iteration
+    uint32_t touched;     // vertices with a value in the current iteration
+    uint32_t last_change; // last round of the current iteration in which one of its values changed
+    uint32_t status;      // ST_OK, ST_LIMIT or ST_TIMEOUT
+    uint32_t off;         // its first vertex in the union
+    uint32_t pad0;
+    uint64_t m;           // its edges
+    uint64_t relax;       // its edges examined (canonical count)
+    uint64_t inner_total; // its rounds, summed
+    uint64_t pad1;
+};
+
 struct Dev {
     uint32_t n, words;
+    // batched runs only (comp == NULL for a single graph)
+    const uint32_t *comp; // graph of each union vertex
+    CompState *cs;        // one record per graph
+    uint32_t *chist;      // rounds per outer iteration, CH_CAP entries per graph
+    uint32_t ncomp;
     const uint32_t *rowptr, *colidx, *rrowptr, *rcol, *rpos;
     uint32_t *colidx_w; // the same array as colidx, for the flag updates
     uint32_t *acc, *mval;
@@ -355,6 +384,93 @@ __device__ void epilogue_check(Ctl *c, Handles hd)
     set_cond(c, hd.outer, go);
 }
 
+// True in every thread of the last block to get here (see last_block).
+__device__ __forceinline__ bool last_block_all(Ctl *ctl)
+{
+    __shared__ bool is_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(&ctl->done.v, 1u);
+        is_last = (t == gridDim.x - 1);
+        if (is_last) {
+            ctl->done.v = 0;
+            __threadfence();
+        }
+    }
+    __syncthreads();
+    return is_last;
+}
+
+// Batched runs, after the self-map test and the elimination (Section 2, per
+// graph): every thread of the last block takes a share of the graphs.
+__device__ void epilogue_batch(const Dev &d, Handles hd)
+{
+    __shared__ uint32_t s_any, s_gst;
+    volatile Ctl *v = d.ctl;
+    if (threadIdx.x == 0) {
+        uint32_t gst = v->status; // a limit or timeout inside the fix-point loop
+        if (gst == ST_OK && timed_out(v)) gst = ST_TIMEOUT;
+        s_gst = gst;
+        s_any = 0;
+    }
+    __syncthreads();
+    const uint32_t gst = s_gst, max_outer = v->max_outer;
+    for (uint32_t c = threadIdx.x; c < d.ncomp; c += blockDim.x) {
+        volatile CompState &S = d.cs[c];
+        if (!S.active) continue;
+        const uint32_t outer = S.outer, rounds = S.last_change + 1;
+        if (outer - 1 < CH_CAP) d.chist[(size_t)c * CH_CAP + outer - 1] = rounds;
+        S.inner_total = S.inner_total + rounds;
+        S.relax = S.relax + S.m; // its dense round
+        bool go = true;
+        if (gst != ST_OK) {
+            S.status = gst;
+            go = false;
+        } else if (S.witness != NONE) {
+            S.verdict = 1;
+            go = false;
+        } else if (S.touched == 0) {
+            go = false; // no map value: nothing reaches a remaining accepting vertex
+        } else {
+            const uint32_t left = S.nacc - S.elim;
+            S.nacc = left;
+            if (left == 0) {
+                go = false;
+            } else if ((max_outer && outer >= max_outer) || outer > S.nacc0) {
+                S.status = ST_LIMIT;
+                go = false;
+            }
+        }
+        if (go) {
+            S.outer = outer + 1;
+            S.witness = NONE;
+            S.elim = 0;
+            S.touched = 0;
+            S.last_change = 0;
+            atomicOr(&s_any, 1u);
+        } else {
+            S.active = 0;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t go = s_any;
+        v->inner_total = v->inner_total + v->k;
+        if (go) {
+            v->outer = v->outer + 1;
+            v->lcnt[0].v = v->lcnt[1].v = v->lcnt[2].v = 0;
+            v->fcnt[0].v = v->fcnt[1].v = v->fcnt[2].v = 0;
+            v->tcnt.v = 0;
+            v->elim.v = 0;
+            v->k = 0;
+        }
+        v->outer_go = go;
+        __threadfence();
+        set_cond(d.ctl, hd.outer, go);
+    }
+}
+
 // Start of a run: fields written by the host (max_outer, max_inner, out,
 // hist_cap, m, nacc0, use_graph, timeout_ns) are kept, the rest is reset.
 __global__ void k_run_begin(Ctl *c, Handles hd)
@@ -439,6 +555,13 @@ __global__ void __launch_bounds__(DT_THREADS, 4) k_dense(const Dev d, Handles hd
     if (t < ntiles) load_rp(t, q, qlast);
     for (; t < ntiles; t += nw) {
         const uint32_t r0 = t * WT_ROWS, rows = min((uint32_t)WT_ROWS, n - r0);
+        if (d.comp) { // batched: a tile inside one frozen graph is skipped whole
+            const uint32_t c0 = __ldg(d.comp + r0), c1 = __ldg(d.comp + r0 + rows - 1);
+            if (c0 == c1 && !*(volatile uint32_t *)&d.cs[c0].active) {
+                if (t + nw < ntiles) load_rp(t + nw, q, qlast);
+                continue;
+            }
+        }
         reinterpret_cast<uint4 *>(rp)[lane] = q;
         if (lane == 0 && rows == WT_ROWS) rp[WT_ROWS] = qlast;
         if (t + nw < ntiles) load_rp(t + nw, q, qlast); // next tile's slice, in flight meanwhile
@@ -472,8 +595,26 @@ __global__ void __launch_bounds__(DT_THREADS, 4) k_dense(const Dev d, Handles hd
         }
         __syncwarp();
         const uint4 b4 = reinterpret_cast<const uint4 *>(best)[lane];
-        const uint32_t bs[4] = {b4.x, b4.y, b4.z, b4.w};
-        if (lane * 4 + 3 < rows) {
+        uint32_t bs[4] = {b4.x, b4.y, b4.z, b4.w};
+        if (d.comp) { // batched: rows of frozen graphs keep their values; record the change
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (lane * 4 + k >= rows) continue;
+                const uint32_t c = __ldg(d.comp + r0 + lane * 4 + k);
+                if (!*(volatile uint32_t *)&d.cs[c].active) {
+                    best[lane * 4 + k] = 0;
+                    bs[k] = 0xFFFFFFFFu; // marker: do not write
+                } else if (bs[k] && *(volatile uint32_t *)&d.cs[c].last_change < 1u) {
+                    atomicMax(&d.cs[c].last_change, 1u);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (lane * 4 + k < rows && bs[k] != 0xFFFFFFFFu) d.mval[r0 + lane * 4 + k] = bs[k];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (bs[k] == 0xFFFFFFFFu) bs[k] = 0;
+        } else if (lane * 4 + 3 < rows) {
             reinterpret_cast<uint4 *>(d.mval + r0)[lane] = b4;
         } else {
 #pragma unroll
@@ -533,14 +674,33 @@ __device__ __forceinline__ void warp_append(bool flag, uint32_t w, uint32_t *arr
 // clear the frontier flag FB(p) of the rows in flist[p] and return their row lengths
 __device__ __forceinline__ unsigned long long clear_frontier(const uint32_t *__restrict__ flist, uint32_t nf,
                                                              uint32_t p, uint4 *rec,
-                                                             const uint32_t *__restrict__ rowptr)
+                                                             const uint32_t *__restrict__ rowptr,
+                                                             const Dev &d)
 {
     unsigned long long relax = 0;
     const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += nthreads) {
-        const uint32_t w = __ldg(flist + i);
-        atomicAnd(rec_flags(rec + w), ~FB(p));
-        relax += __ldg(rowptr + w + 1) - __ldg(rowptr + w);
+    // warp-uniform loop: in batched runs the lanes of a warp add their row
+    // lengths per graph (one atomic per graph present in the warp)
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < nf; base += nthreads) {
+        const uint64_t i = base + lane_id();
+        unsigned long long len = 0;
+        uint32_t w = 0;
+        if (i < nf) {
+            w = __ldg(flist + i);
+            atomicAnd(rec_flags(rec + w), ~FB(p));
+            len = __ldg(rowptr + w + 1) - __ldg(rowptr + w);
+            relax += len;
+        }
+        if (d.comp) {
+            const uint32_t c = i < nf ? __ldg(d.comp + w) : 0xFFFFFFFFu;
+            const unsigned same = __match_any_sync(0xFFFFFFFFu, c);
+            // 64-bit sum of the group's row lengths from two 32-bit reductions (no overflow)
+            const unsigned lo = __reduce_add_sync(same, (unsigned)(len & 0xFFFFu));
+            const unsigned hi = __reduce_add_sync(same, (unsigned)(len >> 16));
+            const unsigned long long sum = (unsigned long long)lo + ((unsigned long long)hi << 16);
+            if (c != 0xFFFFFFFFu && lane_id() == (unsigned)(__ffs(same) - 1) && sum)
+                atomicAdd((unsigned long long *)&d.cs[c].relax, sum);
+        }
     }
     return relax;
 }
@@ -645,7 +805,7 @@ __global__ void __launch_bounds__(256, 4) k_rounds(const Dev d)
         st.buf = s_stage[threadIdx.x >> 5];
         st.cnt[0] = st.cnt[1] = st.cnt[2] = 0;
         // the previous round's frontier: clear its flags, count its relaxations
-        relax += clear_frontier(pick3(p_in, d.flist), vc->fcnt[p_in].v, p_in, d.rec, d.rowptr);
+        relax += clear_frontier(pick3(p_in, d.flist), vc->fcnt[p_in].v, p_in, d.rec, d.rowptr, d);
 
         // chunks of 256 listed vertices per block; their (vertex, reader) pairs
         // are spread evenly over the block's threads
@@ -692,6 +852,10 @@ __global__ void __launch_bounds__(256, 4) k_rounds(const Dev d)
                 if (raised) { // the record's sector is in L2 by now
                     if (SYNC) atomicMax(rec_snap(d.rec + w, p_out), ob);
                     cold = atomicOr(rec_flags(d.rec + w), CB(p_out));
+                    if (d.comp) { // batched: this graph changed in this round
+                        const uint32_t c = __ldg(d.comp + w);
+                        if (*(volatile uint32_t *)&d.cs[c].last_change < rr) atomicMax(&d.cs[c].last_change, rr);
+                    }
                 }
                 stage_append<3>(st, 0, act && !(fold & FB(p_out)), w, dst, ctr);
                 stage_append<3>(st, 1, raised && !(cold & CB(p_out)), w, dst, ctr);
@@ -712,7 +876,7 @@ __global__ void __launch_bounds__(256, 4) k_rounds(const Dev d)
         else if (nl && r + 1 > max_inner) status = ST_LIMIT;
     }
     // the last round's frontier: clear its flags, count its relaxations
-    if (r > 1) relax += clear_frontier(pick3(r % 3, d.flist), vc->fcnt[r % 3].v, r % 3, d.rec, d.rowptr);
+    if (r > 1) relax += clear_frontier(pick3(r % 3, d.flist), vc->fcnt[r % 3].v, r % 3, d.rec, d.rowptr, d);
     block_add_u64(relax, (unsigned long long *)&ctl->relax.v);
     if (lead) {
         vc->k = r;
@@ -732,39 +896,88 @@ __global__ void __launch_bounds__(256) k_check(const Dev d, Handles hd)
 {
     Ctl *ctl = d.ctl;
     const uint32_t nt = *(volatile uint32_t *)&ctl->tcnt.v;
-    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
     unsigned elim = 0;
     uint32_t wit = NONE;
-    for (uint64_t i = tid; i < nt; i += nthreads) {
-        const uint32_t v = __ldg(d.touched + i);
-        const uint32_t x = __ldg(d.mval + v);
-        const uint32_t u = x - 1; // x != 0 for a touched vertex
-        if (u == v) wit = min(wit, u);
-        const uint32_t bit = 1u << (u & 31u);
-        if (*(volatile uint32_t *)(d.acc + (u >> 5)) & bit) {
-            const uint32_t old = atomicAnd(d.acc + (u >> 5), ~bit);
-            if (old & bit) { // this thread removed u: clear u's flag in the matrix entries, log u
-                elim++;
-                d.elog[atomicAdd(&ctl->ecnt.v, 1u)] = u;
-                const uint32_t b = __ldg(d.rrowptr + u), e = __ldg(d.rrowptr + u + 1);
-                for (uint32_t j = b; j < e; ++j) d.colidx_w[__ldg(d.rpos + j)] = u;
+    // warp-uniform loop (batched runs aggregate per graph within the warp)
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < nt; base += nthreads) {
+        const uint64_t i = base + lane_id();
+        uint32_t c = 0xFFFFFFFFu, removed = 0;
+        if (i < nt) {
+            const uint32_t v = __ldg(d.touched + i);
+            const uint32_t x = __ldg(d.mval + v);
+            const uint32_t u = x - 1; // x != 0 for a touched vertex
+            if (d.comp) c = __ldg(d.comp + v);
+            if (u == v) {
+                wit = min(wit, u);
+                if (d.comp) atomicMin(&d.cs[c].witness, u);
+            }
+            const uint32_t bit = 1u << (u & 31u);
+            if (*(volatile uint32_t *)(d.acc + (u >> 5)) & bit) {
+                const uint32_t old = atomicAnd(d.acc + (u >> 5), ~bit);
+                if (old & bit) { // this thread removed u: clear u's flag in the matrix entries, log u
+                    elim++;
+                    removed = 1;
+                    d.elog[atomicAdd(&ctl->ecnt.v, 1u)] = u;
+                    const uint32_t b = __ldg(d.rrowptr + u), e = __ldg(d.rrowptr + u + 1);
+                    for (uint32_t j = b; j < e; ++j) d.colidx_w[__ldg(d.rpos + j)] = u;
+                }
+            }
+        }
+        if (d.comp) { // per graph: touched vertices and removals, one atomic per graph in the warp
+            const unsigned same = __match_any_sync(0xFFFFFFFFu, c);
+            const unsigned nt_c = __popc(same);
+            const unsigned ne_c = __reduce_add_sync(same, removed);
+            if (c != 0xFFFFFFFFu && lane_id() == (unsigned)(__ffs(same) - 1)) {
+                atomicAdd(&d.cs[c].touched, nt_c);
+                if (ne_c) atomicAdd(&d.cs[c].elim, ne_c);
             }
         }
     }
     block_add_min_u32(elim, wit, &ctl->elim.v, &ctl->witness.v);
-    if (last_block(ctl)) epilogue_check(ctl, hd);
+    if (!d.comp) {
+        if (last_block(ctl)) epilogue_check(ctl, hd);
+    } else if (last_block_all(ctl)) {
+        epilogue_batch(d, hd);
+    }
+}
+
+// Batched runs, start of a run: every graph's record (the host keeps off, m, nacc0).
+__global__ void k_batch_begin(const Dev d)
+{
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < d.ncomp; c += gridDim.x * blockDim.x) {
+        CompState &S = d.cs[c];
+        S.active = S.nacc0 ? 1u : 0u;
+        S.outer = S.active;
+        S.verdict = 0;
+        S.witness = NONE;
+        S.nacc = S.nacc0;
+        S.elim = 0;
+        S.touched = 0;
+        S.last_change = 0;
+        S.status = ST_OK;
+        S.relax = 0;
+        S.inner_total = 0;
+    }
 }
 
 // External encoding into `dst` (NULL: ctl->out): MAP_NONE for no value, else
 // the vertex id; all MAP_NONE when no outer iteration ran.
-__global__ void k_export(uint32_t n, const uint32_t *__restrict__ mval, const Ctl *ctl, uint32_t *dst)
+__global__ void k_export(uint32_t n, const uint32_t *__restrict__ mval, const Ctl *ctl, uint32_t *dst,
+                         const uint32_t *__restrict__ comp, const CompState *cs)
 {
     uint32_t *out = dst ? dst : ctl->out;
     const bool none = ctl->outer == 0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
-        out[v] = none ? NONE : __ldg(mval + v) - 1u;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const uint32_t x = __ldg(mval + v);
+        if (comp) { // batched: each graph's own ids, MAP_NONE for a graph that never ran
+            const uint32_t c = __ldg(comp + v);
+            out[v] = (cs[c].outer == 0 || x == 0) ? NONE : x - 1u - cs[c].off;
+        } else {
+            out[v] = none ? NONE : x - 1u;
+        }
+    }
 }
 
 // End of a run: give the vertices eliminated in it their accepting flag back
@@ -858,6 +1071,63 @@ __global__ void __launch_bounds__(256) k_transpose(uint32_t n, const uint32_t *_
             rcol[slot] = (uint32_t)w;
             rpos[slot] = i;
         }
+    }
+}
+
+// ---- batched set-up ------------------------------------------------------
+
+// x[i] += delta for i < len
+__global__ void k_add(uint32_t *x, uint64_t len, uint32_t delta)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) x[i] += delta;
+}
+
+// comp[v] = the graph whose vertex range [off[c], off[c+1]) holds v
+__global__ void k_fill_comp(uint32_t n, const uint32_t *__restrict__ off, uint32_t count, uint32_t *comp)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        uint32_t lo = 0, hi = count; // off[lo] <= v < off[hi]
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (__ldg(off + mid) <= v) lo = mid;
+            else hi = mid;
+        }
+        comp[v] = lo;
+    }
+}
+
+// the union's accepting bitmap from the graphs' own bitmaps (staged one after
+// another at word offsets woff[c]); one thread builds one union word
+__global__ void k_gather_acc(uint32_t n, const uint32_t *__restrict__ off, const uint32_t *__restrict__ woff,
+                             const uint32_t *__restrict__ staged, const uint32_t *__restrict__ comp, uint32_t *acc)
+{
+    const uint32_t words = (n + 31) / 32;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t wd = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; wd < words; wd += stride) {
+        uint32_t x = 0;
+        for (uint32_t b = 0; b < 32; ++b) {
+            const uint32_t v = (uint32_t)wd * 32 + b;
+            if (v >= n) break;
+            const uint32_t c = __ldg(comp + v), i = v - __ldg(off + c);
+            x |= ((__ldg(staged + __ldg(woff + c) + (i >> 5)) >> (i & 31u)) & 1u) << b;
+        }
+        acc[wd] = x;
+    }
+}
+
+// accepting vertices per graph
+__global__ void k_count_acc(uint32_t n, const uint32_t *__restrict__ acc, const uint32_t *__restrict__ comp,
+                            CompState *cs)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += stride) {
+        const uint64_t v = base + lane_id();
+        const bool a = v < n && ((__ldg(acc + (v >> 5)) >> (v & 31u)) & 1u);
+        const uint32_t c = a ? __ldg(comp + v) : 0xFFFFFFFFu;
+        const unsigned same = __match_any_sync(0xFFFFFFFFu, c);
+        if (c != 0xFFFFFFFFu && lane_id() == (unsigned)(__ffs(same) - 1)) atomicAdd(&cs[c].nacc0, (unsigned)__popc(same));
     }
 }
 

@@ -1,0 +1,100 @@
+"""Batched runs (many graphs in one launch): every graph must get exactly what it gets alone --
+verdict, witness (in its own ids), outer count, rounds of every outer iteration, relaxation
+count and final map vector -- checked against separate map_run calls and against the oracle."""
+import numpy as np
+import pytest
+
+import mapgen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_0912_2555_gb300 as p
+
+    return p
+
+
+def _mixed_graphs():
+    gs = []
+    for seed in range(24):
+        rng = np.random.default_rng(9000 + seed)
+        gs.append(mapgen.tiny_graph(seed, int(rng.integers(1, 200)), max_deg=int(rng.integers(0, 6)),
+                                    acc_p=float(rng.choice([0.0, 0.05, 0.3, 1.0]))))
+    gs.append(mapgen.random_16k("cycle"))
+    gs.append(mapgen.random_16k("nocycle"))
+    gs.append(mapgen.layered_graph(50000, 8, seed=4))
+    gs.append(mapgen.layered_graph(50000, 8, seed=4, plant=True))
+    gs.append(mapgen.product_graph(5, 5, interleave=True))
+    gs.append(mapgen.from_lists([[]], [1]))
+    gs.append(mapgen.from_lists([[0]], [1]))
+    gs.append(mapgen.from_lists([[1], [2], []], [1, 1, 1]))
+    return gs
+
+
+@pytest.mark.parametrize("sched", [0, 1])
+@pytest.mark.parametrize("on_device", [False, True])
+def test_batch_equals_separate_runs_and_oracle(pkg, sched, on_device):
+    gs = _mixed_graphs()
+    dev = (lambda a: torch.from_numpy(a.view(np.int32)).cuda()) if on_device else (lambda a: a)
+    items = [(g.n, dev(g.rowptr), dev(g.colidx if g.m else np.zeros(1, np.uint32)), dev(pkg.pack_bits(g.acc)))
+             for g in gs]
+    total = sum(g.n for g in gs)
+    h = pkg.map_batch_create(items)
+    try:
+        out = np.empty(total, np.uint32)
+        res = pkg.map_batch_run(h, len(gs), sched=sched, map_out=out)
+        res2 = pkg.map_batch_run(h, len(gs), sched=sched)  # runs repeat exactly
+    finally:
+        pkg.map_destroy(h)
+    off = 0
+    for g, r, r2 in zip(gs, res, res2):
+        want = oracle.run_graph(g)
+        assert r.status == pkg.MAP_OK
+        assert (r.verdict, r.witness, r.outer) == (want.verdict, want.witness, want.outer), g.name
+        assert np.array_equal(out[off:off + g.n], want.map), g.name
+        if sched == 0:
+            assert r.rounds == want.rounds, g.name
+            assert r.relaxations == want.relaxations, g.name
+            assert r.inner_iters == want.inner_total
+        assert (r2.verdict, r2.witness, r2.outer, r2.rounds, r2.relaxations) == (
+            r.verdict, r.witness, r.outer, r.rounds, r.relaxations)
+        off += g.n
+
+
+def test_batch_of_layered_graphs_with_planted_cycles(pkg):
+    sizes, planted, seeds = mapgen.batch_plan(count=24, lo=1000, hi=100000, frac_cycle=0.4, seed=4)
+    gs = [mapgen.batch_graph(int(s), bool(p), int(sd)) for s, p, sd in zip(sizes, planted, seeds)]
+    h = pkg.map_batch_create([(g.n, g.rowptr, g.colidx, pkg.pack_bits(g.acc)) for g in gs])
+    try:
+        res = pkg.map_batch_run(h, len(gs))
+    finally:
+        pkg.map_destroy(h)
+    for g, p, r in zip(gs, planted, res):
+        want = oracle.run_graph(g)
+        assert (r.verdict, r.witness, r.outer, r.rounds, r.relaxations) == (
+            want.verdict, want.witness, want.outer, want.rounds, want.relaxations)
+        assert r.verdict == int(p)
+
+
+def test_batch_handle_refused_by_map_run(pkg):
+    g = mapgen.from_lists([[1], [0]], [1, 0])
+    h = pkg.map_batch_create([(g.n, g.rowptr, g.colidx, pkg.pack_bits(g.acc))])
+    try:
+        with pytest.raises(pkg.MapError) as e:
+            pkg.map_run(h)
+        assert e.value.code == pkg.MAP_ERR_ARG
+    finally:
+        pkg.map_destroy(h)
+    with pytest.raises(pkg.MapError) as e:  # an edge leaving its graph is rejected
+        pkg.map_batch_create([(2, np.array([0, 1, 1], np.uint32), np.array([2], np.uint32), np.array([1], np.uint32)),
+                              (1, np.array([0, 0], np.uint32), None, np.array([1], np.uint32))])
+    assert e.value.code == pkg.MAP_ERR_CSR
