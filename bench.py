@@ -141,6 +141,106 @@ def cpu_baseline(g, outer):
                       f"including the oracle's own set-up)"}
 
 
+def batched_leg(pkg, np, torch, stream, count=256, steps=2, sched=0):
+    """256 graphs (sizes log-uniform in [1e3, 2e6], 40 % with a planted accepting cycle, layered
+    recipe) in one batched run, against the same 256 graphs run one after another with map_run.
+    Inputs resident in HBM in both legs; device time by CUDA events; jobs/s = graphs / time."""
+    import mapgen
+
+    sizes, planted, seeds = mapgen.batch_plan(count=count, lo=1000, hi=2_000_000, frac_cycle=0.4, seed=4)
+    gs = [mapgen.batch_graph(int(sz), bool(p), int(sd)) for sz, p, sd in zip(sizes, planted, seeds)]
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
+    items = [(g.n, dev(g.rowptr), dev(g.colidx), dev(pkg.pack_bits(g.acc))) for g in gs]
+    hb = pkg.map_batch_create(items, stream)
+    singles = [pkg.map_create(it[0], it[1], it[2], it[3], stream) for it in items]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    try:
+        res = pkg.map_batch_run(hb, count, sched=sched)  # warm-up (builds the graph)
+        for h in singles:
+            pkg.map_run(h, sched=sched)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            res = pkg.map_batch_run(hb, count, sched=sched)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        batch_ms = e0.elapsed_time(e1) / steps
+        e0.record(stream)
+        seq = None
+        for _ in range(steps):
+            seq = [pkg.map_run(h, sched=sched) for h in singles]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        seq_ms = e0.elapsed_time(e1) / steps
+        same = all((a.verdict, a.witness, a.outer, a.rounds, a.relaxations) ==
+                   (b.verdict, b.witness, b.outer, b.rounds, b.relaxations) for a, b in zip(res, seq))
+    finally:
+        pkg.map_destroy(hb)
+        for h in singles:
+            pkg.map_destroy(h)
+    edges = sum(r.edges_total for r in res)
+    return {"workload": f"{count} layered graphs, n log-uniform in [1e3, 2e6], 40 % planted cycles, seed 4",
+            "vertices": int(sum(g.n for g in gs)), "edges": int(sum(g.m for g in gs)),
+            "cycles_found": int(sum(r.verdict for r in res)),
+            "batch_ms": batch_ms, "sequential_ms": seq_ms,
+            "jobs_per_s_batched": count / (batch_ms / 1e3), "jobs_per_s_sequential": count / (seq_ms / 1e3),
+            "speedup": seq_ms / batch_ms, "gteps_batched": edges / (batch_ms / 1e3) / 1e9,
+            "results_identical": bool(same)}
+
+
+def serving_leg(pkg, np, rates=(100, 500, 2000), jobs=150, slots=8):
+    """Poisson arrivals of verification jobs (sizes lognormal, median 1e5, sigma 1.5, within
+    [1e3, 1e7]; half process products with 4-9 processes of 5-7 states, half layered graphs),
+    served with continuous admission by `slots` workers, against the same schedule served one job
+    at a time in arrival order (one worker).  Latency = submission to result, end to end (copy to
+    the device, set-up, run, map back).  The graphs are generated before the clock starts."""
+    import threading
+
+    import mapgen
+
+    arr = mapgen.arrivals(jobs, 1.0, seed=5)  # times at rate 1/s; scaled per rate below
+    graphs = [mapgen.arrival_graph(arr, i) for i in range(jobs)]
+    bits = [pkg.pack_bits(g.acc) for g in graphs]
+
+    def serve(rate, nslots):
+        t_arr = arr["t"] / rate
+        sub, done = [0.0] * jobs, [None] * jobs
+        ids = [None] * jobs
+        with pkg.Server(slots=nslots) as sv:
+            t0 = time.perf_counter()
+
+            def submitter():
+                for i in range(jobs):
+                    wait = t0 + t_arr[i] - time.perf_counter()
+                    if wait > 0:
+                        time.sleep(wait)
+                    g = graphs[i]
+                    sub[i] = time.perf_counter()
+                    ids[i] = sv.submit(g.n, g.rowptr, g.colidx, bits[i])
+
+            th = threading.Thread(target=submitter)
+            th.start()
+            left = set(range(jobs))
+            while left:
+                for i in list(left):
+                    if ids[i] is not None and sv.poll(ids[i], want_map=False) is not None:
+                        done[i] = time.perf_counter()
+                        left.discard(i)
+                time.sleep(0.0002)
+            th.join()
+        lat = np.array([d - s0 for d, s0 in zip(done, sub)]) * 1e3
+        span = max(done) - t0
+        return {"jobs_per_s": jobs / span, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean())}
+
+    out = {"workload": f"{jobs} jobs, lognormal sizes (median 1e5, sigma 1.5, [1e3, 1e7]), "
+                       "half process products, half layered graphs, seed 5",
+           "vertices": int(sum(g.n for g in graphs)), "slots": slots, "rates": {}}
+    for rate in rates:
+        out["rates"][str(rate)] = {"continuous": serve(rate, slots), "fifo_one_at_a_time": serve(rate, 1)}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -152,6 +252,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--n", type=int, default=None, help="override vertex count (smaller runs, not the bench line)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched leg (256 graphs)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg (Poisson arrivals)")
     args = ap.parse_args()
 
     if args.impl == "reference":
@@ -266,6 +368,10 @@ def main():
             "roofline": roofline, "phases": phases, "e2e": e2e, "gpu_launches": sum(r.launches for r in results),
             "clocks": clk.summary()}
     pkg.map_destroy(h)
+    if not args.no_batch and args.n is None:
+        line["batched"] = batched_leg(pkg, np, torch, stream, sched=args.sched)
+    if not args.no_serve and args.n is None and ws == 1:
+        line["serving"] = serving_leg(pkg, np)
     if rank == 0 and ws == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(g, args.cpu_outer)
     if rank == 0:

@@ -181,6 +181,35 @@ MAP_API int map_batch_create(uint32_t count, const uint32_t *ns, const uint32_t 
 MAP_API int map_batch_run(map_graph *g, const map_opts *opts, map_result *results, uint32_t *map_out,
                           uint32_t *rounds_out, uint32_t rounds_cap);
 
+/*
+ * Serving: verification jobs submitted over time and run with continuous
+ * admission.  The server has max_slots worker threads, each with its own CUDA
+ * stream.  A job is copied at submission and queued; the oldest queued job is
+ * started as soon as a worker is free and its device footprint (about
+ * 4 * (3m + 18n) bytes) fits into what is left of hbm_budget_bytes (a job
+ * larger than the whole budget runs when nothing else does).  Jobs that arrive
+ * while others are running are admitted as slots and memory free up, and the
+ * admitted jobs' work overlaps on the device.  Every job gets exactly the result
+ * map_create + map_run give it.
+ *
+ * map_server_create -- hbm_budget_bytes = 0: half of the free device memory.
+ *   The calling thread's current device is used.
+ * map_submit   -- host pointers only (copied); opts as for map_run, no trace.
+ *   *job_id identifies the job.
+ * map_poll     -- MAP_ERR_NOT_READY while the job is queued or running;
+ *   otherwise the job's status, with res and (optional) map_out (n entries,
+ *   host memory) filled, and the job is released (poll it once).
+ * map_server_destroy -- finishes the jobs already admitted and queued, then
+ *   frees everything; unpolled results are discarded.
+ * The server's calls may come from any host threads.
+ */
+typedef struct map_server map_server; /* opaque */
+MAP_API int map_server_create(size_t hbm_budget_bytes, uint32_t max_slots, map_server **out);
+MAP_API int map_submit(map_server *sv, uint32_t n, const uint32_t *rowptr, const uint32_t *colidx,
+                       const uint32_t *acc_bits, const map_opts *opts, uint64_t *job_id);
+MAP_API int map_poll(map_server *sv, uint64_t job_id, map_result *res, uint32_t *map_out);
+MAP_API int map_server_destroy(map_server *sv);
+
 /* map_graph_info -- n and m of a graph (either pointer may be NULL). */
 MAP_API int map_graph_info(const map_graph *g, uint32_t *n, uint64_t *m);
 

@@ -31,7 +31,7 @@ STATUS_NAMES = ["MAP_OK", "MAP_ERR_ARG", "MAP_ERR_CSR", "MAP_ERR_OOM", "MAP_ERR_
 
 # exported symbols of include/map.h (checked by the tests)
 EXPORTS = ["map_create", "map_run", "map_destroy", "map_graph_info", "map_last_error", "map_run_static",
-           "map_batch_create", "map_batch_run"]
+           "map_batch_create", "map_batch_run", "map_server_create", "map_submit", "map_poll", "map_server_destroy"]
 MAP_STATIC_MAX_N = 65536
 MAP_STATIC_MAX_M = 524288
 
@@ -103,8 +103,12 @@ def load(path: str = LIB_PATH):
     lib.map_run_static.argtypes = [u32, vp, vp, vp, ctypes.POINTER(MapOpts), ctypes.POINTER(MapResult), vp, vp]
     lib.map_batch_create.argtypes = [u32, vp, vp, vp, vp, vp, ctypes.POINTER(vp)]
     lib.map_batch_run.argtypes = [vp, ctypes.POINTER(MapOpts), ctypes.POINTER(MapResult), vp, vp, u32]
+    lib.map_server_create.argtypes = [ctypes.c_size_t, u32, ctypes.POINTER(vp)]
+    lib.map_submit.argtypes = [vp, u32, vp, vp, vp, ctypes.POINTER(MapOpts), ctypes.POINTER(ctypes.c_uint64)]
+    lib.map_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(MapResult), vp]
+    lib.map_server_destroy.argtypes = [vp]
     for f in ("map_create", "map_run", "map_destroy", "map_graph_info", "map_run_static", "map_batch_create",
-              "map_batch_run"):
+              "map_batch_run", "map_server_create", "map_submit", "map_poll", "map_server_destroy"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -287,6 +291,63 @@ def map_batch_run(handle, count: int, sched: int = MAP_SCHED_SYNC, max_outer: in
                              r.dense_launches, r.accepting_left, r.launches, r.round_ms, r.check_ms,
                              r.frontier_rows, []))
     return out
+
+
+def _result(r, trace=()):
+    return RunResult(r.status, r.verdict, r.witness, r.outer_iters, [], r.inner_iters, bool(r.inner_canonical),
+                     r.relaxations, r.edges_total, r.device_ms, r.dense_ms, r.dense_launches, r.accepting_left,
+                     r.launches, r.round_ms, r.check_ms, r.frontier_rows, list(trace))
+
+
+class Server:
+    """Continuous-admission serving (map_server_* in include/map.h)."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, slots: int = 4):
+        lib = load()
+        self.handle = ctypes.c_void_p()
+        rc = lib.map_server_create(hbm_budget_bytes, slots, ctypes.byref(self.handle))
+        if rc != MAP_OK:
+            raise MapError(rc, "map_server_create", last_error())
+        self.sizes = {}
+
+    def submit(self, n, rowptr, colidx, acc_bits, sched: int = MAP_SCHED_SYNC, max_outer: int = 0) -> int:
+        lib = load()
+        rp = np.ascontiguousarray(rowptr, dtype=np.uint32)
+        ci = np.ascontiguousarray(colidx, dtype=np.uint32) if colidx is not None else None
+        ab = np.ascontiguousarray(acc_bits, dtype=np.uint32)
+        opts = MapOpts()
+        opts.sched, opts.max_outer = sched, max_outer
+        jid = ctypes.c_uint64()
+        rc = lib.map_submit(self.handle, n, rp.ctypes.data, ci.ctypes.data if ci is not None and ci.size else None,
+                            ab.ctypes.data, ctypes.byref(opts), ctypes.byref(jid))
+        if rc != MAP_OK:
+            raise MapError(rc, "map_submit", last_error())
+        self.sizes[jid.value] = n
+        return jid.value
+
+    def poll(self, job_id: int, want_map: bool = True):
+        """None while the job is queued or running; else (RunResult, map vector or None)."""
+        lib = load()
+        res = MapResult()
+        out = np.empty(self.sizes[job_id], np.uint32) if want_map else None
+        rc = lib.map_poll(self.handle, job_id, ctypes.byref(res), out.ctypes.data if want_map else None)
+        if rc == MAP_ERR_NOT_READY:
+            return None
+        self.sizes.pop(job_id, None)
+        if rc != MAP_OK:
+            raise MapError(rc, "map_poll", last_error())
+        return _result(res), out
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            load().map_server_destroy(self.handle)
+            self.handle.value = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def pack_bits(flags) -> np.ndarray:

@@ -12,6 +12,12 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
 #include <new>
 #include <string>
 #include <vector>
@@ -123,15 +129,15 @@ void free_graph(map_graph *g)
     void *dev[] = {g->rowptr, g->colidx, g->rrowptr, g->rcol,    g->rpos, g->elog, g->acc0, g->acc,
                    g->mval,   g->list,   g->flist,   g->rec,     g->touched, g->xbuf, g->hist, g->ctl};
     for (void *p : dev)
-        if (p) cudaFree(p);
-    if (g->comp) cudaFree(g->comp);
-    if (g->cs) cudaFree(g->cs);
-    if (g->chist) cudaFree(g->chist);
-    if (g->h_cs) cudaFreeHost(g->h_cs);
-    if (g->h_chist) cudaFreeHost(g->h_chist);
-    if (g->h_ctl) cudaFreeHost(g->h_ctl);
-    if (g->h_stage) cudaFreeHost(g->h_stage);
-    if (g->h_hist) cudaFreeHost(g->h_hist);
+        if (p) cudaFreeAsync(p, g->stream); // stream-ordered: no device-wide synchronisation
+    if (g->comp) cudaFreeAsync(g->comp, g->stream);
+    if (g->cs) cudaFreeAsync(g->cs, g->stream);
+    if (g->chist) cudaFreeAsync(g->chist, g->stream);
+    free(g->h_cs);
+    free(g->h_chist);
+    free(g->h_ctl);
+    free(g->h_stage);
+    free(g->h_hist);
     for (auto &e : g->ev)
         if (e) cudaEventDestroy(e);
     cudaGetLastError();
@@ -405,7 +411,9 @@ int create_graph(uint32_t n, uint64_t m, cudaStream_t s, const char *who, Upload
     g->hist_cap = 1u << 16;
 
     auto alloc = [&](uint32_t **p, uint64_t words) -> int {
-        CK(cudaMalloc((void **)p, (words + 4) * sizeof(uint32_t))); // 16 bytes of slack at the end
+        // stream-ordered allocation (does not synchronise the device; graphs on other
+        // streams keep running); 16 bytes of slack at the end
+        CK(cudaMallocAsync((void **)p, (words + 4) * sizeof(uint32_t), s));
         return MAP_OK;
     };
     int rc = MAP_OK;
@@ -426,10 +434,15 @@ int create_graph(uint32_t n, uint64_t m, cudaStream_t s, const char *who, Upload
         return fail(e == cudaErrorMemoryAllocation ? MAP_ERR_OOM : MAP_ERR_CUDA, "%s: %s: %s", who, what,
                     cudaGetErrorString(e));
     };
-    if ((rc = ck(cudaMalloc((void **)&g->ctl, sizeof(Ctl)), "ctl")) ||
-        (rc = ck(cudaMallocHost((void **)&g->h_ctl, sizeof(Ctl)), "h_ctl")) ||
-        (rc = ck(cudaMallocHost((void **)&g->h_stage, (size_t)n * 4), "h_stage")) ||
-        (rc = ck(cudaMallocHost((void **)&g->h_hist, (size_t)g->hist_cap * 4), "h_hist"))) {
+    // host mirrors in pageable memory (pinning or unpinning would synchronise the device)
+    g->h_ctl = static_cast<Ctl *>(aligned_alloc(128, sizeof(Ctl)));
+    g->h_stage = static_cast<uint32_t *>(malloc((size_t)n * 4 + 16));
+    g->h_hist = static_cast<uint32_t *>(malloc((size_t)g->hist_cap * 4));
+    if (!g->h_ctl || !g->h_stage || !g->h_hist) {
+        free_graph(g);
+        return fail(MAP_ERR_OOM, "%s: host allocation failed", who);
+    }
+    if ((rc = ck(cudaMallocAsync((void **)&g->ctl, sizeof(Ctl), s), "ctl"))) {
         free_graph(g);
         return rc;
     }
@@ -541,7 +554,8 @@ int map_destroy(map_graph *g)
     return MAP_OK;
 }
 
-static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint32_t *map_out)
+static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint32_t *map_out,
+                    bool force_stepped = false)
 {
     if (!g || !res) return fail(MAP_ERR_ARG, "map_run: NULL graph or result");
     map_opts opts;
@@ -552,7 +566,7 @@ static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint
     const bool profile = (opts.flags & MAP_FLAG_PROFILE) != 0;
     // the CUDA-graph driver runs the whole loop on the device; per-iteration
     // traces and per-kernel timing need the host-stepped driver (same kernels)
-    const bool stepped = opts.trace != nullptr || profile;
+    const bool stepped = opts.trace != nullptr || profile || force_stepped;
     memset(res, 0, sizeof *res);
     cudaStream_t s = g->stream;
     const uint32_t n = g->n;
@@ -730,11 +744,12 @@ int map_batch_create(uint32_t count, const uint32_t *ns, const uint32_t *const *
         N, M, s, "map_batch_create",
         [&](map_graph *g, uint32_t **acc) -> int {
             g->ncomp = count;
-            CK(cudaMalloc((void **)&g->comp, ((size_t)N + 4) * 4));
-            CK(cudaMalloc((void **)&g->cs, (size_t)count * sizeof(mapk::CompState)));
-            CK(cudaMalloc((void **)&g->chist, (size_t)count * mapk::CH_CAP * 4));
-            CK(cudaMallocHost((void **)&g->h_cs, (size_t)count * sizeof(mapk::CompState)));
-            CK(cudaMallocHost((void **)&g->h_chist, (size_t)count * mapk::CH_CAP * 4));
+            CK(cudaMallocAsync((void **)&g->comp, ((size_t)N + 4) * 4, s));
+            CK(cudaMallocAsync((void **)&g->cs, (size_t)count * sizeof(mapk::CompState), s));
+            CK(cudaMallocAsync((void **)&g->chist, (size_t)count * mapk::CH_CAP * 4, s));
+            g->h_cs = static_cast<mapk::CompState *>(malloc((size_t)count * sizeof(mapk::CompState)));
+            g->h_chist = static_cast<uint32_t *>(malloc((size_t)count * mapk::CH_CAP * 4));
+            if (!g->h_cs || !g->h_chist) return fail(MAP_ERR_OOM, "map_batch_create: host allocation failed");
             // graph by graph: its rows and edges into the union, checked in its own ids, then offset
             uint32_t *staged = g->xbuf; // accepting bitmaps one after another (sum of words <= N)
             for (uint32_t c = 0; c < count; ++c) {
@@ -1069,3 +1084,213 @@ extern "C" int map_run_static(uint32_t n, const uint32_t *rowptr, const uint32_t
     if (h.status == mapk::ST_TIMEOUT) return fail(MAP_ERR_TIMEOUT, "map_run_static: stopped after the timeout");
     return MAP_OK;
 }
+
+// ============================================================================
+// Serving: a request loop with continuous admission (map_server_*).
+//
+// Jobs are copied at submission and queued.  Each of the server's worker
+// threads owns a CUDA stream; a worker takes the oldest queued job as soon as
+// the job's device footprint fits into what is left of the memory budget, and
+// runs it (map_create, map_run, map output, map_destroy) on its stream.  Jobs
+// that arrive while others are on the GPU are admitted as workers and memory
+// free up, and the work of admitted jobs overlaps on the device.  Allocation is
+// stream-ordered, so one job's set-up does not stall the others.
+// ============================================================================
+
+namespace {
+
+struct ServerJob {
+    uint64_t id = 0;
+    uint32_t n = 0;
+    uint64_t m = 0;
+    std::vector<uint32_t> rowptr, colidx, acc;
+    map_opts opts{};
+    size_t footprint = 0;
+    bool done = false;
+    int status = MAP_OK;
+    map_result res{};
+    std::vector<uint32_t> map;
+    std::string err;
+};
+
+// device bytes of a graph: the allocations of create_graph
+size_t graph_footprint(uint64_t n, uint64_t m)
+{
+    const uint64_t W = (n + 31) / 32;
+    const uint64_t words = 2 * (n + 5) + 3 * (m + 4) + 2 * (W + 4) + (n + 4) + 2 * 3 * (n + 4) + 4 * (n + 4) +
+                           3 * (n + 4) + (1u << 16);
+    return (size_t)words * 4 + sizeof(Ctl) + (1u << 20);
+}
+
+} // namespace
+
+struct map_server {
+    size_t budget = 0;
+    size_t used = 0;
+    int device = 0;
+    bool stop = false;
+    uint64_t next_id = 1;
+    std::mutex mu;
+    std::condition_variable cv_work;
+    std::deque<ServerJob *> queue;
+    std::unordered_map<uint64_t, ServerJob *> jobs;
+    std::vector<std::thread> workers;
+    std::vector<cudaStream_t> streams;
+};
+
+namespace {
+
+void server_worker(map_server *sv, cudaStream_t stream)
+{
+    cudaSetDevice(sv->device);
+    for (;;) {
+        ServerJob *job = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            sv->cv_work.wait(lk, [&] {
+                if (sv->stop) return true;
+                if (sv->queue.empty()) return false;
+                const size_t fp = sv->queue.front()->footprint;
+                return sv->used + fp <= sv->budget || sv->used == 0; // a job larger than the budget runs alone
+            });
+            if (sv->stop && sv->queue.empty()) return;
+            if (sv->queue.empty()) continue;
+            job = sv->queue.front();
+            sv->queue.pop_front();
+            sv->used += job->footprint;
+        }
+        map_graph *g = nullptr;
+        int rc = map_create(job->n, job->rowptr.data(), job->m ? job->colidx.data() : nullptr, job->acc.data(),
+                            stream, &g);
+        if (rc == MAP_OK) {
+            job->map.resize(job->n);
+            rc = run_impl(g, &job->opts, &job->res, job->map.data(), true);
+            job->res.status = (uint32_t)rc;
+            map_destroy(g);
+        }
+        if (rc != MAP_OK) job->err = g_err;
+        // the job's inputs are not needed any more
+        std::vector<uint32_t>().swap(job->rowptr);
+        std::vector<uint32_t>().swap(job->colidx);
+        std::vector<uint32_t>().swap(job->acc);
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            job->status = rc;
+            job->done = true;
+            sv->used -= job->footprint;
+        }
+        sv->cv_work.notify_all();
+    }
+}
+
+} // namespace
+
+extern "C" {
+
+int map_server_create(size_t hbm_budget_bytes, uint32_t max_slots, map_server **out)
+{
+    g_err.clear();
+    if (!out) return fail(MAP_ERR_ARG, "map_server_create: out is NULL");
+    *out = nullptr;
+    if (max_slots == 0 || max_slots > 64) return fail(MAP_ERR_ARG, "map_server_create: max_slots must be 1..64");
+    map_server *sv = new (std::nothrow) map_server;
+    if (!sv) return fail(MAP_ERR_OOM, "map_server_create: host allocation failed");
+    CK(cudaGetDevice(&sv->device));
+    if (hbm_budget_bytes == 0) {
+        size_t free_b = 0, total_b = 0;
+        CK(cudaMemGetInfo(&free_b, &total_b));
+        hbm_budget_bytes = free_b / 2;
+    }
+    sv->budget = hbm_budget_bytes;
+    for (uint32_t i = 0; i < max_slots; ++i) {
+        cudaStream_t st;
+        cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            map_server_destroy(sv);
+            return fail(MAP_ERR_CUDA, "map_server_create: stream: %s", cudaGetErrorString(e));
+        }
+        sv->streams.push_back(st);
+    }
+    for (uint32_t i = 0; i < max_slots; ++i) sv->workers.emplace_back(server_worker, sv, sv->streams[i]);
+    *out = sv;
+    return MAP_OK;
+}
+
+int map_submit(map_server *sv, uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const uint32_t *acc_bits,
+               const map_opts *opts, uint64_t *job_id)
+{
+    g_err.clear();
+    if (!sv || !job_id) return fail(MAP_ERR_ARG, "map_submit: NULL server or job_id");
+    if (n == 0 || n >= 0x7FFFFFFFu || !rowptr || !acc_bits) return fail(MAP_ERR_ARG, "map_submit: bad graph");
+    if (opts && opts->trace) return fail(MAP_ERR_ARG, "map_submit: traces are not offered for served jobs");
+    if (is_device_ptr(rowptr) || is_device_ptr(colidx) || is_device_ptr(acc_bits))
+        return fail(MAP_ERR_ARG, "map_submit: inputs must be host memory (the job is copied at submission)");
+    const uint64_t m = rowptr[n];
+    if (m > 0 && !colidx) return fail(MAP_ERR_ARG, "map_submit: colidx is NULL");
+    ServerJob *job = new (std::nothrow) ServerJob;
+    if (!job) return fail(MAP_ERR_OOM, "map_submit: host allocation failed");
+    try {
+        job->n = n;
+        job->m = m;
+        job->rowptr.assign(rowptr, rowptr + (size_t)n + 1);
+        job->colidx.assign(colidx, colidx + m);
+        job->acc.assign(acc_bits, acc_bits + (n + 31) / 32);
+    } catch (...) {
+        delete job;
+        return fail(MAP_ERR_OOM, "map_submit: host allocation failed");
+    }
+    if (opts) job->opts = *opts;
+    job->opts.rounds_out = nullptr;
+    job->opts.rounds_cap = 0;
+    job->footprint = graph_footprint(n, m);
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        job->id = sv->next_id++;
+        sv->jobs[job->id] = job;
+        sv->queue.push_back(job);
+        *job_id = job->id;
+    }
+    sv->cv_work.notify_all();
+    return MAP_OK;
+}
+
+int map_poll(map_server *sv, uint64_t job_id, map_result *res, uint32_t *map_out)
+{
+    g_err.clear();
+    if (!sv) return fail(MAP_ERR_ARG, "map_poll: NULL server");
+    ServerJob *job = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        auto it = sv->jobs.find(job_id);
+        if (it == sv->jobs.end()) return fail(MAP_ERR_ARG, "map_poll: unknown job %llu", (unsigned long long)job_id);
+        if (!it->second->done) return MAP_ERR_NOT_READY;
+        job = it->second;
+        sv->jobs.erase(it);
+    }
+    if (res) *res = job->res;
+    if (map_out && job->status == MAP_OK) memcpy(map_out, job->map.data(), (size_t)job->n * 4);
+    const int rc = job->status;
+    if (rc != MAP_OK) fail(rc, "%s", job->err.c_str());
+    delete job;
+    return rc;
+}
+
+int map_server_destroy(map_server *sv)
+{
+    if (!sv) return MAP_OK;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv_work.notify_all();
+    for (auto &t : sv->workers) t.join();
+    for (auto st : sv->streams) cudaStreamDestroy(st);
+    for (auto &kv : sv->jobs) delete kv.second;
+    for (ServerJob *j : sv->queue)
+        if (!sv->jobs.count(j->id)) delete j;
+    delete sv;
+    return MAP_OK;
+}
+
+} // extern "C"

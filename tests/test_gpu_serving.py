@@ -1,0 +1,92 @@
+"""Serving with continuous admission: jobs submitted over time while others run, admitted as
+workers and the memory budget free up; every job's result must be exactly its result alone
+(checked against the oracle), whatever else is in flight."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import mapgen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_0912_2555_gb300 as p
+
+    return p
+
+
+def _jobs():
+    gs = []
+    for seed in range(20):
+        rng = np.random.default_rng(4000 + seed)
+        gs.append(mapgen.tiny_graph(seed, int(rng.integers(1, 300)), max_deg=int(rng.integers(0, 6)),
+                                    acc_p=float(rng.choice([0.0, 0.1, 0.5]))))
+    gs += [mapgen.random_16k("cycle"), mapgen.random_16k("nocycle"), mapgen.layered_graph(80000, 10, seed=2),
+           mapgen.layered_graph(80000, 10, seed=2, plant=True), mapgen.product_graph(5, 6, interleave=False)]
+    return gs
+
+
+@pytest.mark.parametrize("slots,budget", [(4, 0), (3, 8 << 20)])
+def test_jobs_in_flight_get_their_own_results(pkg, slots, budget):
+    gs = _jobs()
+    want = [oracle.run_graph(g) for g in gs]
+    ids = [None] * len(gs)
+    with pkg.Server(hbm_budget_bytes=budget, slots=slots) as sv:
+        def submitter():
+            rng = np.random.default_rng(1)
+            for i in rng.permutation(len(gs)):
+                g = gs[i]
+                ids[i] = sv.submit(g.n, g.rowptr, g.colidx if g.m else None, pkg.pack_bits(g.acc))
+                time.sleep(float(rng.exponential(0.002)))
+        th = threading.Thread(target=submitter)
+        th.start()
+        th.join()
+        results = [None] * len(gs)
+        deadline = time.time() + 120
+        while any(r is None for r in results) and time.time() < deadline:
+            for i, jid in enumerate(ids):
+                if results[i] is None:
+                    results[i] = sv.poll(jid)
+            time.sleep(0.001)
+    assert all(r is not None for r in results)
+    for g, w, (r, mp) in zip(gs, want, results):
+        assert (r.verdict, r.witness, r.outer, r.relaxations, r.inner_iters) == (
+            w.verdict, w.witness, w.outer, w.relaxations, w.inner_total), g.name
+        assert np.array_equal(mp, w.map), g.name
+
+
+def test_poll_before_ready_and_unknown_job(pkg):
+    g = mapgen.layered_graph(200000, 12, seed=3)
+    with pkg.Server(slots=1) as sv:
+        jid = sv.submit(g.n, g.rowptr, g.colidx, pkg.pack_bits(g.acc))
+        first = sv.poll(jid)  # most likely still running
+        while first is None:
+            time.sleep(0.001)
+            first = sv.poll(jid)
+        assert first[0].verdict == oracle.run_graph(g).verdict
+        with pytest.raises(pkg.MapError) as e:
+            sv.poll(jid)  # released after the first successful poll
+        assert e.value.code == pkg.MAP_ERR_ARG
+
+
+def test_submit_refuses_device_inputs(pkg):
+    g = mapgen.from_lists([[1], [0]], [1, 0])
+    lib = pkg.load()
+    import ctypes
+    with pkg.Server(slots=1) as sv:
+        d = torch.from_numpy(g.rowptr.view(np.int32)).cuda()
+        jid = ctypes.c_uint64()
+        rc = lib.map_submit(sv.handle, g.n, d.data_ptr(), g.colidx.ctypes.data, pkg.pack_bits(g.acc).ctypes.data,
+                            None, ctypes.byref(jid))
+        assert rc == pkg.MAP_ERR_ARG
