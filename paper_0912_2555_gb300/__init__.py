@@ -329,8 +329,9 @@ class Server:
         """None while the job is queued or running; else (RunResult, map vector or None)."""
         lib = load()
         res = MapResult()
-        out = np.empty(self.sizes[job_id], np.uint32) if want_map else None
-        rc = lib.map_poll(self.handle, job_id, ctypes.byref(res), out.ctypes.data if want_map else None)
+        n = self.sizes.get(job_id)
+        out = np.empty(n, np.uint32) if (want_map and n) else None
+        rc = lib.map_poll(self.handle, job_id, ctypes.byref(res), out.ctypes.data if out is not None else None)
         if rc == MAP_ERR_NOT_READY:
             return None
         self.sizes.pop(job_id, None)
