@@ -383,9 +383,31 @@ namespace {
 // fills g->rowptr (n + 1 words) and g->colidx (m words) on stream s and sets acc
 // to a device bitmap of the accepting vertices; it may also set up the batch
 // fields.  Then: validation, accepting set, readers (reverse CSR), flags.
+// The stream-ordered allocator returns freed memory to the system at every
+// synchronisation unless told otherwise; graphs are created and destroyed
+// often (serving), so the device's default pool keeps what it has.
+void keep_pool_memory()
+{
+    static std::atomic<uint64_t> done_mask{0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return;
+    }
+    if (done_mask.load() & (1ull << dev)) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    done_mask.fetch_or(1ull << dev);
+}
+
 template <class Upload>
 int create_graph(uint32_t n, uint64_t m, cudaStream_t s, const char *who, Upload upload, map_graph **out)
 {
+    keep_pool_memory();
     map_graph *g = new (std::nothrow) map_graph;
     if (!g) return fail(MAP_ERR_OOM, "%s: host allocation failed", who);
     g->n = n;
@@ -1143,6 +1165,15 @@ namespace {
 void server_worker(map_server *sv, cudaStream_t stream)
 {
     cudaSetDevice(sv->device);
+    uint32_t *stage = nullptr; // pinned staging for the job's inputs
+    size_t stage_words = 0;
+    struct Release {
+        uint32_t *&p;
+        ~Release()
+        {
+            if (p) cudaFreeHost(p);
+        }
+    } release{stage};
     for (;;) {
         ServerJob *job = nullptr;
         {
@@ -1159,9 +1190,32 @@ void server_worker(map_server *sv, cudaStream_t stream)
             sv->queue.pop_front();
             sv->used += job->footprint;
         }
+        // the job's inputs into this worker's pinned staging buffer (grown when needed), so
+        // that the copies to the device are asynchronous DMA transfers
+        const size_t words = (size_t)job->n + 1 + job->m + job->acc.size();
+        if (words > stage_words) {
+            if (stage) cudaFreeHost(stage);
+            stage = nullptr;
+            stage_words = 0;
+            if (cudaMallocHost((void **)&stage, words * 4 * 5 / 4) == cudaSuccess) stage_words = words * 5 / 4;
+            else cudaGetLastError();
+        }
+        const uint32_t *rp = job->rowptr.data(), *ci = job->m ? job->colidx.data() : nullptr, *ab = job->acc.data();
+        if (stage) {
+            uint32_t *p = stage;
+            memcpy(p, rp, ((size_t)job->n + 1) * 4);
+            rp = p;
+            p += job->n + 1;
+            if (job->m) {
+                memcpy(p, ci, job->m * 4);
+                ci = p;
+                p += job->m;
+            }
+            memcpy(p, ab, job->acc.size() * 4);
+            ab = p;
+        }
         map_graph *g = nullptr;
-        int rc = map_create(job->n, job->rowptr.data(), job->m ? job->colidx.data() : nullptr, job->acc.data(),
-                            stream, &g);
+        int rc = map_create(job->n, rp, ci, ab, stream, &g);
         if (rc == MAP_OK) {
             job->map.resize(job->n);
             rc = run_impl(g, &job->opts, &job->res, job->map.data(), true);

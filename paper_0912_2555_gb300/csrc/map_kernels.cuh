@@ -768,6 +768,10 @@ __device__ __forceinline__ bool grid_barrier(Ctl *ctl)
     return s_ok != 0;
 }
 
+constexpr int RC_E = 4;                 // listed vertices per thread and chunk
+constexpr int RC_ENTRIES = 256 * RC_E;  // per block and chunk
+constexpr int RC_P = 4;                 // push pairs per thread and step
+
 // The fix-point loop of one outer iteration: rounds 2, 3, ... until a round
 // changes nothing.  Round r reads list[(r-1) % 3] and appends to list[r % 3];
 // the counters of list[(r+1) % 3] (read in round r-1, appended again in round
@@ -777,7 +781,7 @@ __global__ void __launch_bounds__(256, 4) k_rounds(const Dev d)
 {
     __shared__ uint32_t s_stage[8][3 * SB_ENTRIES];
     __shared__ uint32_t s_cnt[8][3], s_base[3];
-    __shared__ uint32_t s_incl[256], s_o[256], s_b[256], s_scan[8];
+    __shared__ uint32_t s_incl[RC_ENTRIES], s_o[RC_ENTRIES], s_b[RC_ENTRIES], s_scan[8];
     Ctl *ctl = d.ctl;
     volatile Ctl *vc = ctl;
     const unsigned lane = lane_id();
@@ -807,59 +811,93 @@ __global__ void __launch_bounds__(256, 4) k_rounds(const Dev d)
         // the previous round's frontier: clear its flags, count its relaxations
         relax += clear_frontier(pick3(p_in, d.flist), vc->fcnt[p_in].v, p_in, d.rec, d.rowptr, d);
 
-        // chunks of 256 listed vertices per block; their (vertex, reader) pairs
-        // are spread evenly over the block's threads
-        for (uint64_t c0 = (uint64_t)blockIdx.x * 256; c0 < nl; c0 += (uint64_t)gridDim.x * 256) {
-            // each thread reads one listed vertex and consumes its snapshot and
-            // list flag (nothing else reads them in this round)
-            const uint64_t i = c0 + threadIdx.x;
-            uint32_t o = 0, b = 0, len = 0;
-            if (i < nl) {
-                const uint32_t u = __ldg(list + i);
-                const uint32_t mu = SYNC ? *(volatile uint32_t *)rec_snap(d.rec + u, p_in)
-                                         : *(volatile uint32_t *)(d.mval + u);
-                o = acc_bit(d.acc, u) ? max(mu, u + 1) : mu;
-                b = __ldg(d.rrowptr + u);
-                len = __ldg(d.rrowptr + u + 1) - b;
-                if (SYNC) *rec_snap(d.rec + u, p_in) = 0;
-                atomicAnd(rec_flags(d.rec + u), ~CB(p_in));
-            }
-            const uint32_t incl = block_inclusive_scan(len, s_scan);
-            s_incl[threadIdx.x] = incl;
-            s_o[threadIdx.x] = o;
-            s_b[threadIdx.x] = b - (incl - len); // reader j of pair p is rcol[s_b[owner] + p]
-            __syncthreads();
-            const uint32_t total = s_incl[255];
-            for (uint32_t p0 = 0; p0 < total; p0 += 256) {
-                const uint32_t p = p0 + threadIdx.x;
-                const bool act = p < total;
-                uint32_t w = 0, ob = 0, fold = FB(p_out), mold = 0xFFFFFFFFu;
-                if (act) {
-                    uint32_t lo = 0, hi = 255; // the owner: first entry with s_incl > p
-                    while (lo < hi) {
-                        const uint32_t mid = (lo + hi) >> 1;
-                        if (s_incl[mid] > p) hi = mid;
-                        else lo = mid + 1;
-                    }
-                    ob = s_o[lo];
-                    const uint32_t j = s_b[lo] + p; // 32-bit wrap-around is intended: j = b + (p - excl)
-                    w = __ldg(d.rcol + j);
-                    fold = atomicOr(rec_flags(d.rec + w), FB(p_out)); // both atomics in flight together
-                    mold = atomicMax(d.mval + w, ob);
+        // chunks of RC_ENTRIES listed vertices per block (RC_E per thread, loaded
+        // together); their (vertex, reader) pairs are spread evenly over the block's
+        // threads, RC_P pairs per thread per step with all their loads and atomics
+        // in flight before any result is used
+        for (uint64_t c0 = (uint64_t)blockIdx.x * RC_ENTRIES; c0 < nl; c0 += (uint64_t)gridDim.x * RC_ENTRIES) {
+            // each thread reads RC_E listed vertices and consumes their snapshots
+            // and list flags (nothing else reads them in this round)
+            uint32_t o[RC_E], b[RC_E], len[RC_E];
+#pragma unroll
+            for (int k = 0; k < RC_E; ++k) {
+                const uint64_t i = c0 + threadIdx.x * RC_E + k;
+                o[k] = b[k] = len[k] = 0;
+                if (i < nl) {
+                    const uint32_t u = __ldg(list + i);
+                    const uint32_t mu = SYNC ? *(volatile uint32_t *)rec_snap(d.rec + u, p_in)
+                                             : *(volatile uint32_t *)(d.mval + u);
+                    o[k] = acc_bit(d.acc, u) ? max(mu, u + 1) : mu;
+                    b[k] = __ldg(d.rrowptr + u);
+                    len[k] = __ldg(d.rrowptr + u + 1) - b[k];
+                    if (SYNC) *rec_snap(d.rec + u, p_in) = 0;
+                    atomicAnd(rec_flags(d.rec + u), ~CB(p_in));
                 }
-                const bool raised = act && ob > mold;
-                uint32_t cold = CB(p_out);
-                if (raised) { // the record's sector is in L2 by now
-                    if (SYNC) atomicMax(rec_snap(d.rec + w, p_out), ob);
-                    cold = atomicOr(rec_flags(d.rec + w), CB(p_out));
-                    if (d.comp) { // batched: this graph changed in this round
-                        const uint32_t c = __ldg(d.comp + w);
+            }
+            uint32_t tot = 0;
+#pragma unroll
+            for (int k = 0; k < RC_E; ++k) tot += len[k];
+            uint32_t run = block_inclusive_scan(tot, s_scan) - tot; // pairs before this thread's entries
+#pragma unroll
+            for (int k = 0; k < RC_E; ++k) {
+                const uint32_t e = threadIdx.x * RC_E + k;
+                s_o[e] = o[k];
+                s_b[e] = b[k] - run; // reader of pair p is rcol[s_b[owner] + p] (32-bit wrap intended)
+                run += len[k];
+                s_incl[e] = run;
+            }
+            __syncthreads();
+            const uint32_t total = s_incl[RC_ENTRIES - 1];
+            for (uint32_t p0 = 0; p0 < total; p0 += 256 * RC_P) {
+                uint32_t w[RC_P], ob[RC_P], fold[RC_P], mold[RC_P];
+                bool act[RC_P];
+#pragma unroll
+                for (int j = 0; j < RC_P; ++j) {
+                    const uint32_t p = p0 + j * 256 + threadIdx.x;
+                    act[j] = p < total;
+                    w[j] = 0;
+                    ob[j] = 0;
+                    if (act[j]) {
+                        uint32_t lo = 0, hi = RC_ENTRIES - 1; // the owner: first entry with s_incl > p
+                        while (lo < hi) {
+                            const uint32_t mid = (lo + hi) >> 1;
+                            if (s_incl[mid] > p) hi = mid;
+                            else lo = mid + 1;
+                        }
+                        ob[j] = s_o[lo];
+                        const uint32_t jj = s_b[lo] + p; // 32-bit arithmetic: jj = b + (p - excl)
+                        w[j] = __ldg(d.rcol + jj);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < RC_P; ++j) {
+                    fold[j] = FB(p_out);
+                    mold[j] = 0xFFFFFFFFu;
+                    if (act[j]) {
+                        fold[j] = atomicOr(rec_flags(d.rec + w[j]), FB(p_out));
+                        mold[j] = atomicMax(d.mval + w[j], ob[j]);
+                    }
+                }
+                uint32_t cold[RC_P];
+#pragma unroll
+                for (int j = 0; j < RC_P; ++j) {
+                    cold[j] = CB(p_out);
+                    if (act[j] && ob[j] > mold[j]) { // raised; the record's sector is in L2 by now
+                        if (SYNC) atomicMax(rec_snap(d.rec + w[j], p_out), ob[j]);
+                        cold[j] = atomicOr(rec_flags(d.rec + w[j]), CB(p_out));
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < RC_P; ++j) {
+                    const bool raised = act[j] && ob[j] > mold[j];
+                    if (raised && d.comp) { // batched: this graph changed in this round
+                        const uint32_t c = __ldg(d.comp + w[j]);
                         if (*(volatile uint32_t *)&d.cs[c].last_change < rr) atomicMax(&d.cs[c].last_change, rr);
                     }
+                    stage_append<3>(st, 0, act[j] && !(fold[j] & FB(p_out)), w[j], dst, ctr);
+                    stage_append<3>(st, 1, raised && !(cold[j] & CB(p_out)), w[j], dst, ctr);
+                    stage_append<3>(st, 2, raised && mold[j] == 0, w[j], dst, ctr);
                 }
-                stage_append<3>(st, 0, act && !(fold & FB(p_out)), w, dst, ctr);
-                stage_append<3>(st, 1, raised && !(cold & CB(p_out)), w, dst, ctr);
-                stage_append<3>(st, 2, raised && mold == 0, w, dst, ctr);
             }
             __syncthreads(); // before the shared arrays are refilled
         }
