@@ -815,15 +815,18 @@ __global__ void __launch_bounds__(256, 4) k_rounds(const Dev d)
         // together); their (vertex, reader) pairs are spread evenly over the block's
         // threads, RC_P pairs per thread per step with all their loads and atomics
         // in flight before any result is used
-        for (uint64_t c0 = (uint64_t)blockIdx.x * RC_ENTRIES; c0 < nl; c0 += (uint64_t)gridDim.x * RC_ENTRIES) {
-            // each thread reads RC_E listed vertices and consumes their snapshots
-            // and list flags (nothing else reads them in this round)
+        // every block takes an even contiguous share of the list
+        const uint64_t per = (nl + gridDim.x - 1) / gridDim.x;
+        const uint64_t beg = (uint64_t)blockIdx.x * per, end = min((uint64_t)nl, beg + per);
+        for (uint64_t c0 = beg; c0 < end; c0 += RC_ENTRIES) {
+            // each thread reads up to RC_E listed vertices and consumes their
+            // snapshots and list flags (nothing else reads them in this round)
             uint32_t o[RC_E], b[RC_E], len[RC_E];
 #pragma unroll
             for (int k = 0; k < RC_E; ++k) {
                 const uint64_t i = c0 + threadIdx.x * RC_E + k;
                 o[k] = b[k] = len[k] = 0;
-                if (i < nl) {
+                if (i < end) {
                     const uint32_t u = __ldg(list + i);
                     const uint32_t mu = SYNC ? *(volatile uint32_t *)rec_snap(d.rec + u, p_in)
                                              : *(volatile uint32_t *)(d.mval + u);
