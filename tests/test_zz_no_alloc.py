@@ -50,11 +50,12 @@ def _static(pkg, g, sched, on_device):
     return r, out
 
 
-def _same(a, b):
+def _same(a, b, sched=0):
     ra, ma = a
     rb, mb = b
-    assert (ra.verdict, ra.witness, ra.outer, ra.rounds, ra.inner_iters, ra.relaxations, ra.edges_total) == (
-        rb.verdict, rb.witness, rb.outer, rb.rounds, rb.inner_iters, rb.relaxations, rb.edges_total)
+    assert (ra.verdict, ra.witness, ra.outer, ra.edges_total) == (rb.verdict, rb.witness, rb.outer, rb.edges_total)
+    if sched == 0:  # the asynchronous schedule's sweep and relaxation counts depend on timing
+        assert (ra.rounds, ra.inner_iters, ra.relaxations) == (rb.rounds, rb.inner_iters, rb.relaxations)
     assert np.array_equal(ma, mb)
 
 
@@ -76,8 +77,8 @@ def test_matches_map_run_on_two_calls_in_a_row(pkg, name, make, sched):
     for on_device in (False, True):
         first = _static(pkg, g, sched, on_device)
         second = _static(pkg, g, sched, on_device)
-        _same(first, want)
-        _same(second, want)
+        _same(first, want, sched)
+        _same(second, want, sched)
 
 
 def test_a_larger_then_a_smaller_graph(pkg):
