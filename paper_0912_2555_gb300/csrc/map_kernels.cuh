@@ -768,9 +768,9 @@ __device__ __forceinline__ bool grid_barrier(Ctl *ctl)
     return s_ok != 0;
 }
 
-constexpr int RC_E = 4;                 // listed vertices per thread and chunk
+constexpr int RC_E = 1;                 // listed vertices per thread and chunk
 constexpr int RC_ENTRIES = 256 * RC_E;  // per block and chunk
-constexpr int RC_P = 4;                 // push pairs per thread and step
+constexpr int RC_P = 1;                 // push pairs per thread and step
 
 // The fix-point loop of one outer iteration: rounds 2, 3, ... until a round
 // changes nothing.  Round r reads list[(r-1) % 3] and appends to list[r % 3];
