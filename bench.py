@@ -34,6 +34,28 @@ WORKLOAD = dict(workload="layered-2^26v-4000L", n=1 << 26, layers=4000, seed=3, 
 METRIC = "MAP edge relaxations/s (GTEPS)"
 
 
+# DRAM traffic of one k_dense launch from the ncu capture summarised in
+# profiles/k_dense_layered-2p24.md (dram__bytes_read.sum + dram__bytes_write.sum on the 2^24-vertex
+# case, whose algorithmic bytes are 402,663,176); valid only for the kernel source it was taken on.
+DENSE_TRAFFIC = {"kernel_file_sha256_16": "6290ec13dfa9a331", "bytes": 394_429_696,
+                 "algorithmic_bytes": 402_663_176, "case": "layered 2^24 vertices, m = 67,111,361"}
+
+
+def _dense_traffic(dense_bytes):
+    import hashlib
+
+    path = os.path.join(ROOT, "paper_0912_2555_gb300", "csrc", "map_kernels.cuh")
+    try:
+        sha = hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None, "kernel source not found"
+    if sha != DENSE_TRAFFIC["kernel_file_sha256_16"]:
+        return None, "kernel changed since the ncu capture"
+    scale = dense_bytes / DENSE_TRAFFIC["algorithmic_bytes"]
+    return DENSE_TRAFFIC["bytes"] * scale, (f"ncu capture on {DENSE_TRAFFIC['case']}, scaled by the ratio of "
+                                             f"algorithmic bytes ({scale:.3f})")
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -327,8 +349,9 @@ def main():
     peaks = _peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     achieved = dense_bytes * dense_launches / (dense_ms / 1e3) / 1e9 if dense_ms > 0 else None
+    traffic, traffic_note = _dense_traffic(dense_bytes)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "traffic": None,
+                "frac": achieved / peak if achieved else None, "traffic": traffic, "traffic_note": traffic_note,
                 "kernel": "k_dense (round 1 of each outer iteration)", "bytes_per_launch": dense_bytes,
                 "launch_ms": dense_ms / max(dense_launches, 1),
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s",
