@@ -428,6 +428,12 @@ int create_graph(uint32_t n, uint64_t m, cudaStream_t s, const char *who, Upload
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_r, mapk::k_rounds<true>, 256, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, mapk::k_rounds<false>, 256, 0);
     occ_r = std::max(1, std::min(occ_r, occ_a));
+    // launch shape of the fix-point kernel: MAPGPU_ROUNDS_BLOCKS_PER_SM (1 .. the occupancy
+    // limit) overrides the default of every resident slot
+    if (const char *e = getenv("MAPGPU_ROUNDS_BLOCKS_PER_SM")) {
+        const int v = atoi(e);
+        if (v >= 1 && v < occ_r) occ_r = v;
+    }
     g->rounds_grid = (int)std::min<uint64_t>(((uint64_t)n + 255) / 256, (uint64_t)g->sms * occ_r);
     g->check_grid = (int)std::min<uint64_t>(((uint64_t)n + 255) / 256, (uint64_t)g->sms * 4);
     g->hist_cap = 1u << 16;
