@@ -31,7 +31,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC,-fvisibility=hidden",
+    extra = os.environ.get("MAPGPU_NVCC_FLAGS", "").split()  # e.g. launch-shape experiments
+    cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC,-fvisibility=hidden", *extra,
            "-cudart", "static", "-Xlinker", "--exclude-libs,ALL", "-I", os.path.join(ROOT, "include"),
            "-o", tmp] + [os.path.join(CSRC, f) for f in SOURCES]
     if verbose:

@@ -519,7 +519,11 @@ constexpr int WT_ROWS = 128;
 constexpr int WT_UNROLL = 4;
 constexpr size_t DT_SMEM = 0; // static shared memory only
 
-__global__ void __launch_bounds__(DT_THREADS, 4) k_dense(const Dev d, Handles hd)
+#ifndef MAPGPU_DENSE_MIN_BLOCKS
+#define MAPGPU_DENSE_MIN_BLOCKS 4
+#endif
+
+__global__ void __launch_bounds__(DT_THREADS, MAPGPU_DENSE_MIN_BLOCKS) k_dense(const Dev d, Handles hd)
 {
     __shared__ __align__(16) uint32_t s_rp[WT_WARPS][WT_ROWS + 4];
     __shared__ __align__(16) uint32_t s_best[WT_WARPS][WT_ROWS];
@@ -776,8 +780,12 @@ constexpr int RC_P = 1;                 // push pairs per thread and step
 // changes nothing.  Round r reads list[(r-1) % 3] and appends to list[r % 3];
 // the counters of list[(r+1) % 3] (read in round r-1, appended again in round
 // r+1) are reset by block 0 during round r, so one barrier per round suffices.
+#ifndef MAPGPU_ROUNDS_MIN_BLOCKS
+#define MAPGPU_ROUNDS_MIN_BLOCKS 6 // resident blocks per SM the register budget is sized for (measured best)
+#endif
+
 template <bool SYNC>
-__global__ void __launch_bounds__(256, 4) k_rounds(const Dev d)
+__global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const Dev d)
 {
     __shared__ uint32_t s_stage[8][3 * SB_ENTRIES];
     __shared__ uint32_t s_cnt[8][3], s_base[3];
