@@ -520,7 +520,7 @@ constexpr int WT_UNROLL = 4;
 constexpr size_t DT_SMEM = 0; // static shared memory only
 
 #ifndef MAPGPU_DENSE_MIN_BLOCKS
-#define MAPGPU_DENSE_MIN_BLOCKS 4
+#define MAPGPU_DENSE_MIN_BLOCKS 6 // resident blocks per SM the register budget is sized for (measured best)
 #endif
 
 __global__ void __launch_bounds__(DT_THREADS, MAPGPU_DENSE_MIN_BLOCKS) k_dense(const Dev d, Handles hd)
@@ -790,6 +790,8 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
     __shared__ uint32_t s_stage[8][3 * SB_ENTRIES];
     __shared__ uint32_t s_cnt[8][3], s_base[3];
     __shared__ uint32_t s_incl[RC_ENTRIES], s_o[RC_ENTRIES], s_b[RC_ENTRIES], s_scan[8];
+    __shared__ uint32_t *s_dst[3][2];
+    __shared__ unsigned int *s_ctr[3];
     Ctl *ctl = d.ctl;
     volatile Ctl *vc = ctl;
     const unsigned lane = lane_id();
@@ -810,9 +812,20 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
         const uint32_t *__restrict__ list = pick3(p_in, d.list);
         uint32_t *const list_out = pick3(p_out, d.list);
         uint32_t *const flist_out = pick3(p_out, d.flist);
-        // appends: 0 = this round's frontier, 1 = changed vertices, 2 = newly touched vertices
-        uint32_t *const dst[3][2] = {{flist_out, nullptr}, {list_out, nullptr}, {d.touched, nullptr}};
-        unsigned int *const ctr[3] = {&ctl->fcnt[p_out].v, &ctl->lcnt[p_out].v, &ctl->tcnt.v};
+        // appends: 0 = this round's frontier, 1 = changed vertices, 2 = newly touched vertices.
+        // Their destinations live in shared memory (read only when a buffer is flushed), which
+        // keeps registers free for occupancy; the first read comes after a __syncthreads.
+        if (threadIdx.x == 0) {
+            s_dst[0][0] = flist_out;
+            s_dst[1][0] = list_out;
+            s_dst[2][0] = d.touched;
+            s_dst[0][1] = s_dst[1][1] = s_dst[2][1] = nullptr;
+            s_ctr[0] = &ctl->fcnt[p_out].v;
+            s_ctr[1] = &ctl->lcnt[p_out].v;
+            s_ctr[2] = &ctl->tcnt.v;
+        }
+        uint32_t *(*const dst)[2] = s_dst;
+        unsigned int **const ctr = s_ctr;
         Stage<3> st;
         st.buf = s_stage[threadIdx.x >> 5];
         st.cnt[0] = st.cnt[1] = st.cnt[2] = 0;
