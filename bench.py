@@ -113,6 +113,22 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def replica_value(ms, edges, device="cuda"):
+    """Whole-job GTEPS of independent replicas (one per rank): the edges all ranks processed
+    over the slowest rank's time.  Returns (GTEPS, slowest ms, total edges)."""
+    import torch.distributed as dist
+
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        import torch
+
+        t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e = torch.tensor([float(edges)], dtype=torch.float64, device=device)
+        dist.all_reduce(e, op=dist.ReduceOp.SUM)
+        ms, edges = float(t.item()), float(e.item())
+    return edges / (ms / 1e3) / 1e9, ms, edges
+
+
 def dist_init():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -331,12 +347,7 @@ def main():
     if ws > 1:
         dist.barrier()
     ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    edges = sum(r.edges_total for r in results)
-    value = edges * ws / (ms / 1e3) / 1e9
+    value, ms, _ = replica_value(ms, sum(r.edges_total for r in results), device="cuda")
 
     # roofline of the dominant kernel (the dense round): algorithmic bytes per launch over its
     # CUDA-event time.  Events cannot sit inside the graph's loop bodies, so this pass runs
@@ -391,7 +402,7 @@ def main():
             "roofline": roofline, "phases": phases, "e2e": e2e, "gpu_launches": sum(r.launches for r in results),
             "clocks": clk.summary()}
     pkg.map_destroy(h)
-    if not args.no_batch and args.n is None:
+    if not args.no_batch and args.n is None and ws == 1:
         line["batched"] = batched_leg(pkg, np, torch, stream, sched=args.sched)
     if not args.no_serve and args.n is None and ws == 1:
         line["serving"] = serving_leg(pkg, np)
