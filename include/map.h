@@ -72,6 +72,13 @@ enum { MAP_SCHED_SYNC = 0, MAP_SCHED_ASYNC = 1 };
 #define MAP_FLAG_PROFILE 1u /* step the loop from the host and time each phase with CUDA events
                                (result.dense_ms, round_ms, check_ms, frontier_rows) */
 
+#define MAP_FLAG_EARLY_EXIT 2u /* stop an outer iteration's propagation as soon as some vertex becomes its own
+                                  map value: values only grow and each is a real accepting successor, so that
+                                  vertex lies on an accepting cycle.  The verdict is the same; the witness is
+                                  an accepting vertex on a cycle (not necessarily the smallest the full
+                                  fix-point would give), the outer count may be smaller, and the round
+                                  counts are no longer canonical.  Single graphs only. */
+
 /* Called after the fix-point of every outer iteration, before the cycle test
  * and the elimination: map[v] is map(v) of that iteration (MAP_NONE if none),
  * host memory valid during the call only; rounds is that iteration's round

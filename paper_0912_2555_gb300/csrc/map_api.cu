@@ -611,6 +611,7 @@ static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint
     init.rounds_hist = g->hist;
     init.out = out_dev ? map_out : g->xbuf;
     init.use_graph = stepped ? 0 : 1;
+    init.early_exit = (opts.flags & MAP_FLAG_EARLY_EXIT) ? 1 : 0;
     init.timeout_ns = (uint64_t)(opts.timeout_ms ? opts.timeout_ms : 120000u) * 1000000ull;
     init.witness.v = mapk::NONE;
 
@@ -688,7 +689,7 @@ static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint
     res->verdict = c.verdict ? MAP_CYCLE : MAP_NO_CYCLE;
     res->witness = c.verdict ? c.witness.v : MAP_NONE;
     res->outer_iters = c.outer;
-    res->inner_canonical = sync_sched ? 1 : 0;
+    res->inner_canonical = (sync_sched && !c.early_hit) ? 1 : 0;
     res->inner_iters = c.inner_total;
     res->relaxations = c.relax.v;
     res->edges_total = g->m * (uint64_t)c.outer;
@@ -711,7 +712,7 @@ static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint
         CK(cudaStreamSynchronize(s));
         memcpy(map_out, g->h_stage, (size_t)n * 4);
     }
-    g->dirty = c.status != mapk::ST_OK;
+    g->dirty = c.status != mapk::ST_OK || c.early_hit;
     if (c.status == mapk::ST_LIMIT) return fail(MAP_ERR_LIMIT, "map_run: max_outer or max_inner reached");
     if (c.status == mapk::ST_TIMEOUT)
         return fail(MAP_ERR_TIMEOUT, "map_run: stopped after timeout_ms = %u", opts.timeout_ms ? opts.timeout_ms : 120000u);

@@ -69,6 +69,7 @@ struct Ctl {
     Cnt32 bar_count;       // grid barrier of k_rounds: arrivals
     Cnt32 bar_gen;         // ... and generation
     Cnt32 stop_req;        // k_rounds: block 0 asks every block to stop after the next barrier
+    Cnt32 self_seen;       // early exit: some vertex became its own map value
     // fix-point loop
     uint32_t k;            // rounds completed in the current outer iteration
     // outer loop
@@ -89,7 +90,9 @@ struct Ctl {
     uint64_t t0;           // %globaltimer at the start of the run (ns)
     uint64_t timeout_ns;   // the loop stops with ST_TIMEOUT past t0 + timeout_ns
     uint32_t use_graph;    // epilogues set the conditional handles
-    uint32_t pad[5];
+    uint32_t early_exit;   // stop the fix-point loop at the first self-mapped vertex
+    uint32_t early_hit;    // it did (the run's round state is then left dirty)
+    uint32_t pad[3];
 };
 
 struct Handles {
@@ -483,6 +486,8 @@ __global__ void k_run_begin(Ctl *c, Handles hd)
     v->frontier_rows.v = 0;
     v->bar_count.v = 0;
     v->stop_req.v = 0;
+    v->self_seen.v = 0;
+    v->early_hit = 0;
     v->k = 0;
     v->status = ST_OK;
     v->verdict = 0;
@@ -632,6 +637,7 @@ __global__ void __launch_bounds__(DT_THREADS, MAPGPU_DENSE_MIN_BLOCKS) k_dense(c
             if (got) {
                 best[lane * 4 + k] = 0;
                 *rec_snap(d.rec + v, 1) = bs[k];
+                if (bs[k] == v + 1) ctl->self_seen.v = 1; // v reaches itself: an accepting cycle
             }
             stage_append<1>(st, 0, got, v, dst, ctr);
         }
@@ -801,6 +807,8 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
     uint32_t status = ST_OK;
     uint32_t nl = vc->lcnt[1].v; // vertices that got a value in the dense round
     uint32_t r = 1;              // rounds completed
+    const bool early = vc->early_exit && !d.comp;
+    if (early && vc->self_seen.v) nl = 0; // the dense round already found a self-mapped vertex
     if (nl && max_inner < 2) status = ST_LIMIT;
     while (nl && status == ST_OK) {
         const uint32_t rr = r + 1; // this round
@@ -914,6 +922,7 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
 #pragma unroll
                 for (int j = 0; j < RC_P; ++j) {
                     const bool raised = act[j] && ob[j] > mold[j];
+                    if (raised && ob[j] == w[j] + 1) ctl->self_seen.v = 1; // w reaches itself
                     if (raised && d.comp) { // batched: this graph changed in this round
                         const uint32_t c = __ldg(d.comp + w[j]);
                         if (*(volatile uint32_t *)&d.cs[c].last_change < rr) atomicMax(&d.cs[c].last_change, rr);
@@ -934,6 +943,10 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
         r = rr;
         nl = vc->lcnt[p_out].v; // changed in this round
         frows += vc->fcnt[p_out].v;
+        if (early && nl && vc->self_seen.v) { // stop here: the cycle test will find the vertex
+            nl = 0;
+            if (lead) vc->early_hit = 1;
+        }
         if (vc->stop_req.v) status = ST_TIMEOUT;
         else if (nl && r + 1 > max_inner) status = ST_LIMIT;
     }

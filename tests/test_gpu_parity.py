@@ -223,3 +223,36 @@ def test_layered_64m_full_size(pkg):
     g = mapgen.layered_64m()
     got, want = assert_parity(pkg, g, 0, on_device=True, hashed=True)
     assert got.verdict == 0 and got.outer > 10
+
+
+@pytest.mark.parametrize("sched", [0, 1])
+def test_early_exit_mode(pkg, sched):
+    """MAP_FLAG_EARLY_EXIT: same verdict; a cycle's witness is accepting and lies on a cycle;
+    the outer count never exceeds the full algorithm's; no-cycle graphs are unaffected."""
+    from tests import _brute as bf
+
+    gs = [mapgen.random_16k("cycle"), mapgen.random_16k("nocycle"), mapgen.layered_graph(1 << 20, 62, seed=3),
+          mapgen.layered_graph(1 << 20, 62, seed=3, plant=True)]
+    for seed in range(40):
+        rng = np.random.default_rng(300 + seed)
+        gs.append(mapgen.tiny_graph(seed, int(rng.integers(2, 120)), max_deg=3, acc_p=0.3))
+    for g in gs:
+        want = oracle.run_graph(g)
+        h = pkg.map_create(g.n, g.rowptr, g.colidx if g.m else None, pkg.pack_bits(g.acc))
+        try:
+            final = np.empty(g.n, np.uint32)
+            got = pkg.map_run(h, sched=sched, flags=pkg.MAP_FLAG_EARLY_EXIT, map_out=final)
+            again = pkg.map_run(h, sched=sched)  # a normal run on the same handle after an early one
+        finally:
+            pkg.map_destroy(h)
+        assert got.verdict == want.verdict, g.name
+        assert got.outer <= want.outer
+        assert (again.verdict, again.witness, again.outer) == (want.verdict, want.witness, want.outer)
+        if sched == 0:
+            assert (again.rounds, again.relaxations) == (want.rounds, want.relaxations)
+        if got.verdict == 1:
+            _, on_cycle = bf.tarjan_verdict(g.n, g.rowptr, g.colidx, g.acc)
+            assert g.acc[got.witness] and on_cycle[got.witness]
+        else:
+            assert (got.outer, got.witness) == (want.outer, want.witness)
+            assert np.array_equal(final, want.map)
