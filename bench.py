@@ -193,6 +193,9 @@ def batched_leg(pkg, np, torch, stream, count=256, steps=2, sched=0):
     singles = [pkg.map_create(it[0], it[1], it[2], it[3], stream) for it in items]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     try:
+        t_tune = time.perf_counter()
+        tune = pkg.map_autotune(hb, sched)  # launch shapes for this batch, by measurement
+        t_tune = time.perf_counter() - t_tune
         res = pkg.map_batch_run(hb, count, sched=sched)  # warm-up (builds the graph)
         for h in singles:
             pkg.map_run(h, sched=sched)
@@ -223,7 +226,7 @@ def batched_leg(pkg, np, torch, stream, count=256, steps=2, sched=0):
             "batch_ms": batch_ms, "sequential_ms": seq_ms,
             "jobs_per_s_batched": count / (batch_ms / 1e3), "jobs_per_s_sequential": count / (seq_ms / 1e3),
             "speedup": seq_ms / batch_ms, "gteps_batched": edges / (batch_ms / 1e3) / 1e9,
-            "results_identical": bool(same)}
+            "results_identical": bool(same), "autotune": dict(tune, seconds=t_tune)}
 
 
 def serving_leg(pkg, np, rates=(100, 500, 2000), jobs=150, slots=8):

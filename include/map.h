@@ -217,6 +217,24 @@ MAP_API int map_submit(map_server *sv, uint32_t n, const uint32_t *rowptr, const
 MAP_API int map_poll(map_server *sv, uint64_t job_id, map_result *res, uint32_t *map_out);
 MAP_API int map_server_destroy(map_server *sv);
 
+/*
+ * map_autotune -- pick the launch shapes of a handle (single graph or batch) by
+ * measurement.  The dense-round kernel and the fix-point kernel are timed with
+ * CUDA events on full runs of this very graph, at several numbers of resident
+ * blocks per SM (up to each kernel's occupancy limit).  The fastest shape of
+ * each is kept for later runs of the handle.  It takes about a dozen runs;
+ * results are unaffected (only the launch shapes change).
+ */
+typedef struct {
+    uint32_t dense_blocks_per_sm;  /* chosen shape of the dense-round kernel */
+    uint32_t rounds_blocks_per_sm; /* chosen shape of the fix-point kernel */
+    double dense_ms;               /* its dense-round time per run at that shape */
+    double rounds_ms;              /* its fix-point time per run at that shape */
+    uint32_t trials;               /* runs made */
+    uint32_t reserved;
+} map_tune_result;
+MAP_API int map_autotune(map_graph *g, uint32_t sched, map_tune_result *out);
+
 /* map_graph_info -- n and m of a graph (either pointer may be NULL). */
 MAP_API int map_graph_info(const map_graph *g, uint32_t *n, uint64_t *m);
 

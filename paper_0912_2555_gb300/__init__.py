@@ -32,7 +32,8 @@ STATUS_NAMES = ["MAP_OK", "MAP_ERR_ARG", "MAP_ERR_CSR", "MAP_ERR_OOM", "MAP_ERR_
 
 # exported symbols of include/map.h (checked by the tests)
 EXPORTS = ["map_create", "map_run", "map_destroy", "map_graph_info", "map_last_error", "map_run_static",
-           "map_batch_create", "map_batch_run", "map_server_create", "map_submit", "map_poll", "map_server_destroy"]
+           "map_batch_create", "map_batch_run", "map_server_create", "map_submit", "map_poll", "map_server_destroy",
+           "map_autotune"]
 MAP_STATIC_MAX_N = 65536
 MAP_STATIC_MAX_M = 524288
 
@@ -77,6 +78,28 @@ class MapResult(ctypes.Structure):
     ]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [
+        ("dense_blocks_per_sm", ctypes.c_uint32),
+        ("rounds_blocks_per_sm", ctypes.c_uint32),
+        ("dense_ms", ctypes.c_double),
+        ("rounds_ms", ctypes.c_double),
+        ("trials", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
+    ]
+
+
+def map_autotune(handle, sched: int = MAP_SCHED_SYNC) -> dict:
+    """Pick the handle's launch shapes by measurement (see include/map.h)."""
+    lib = load()
+    t = TuneResult()
+    rc = lib.map_autotune(handle, sched, ctypes.byref(t))
+    if rc != MAP_OK:
+        raise MapError(rc, "map_autotune", last_error())
+    return {"dense_blocks_per_sm": t.dense_blocks_per_sm, "rounds_blocks_per_sm": t.rounds_blocks_per_sm,
+            "dense_ms": t.dense_ms, "rounds_ms": t.rounds_ms, "trials": t.trials}
+
+
 class MapError(RuntimeError):
     def __init__(self, code: int, what: str, msg: str):
         self.code = code
@@ -108,8 +131,9 @@ def load(path: str = LIB_PATH):
     lib.map_submit.argtypes = [vp, u32, vp, vp, vp, ctypes.POINTER(MapOpts), ctypes.POINTER(ctypes.c_uint64)]
     lib.map_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(MapResult), vp]
     lib.map_server_destroy.argtypes = [vp]
+    lib.map_autotune.argtypes = [vp, u32, ctypes.POINTER(TuneResult)]
     for f in ("map_create", "map_run", "map_destroy", "map_graph_info", "map_run_static", "map_batch_create",
-              "map_batch_run", "map_server_create", "map_submit", "map_poll", "map_server_destroy"):
+              "map_batch_run", "map_server_create", "map_submit", "map_poll", "map_server_destroy", "map_autotune"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib

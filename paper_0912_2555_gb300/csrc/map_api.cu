@@ -729,6 +729,73 @@ int map_run(map_graph *g, const map_opts *opts, map_result *res, uint32_t *map_o
     return rc;
 }
 
+// Launch shapes of a handle: blocks per SM of the dense-round and fix-point kernels.
+static void set_shapes(map_graph *g, uint32_t dense_bps, uint32_t rounds_bps)
+{
+    const uint64_t ntiles = ((uint64_t)g->n + mapk::WT_ROWS - 1) / mapk::WT_ROWS;
+    g->dense_grid = (int)std::max<uint64_t>(
+        1, std::min<uint64_t>((ntiles + mapk::WT_WARPS - 1) / mapk::WT_WARPS, (uint64_t)g->sms * dense_bps));
+    g->rounds_grid = (int)std::max<uint64_t>(
+        1, std::min<uint64_t>(((uint64_t)g->n + 255) / 256, (uint64_t)g->sms * rounds_bps));
+    for (int i = 0; i < 2; ++i) { // the captured graphs hold the old shapes
+        if (g->exec[i]) cudaGraphExecDestroy(g->exec[i]);
+        if (g->graph[i]) cudaGraphDestroy(g->graph[i]);
+        g->exec[i] = nullptr;
+        g->graph[i] = nullptr;
+    }
+}
+
+int map_autotune(map_graph *g, uint32_t sched, map_tune_result *out)
+{
+    g_err.clear();
+    if (!g || !out) return fail(MAP_ERR_ARG, "map_autotune: NULL handle or result");
+    if (sched > MAP_SCHED_ASYNC) return fail(MAP_ERR_ARG, "map_autotune: unknown schedule %u", sched);
+    int occ_d = 0, occ_r = 0, occ_a = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_d, mapk::k_dense, mapk::DT_THREADS, mapk::DT_SMEM));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_r, mapk::k_rounds<true>, 256, 0));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, mapk::k_rounds<false>, 256, 0));
+    occ_r = std::min(occ_r, occ_a);
+    memset(out, 0, sizeof *out);
+    map_opts o;
+    memset(&o, 0, sizeof o);
+    o.sched = sched;
+    o.flags = MAP_FLAG_PROFILE; // host-stepped run, CUDA events around every phase
+    map_result r;
+    // the dense-round shape first (with the fix-point shape as it is), then the fix-point shape
+    const uint32_t cands[] = {1, 2, 3, 4, 6, 8};
+    uint32_t best_d = 0, best_r = 0;
+    double t_d = 1e30, t_r = 1e30;
+    const uint32_t cur_r = (uint32_t)std::max(1, (g->rounds_grid + g->sms - 1) / g->sms);
+    for (uint32_t bps : cands) {
+        if ((int)bps > occ_d) continue;
+        set_shapes(g, bps, cur_r);
+        const int rc = run_impl(g, &o, &r, nullptr);
+        if (rc != MAP_OK) return rc;
+        out->trials++;
+        if (r.dense_ms < t_d) {
+            t_d = r.dense_ms;
+            best_d = bps;
+        }
+    }
+    for (uint32_t bps : cands) {
+        if ((int)bps > occ_r) continue;
+        set_shapes(g, best_d, bps);
+        const int rc = run_impl(g, &o, &r, nullptr);
+        if (rc != MAP_OK) return rc;
+        out->trials++;
+        if (r.round_ms < t_r) {
+            t_r = r.round_ms;
+            best_r = bps;
+        }
+    }
+    set_shapes(g, best_d, best_r);
+    out->dense_blocks_per_sm = best_d;
+    out->rounds_blocks_per_sm = best_r;
+    out->dense_ms = t_d;
+    out->rounds_ms = t_r;
+    return MAP_OK;
+}
+
 int map_batch_create(uint32_t count, const uint32_t *ns, const uint32_t *const *rowptrs,
                      const uint32_t *const *colidxs, const uint32_t *const *acc_bits, void *cuda_stream,
                      map_graph **out)

@@ -101,3 +101,29 @@ def test_batch_handle_refused_by_map_run(pkg):
         pkg.map_batch_create([(2, np.array([0, 1, 1], np.uint32), np.array([2], np.uint32), np.array([1], np.uint32)),
                               (1, np.array([0, 0], np.uint32), None, np.array([1], np.uint32))])
     assert e.value.code == pkg.MAP_ERR_CSR
+
+
+def test_autotune_keeps_results(pkg):
+    """map_autotune only changes launch shapes: results before and after are identical."""
+    gs = _mixed_graphs()[-8:]
+    h = pkg.map_batch_create([(g.n, g.rowptr, g.colidx if g.m else None, pkg.pack_bits(g.acc)) for g in gs])
+    try:
+        before = pkg.map_batch_run(h, len(gs))
+        tune = pkg.map_autotune(h)
+        after = pkg.map_batch_run(h, len(gs))
+    finally:
+        pkg.map_destroy(h)
+    assert tune["trials"] >= 2 and tune["dense_blocks_per_sm"] >= 1 and tune["rounds_blocks_per_sm"] >= 1
+    for a, b in zip(before, after):
+        assert (a.verdict, a.witness, a.outer, a.rounds, a.relaxations) == (
+            b.verdict, b.witness, b.outer, b.rounds, b.relaxations)
+    g = mapgen.random_16k("nocycle")
+    h = pkg.map_create(g.n, g.rowptr, g.colidx, pkg.pack_bits(g.acc))
+    try:
+        want = oracle.run_graph(g)
+        pkg.map_autotune(h)
+        r = pkg.map_run(h)
+        assert (r.verdict, r.outer, r.rounds, r.relaxations) == (want.verdict, want.outer, want.rounds,
+                                                                 want.relaxations)
+    finally:
+        pkg.map_destroy(h)
