@@ -235,6 +235,24 @@ typedef struct {
 } map_tune_result;
 MAP_API int map_autotune(map_graph *g, uint32_t sched, map_tune_result *out);
 
+/*
+ * map_lasso -- a counterexample for a cycle verdict (Section 5 of the paper
+ * names counterexample generation as missing from the tool): a lasso that
+ * leads from `init` to the accepting witness and around a cycle back to it,
+ * found by breadth-first search along rows (successors in G) on the device.
+ *   witness  an accepting vertex on a cycle (map_result.witness of a CYCLE run)
+ *   init     start of the prefix, or MAP_NONE for the cycle alone
+ *   path     host array of cap entries: the prefix init .. (before the witness),
+ *            *prefix_len vertices, then the cycle witness .. witness,
+ *            *cycle_len vertices (first == last); each step is an edge of G.
+ *            Both parts are shortest.
+ * Uses the handle's work space (not while a run is in flight on it).
+ * MAP_ERR_ARG if the witness is not reachable as asked; MAP_ERR_LIMIT if the
+ * path does not fit into cap entries.  Single graphs only.
+ */
+MAP_API int map_lasso(map_graph *g, uint32_t init, uint32_t witness, uint32_t *path, uint32_t cap,
+                      uint32_t *prefix_len, uint32_t *cycle_len);
+
 /* map_graph_info -- n and m of a graph (either pointer may be NULL). */
 MAP_API int map_graph_info(const map_graph *g, uint32_t *n, uint64_t *m);
 

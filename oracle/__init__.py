@@ -116,3 +116,51 @@ def run(n: int, rowptr, colidx, acc, max_outer: int = 0, keep_trace: bool = Fals
 def run_graph(g, **kw) -> OracleResult:
     """Run the oracle on a ``mapgen.Graph``."""
     return run(g.n, g.rowptr, g.colidx, g.acc, **kw)
+
+
+# ---------------------------------------------------------------------------
+# Counterexamples (the lasso behind a cycle verdict).  Section 5 of the paper
+# names counterexample generation as missing; a lasso is the standard form
+# of an LTL counterexample: a path from the initial vertex to an accepting
+# vertex, then a cycle through that vertex.  Shortest paths are not unique, so
+# the oracle fixes what is: the lengths.  Plain breadth-first search.
+# ---------------------------------------------------------------------------
+
+def bfs_dist(n, rowptr, colidx, source):
+    """Edge count of a shortest path source -> v along rows (successors) for every v (an int64
+    array); -1 if none.  Level by level: the unseen successors of level d form level d + 1."""
+    rowptr = np.asarray(rowptr, np.int64)
+    colidx = np.asarray(colidx, np.int64)
+    dist = np.full(n, -1, np.int64)
+    dist[source] = 0
+    level, front = 0, np.array([source], np.int64)
+    while front.size:
+        level += 1
+        b, e = rowptr[front], rowptr[front + 1]
+        cnt = e - b
+        first = np.cumsum(cnt) - cnt  # where each frontier row's successors start in succ
+        succ = colidx[np.repeat(b - first, cnt) + np.arange(int(cnt.sum()))]
+        new = np.unique(succ[dist[succ] < 0])
+        dist[new] = level
+        front = new
+    return dist
+
+
+def lasso_lengths(n, rowptr, colidx, witness, init=None):
+    """(prefix edges, cycle edges) of a shortest lasso: dist(init, witness) (0 without init or when
+    init is the witness) and the shortest cycle through the witness, 1 + min dist(witness, u) over
+    the edges u -> witness; None for a part that does not exist."""
+    rowptr = np.asarray(rowptr, np.int64)
+    colidx = np.asarray(colidx, np.int64)
+    d = bfs_dist(n, rowptr, colidx, witness)
+    cyc = None
+    for j in np.nonzero(colidx == witness)[0]:  # the edges u -> witness
+        u = int(np.searchsorted(rowptr, j, side="right")) - 1  # the row holding position j
+        if d[u] >= 0:
+            cyc = int(d[u]) + 1 if cyc is None else min(cyc, int(d[u]) + 1)
+    if init is None or init == witness:
+        pre = 0
+    else:
+        pre = int(bfs_dist(n, rowptr, colidx, init)[witness])
+        pre = None if pre < 0 else pre
+    return pre, cyc

@@ -33,7 +33,7 @@ STATUS_NAMES = ["MAP_OK", "MAP_ERR_ARG", "MAP_ERR_CSR", "MAP_ERR_OOM", "MAP_ERR_
 # exported symbols of include/map.h (checked by the tests)
 EXPORTS = ["map_create", "map_run", "map_destroy", "map_graph_info", "map_last_error", "map_run_static",
            "map_batch_create", "map_batch_run", "map_server_create", "map_submit", "map_poll", "map_server_destroy",
-           "map_autotune"]
+           "map_autotune", "map_lasso"]
 MAP_STATIC_MAX_N = 65536
 MAP_STATIC_MAX_M = 524288
 
@@ -100,6 +100,17 @@ def map_autotune(handle, sched: int = MAP_SCHED_SYNC) -> dict:
             "dense_ms": t.dense_ms, "rounds_ms": t.rounds_ms, "trials": t.trials}
 
 
+def map_lasso(handle, witness: int, init: int = MAP_NONE, cap: int = 1 << 20):
+    """Counterexample for a cycle verdict: (prefix list, cycle list) -- see include/map.h."""
+    lib = load()
+    path = np.zeros(cap, np.uint32)
+    pl, cl = ctypes.c_uint32(), ctypes.c_uint32()
+    rc = lib.map_lasso(handle, init, witness, path.ctypes.data, cap, ctypes.byref(pl), ctypes.byref(cl))
+    if rc != MAP_OK:
+        raise MapError(rc, "map_lasso", last_error())
+    return [int(x) for x in path[:pl.value]], [int(x) for x in path[pl.value:pl.value + cl.value]]
+
+
 class MapError(RuntimeError):
     def __init__(self, code: int, what: str, msg: str):
         self.code = code
@@ -132,8 +143,10 @@ def load(path: str = LIB_PATH):
     lib.map_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(MapResult), vp]
     lib.map_server_destroy.argtypes = [vp]
     lib.map_autotune.argtypes = [vp, u32, ctypes.POINTER(TuneResult)]
+    lib.map_lasso.argtypes = [vp, u32, u32, vp, u32, ctypes.POINTER(u32), ctypes.POINTER(u32)]
     for f in ("map_create", "map_run", "map_destroy", "map_graph_info", "map_run_static", "map_batch_create",
-              "map_batch_run", "map_server_create", "map_submit", "map_poll", "map_server_destroy", "map_autotune"):
+              "map_batch_run", "map_server_create", "map_submit", "map_poll", "map_server_destroy", "map_autotune",
+              "map_lasso"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -396,6 +409,9 @@ class Graph:
 
     def run(self, **kw) -> RunResult:
         return map_run(self.handle, **kw)
+
+    def lasso(self, witness: int, init: int = MAP_NONE, cap: int = 1 << 20):
+        return map_lasso(self.handle, witness, init, cap)
 
     def close(self):
         map_destroy(self.handle)

@@ -796,6 +796,74 @@ int map_autotune(map_graph *g, uint32_t sched, map_tune_result *out)
     return MAP_OK;
 }
 
+// shortest path source -> target along rows (at least one edge) into host path[0..cap); *len = vertices
+static int bfs_path(map_graph *g, uint32_t source, uint32_t target, uint32_t *path, uint32_t cap, uint32_t *len)
+{
+    cudaStream_t s = g->stream;
+    const uint32_t n = g->n;
+    uint32_t *parent = g->xbuf, *q0 = g->list, *q1 = g->list + n; // list holds 3n entries
+    uint32_t *cnt = &g->ctl->lcnt[0].v, *cnt2 = &g->ctl->lcnt[1].v, *found = &g->ctl->lcnt[2].v;
+    mapk::k_fill<<<grid_for(g, n, 1), 256, 0, s>>>(parent, n, mapk::NONE);
+    CK(cudaGetLastError());
+    if (source != target) { // the source is reached from the start
+        CK(cudaMemcpyAsync(parent + source, &source, 4, cudaMemcpyHostToDevice, s));
+    }
+    uint32_t one = 1, zero = 0;
+    CK(cudaMemcpyAsync(q0, &source, 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(cnt, &one, 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(found, &zero, 4, cudaMemcpyHostToDevice, s));
+    uint32_t h[2] = {1, 0};
+    for (uint32_t level = 0; level <= n && h[0]; ++level) {
+        CK(cudaMemcpyAsync(cnt2, &zero, 4, cudaMemcpyHostToDevice, s));
+        mapk::k_bfs_level<<<grid_for(g, h[0], 1), 256, 0, s>>>(q0, cnt, g->rowptr, g->colidx, parent, q1, cnt2,
+                                                                 target, found);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(&h[0], cnt2, 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&h[1], found, 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (h[1]) break;
+        std::swap(q0, q1);
+        std::swap(cnt, cnt2);
+    }
+    if (!h[1]) return fail(MAP_ERR_ARG, "map_lasso: vertex %u is not reachable from %u", target, source);
+    // a parent chain visits distinct vertices (target twice when it is the source): <= n + 1 entries
+    uint32_t k = 0, *out = g->list;
+    const uint32_t dcap = cap < n + 1 ? cap : n + 1;
+    mapk::k_walk_back<<<1, 32, 0, s>>>(parent, source, target, out, dcap, n + 1, found);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&k, found, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (k == 0xFFFFFFFFu || k > cap) return fail(MAP_ERR_LIMIT, "map_lasso: the path does not fit into %u entries", cap);
+    std::vector<uint32_t> rev(k);
+    CK(cudaMemcpyAsync(rev.data(), out, (size_t)k * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (uint32_t i = 0; i < k; ++i) path[i] = rev[k - 1 - i];
+    *len = k;
+    return MAP_OK;
+}
+
+int map_lasso(map_graph *g, uint32_t init, uint32_t witness, uint32_t *path, uint32_t cap, uint32_t *prefix_len,
+              uint32_t *cycle_len)
+{
+    g_err.clear();
+    if (!g || !path || !prefix_len || !cycle_len) return fail(MAP_ERR_ARG, "map_lasso: NULL argument");
+    if (g->comp) return fail(MAP_ERR_ARG, "map_lasso: single graphs only");
+    if (witness >= g->n || (init != MAP_NONE && init >= g->n)) return fail(MAP_ERR_ARG, "map_lasso: vertex out of range");
+    *prefix_len = *cycle_len = 0;
+    uint32_t used = 0;
+    int rc = MAP_OK;
+    if (init != MAP_NONE && init != witness) { // init -> ... -> witness
+        uint32_t k = 0;
+        if ((rc = bfs_path(g, init, witness, path, cap, &k))) return rc;
+        used = k - 1; // the witness opens the cycle part
+        *prefix_len = used;
+    }
+    uint32_t k = 0; // witness -> ... -> witness
+    if ((rc = bfs_path(g, witness, witness, path + used, cap - used, &k))) return rc;
+    *cycle_len = k;
+    return MAP_OK;
+}
+
 int map_batch_create(uint32_t count, const uint32_t *ns, const uint32_t *const *rowptrs,
                      const uint32_t *const *colidxs, const uint32_t *const *acc_bits, void *cuda_stream,
                      map_graph **out)

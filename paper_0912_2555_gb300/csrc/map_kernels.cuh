@@ -1070,6 +1070,60 @@ __global__ void __launch_bounds__(256) k_restore(const Dev d)
     if (last_block(ctl)) ctl->ecnt.v = 0;
 }
 
+// ---------------------------------------------------------- counterexample --
+//
+// A lasso for a cycle verdict (the paper lists counterexample generation as
+// missing): breadth-first search along rows (successors in G) with parent
+// pointers, one level per launch.  parent[v] = NONE while v is unreached.
+
+__global__ void k_fill(uint32_t *x, uint64_t len, uint32_t value)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) x[i] = value;
+}
+
+// one level: every row u of the frontier offers its successors; the first
+// offer to reach an unreached vertex v sets parent[v] = u and queues v
+__global__ void k_bfs_level(const uint32_t *__restrict__ front, const uint32_t *cnt_in, const uint32_t *__restrict__ rowptr,
+                            const uint32_t *__restrict__ colidx, uint32_t *parent, uint32_t *next, uint32_t *cnt_out,
+                            uint32_t target, uint32_t *found)
+{
+    const uint32_t nf = *(volatile const uint32_t *)cnt_in;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += stride) {
+        const uint32_t u = __ldg(front + i);
+        const uint32_t b = __ldg(rowptr + u), e = __ldg(rowptr + u + 1);
+        for (uint32_t j = b; j < e; ++j) {
+            const uint32_t v = __ldg(colidx + j) & 0x7FFFFFFFu; // bit 31 is the accepting flag
+            if (*(volatile uint32_t *)(parent + v) != NONE) continue;
+            if (atomicCAS(parent + v, NONE, u) == NONE) {
+                next[atomicAdd(cnt_out, 1u)] = v;
+                if (v == target) *found = 1;
+            }
+        }
+    }
+}
+
+// the path source -> ... -> target, walked back from target along parents (one
+// thread); out[0..len) holds it reversed; at most cap vertices, at most limit steps
+__global__ void k_walk_back(const uint32_t *__restrict__ parent, uint32_t source, uint32_t target, uint32_t *out,
+                            uint32_t cap, uint32_t limit, uint32_t *len)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    uint32_t k = 0, v = target;
+    out[k++] = v;
+    for (uint32_t steps = 0; steps < limit; ++steps) {
+        v = parent[v];
+        if (v == NONE || k >= cap) {
+            k = 0xFFFFFFFFu; // broken chain or no room
+            break;
+        }
+        out[k++] = v;
+        if (v == source) break;
+    }
+    *len = k;
+}
+
 // ---------------------------------------------------------------- set-up --
 
 // CSR validation: rowptr non-decreasing, every colidx < n.

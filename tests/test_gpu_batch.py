@@ -127,3 +127,29 @@ def test_autotune_keeps_results(pkg):
                                                                  want.relaxations)
     finally:
         pkg.map_destroy(h)
+
+
+def test_full_256_graph_batch_sampled_against_oracle(pkg):
+    """The batch the benchmark times (256 layered graphs, n log-uniform in [1e3, 2e6], 40 % planted
+    cycles, seed 4), run as one batch; a sample of graphs across the size range is checked one by
+    one against the oracle, and every graph's verdict against its planted cycle."""
+    sizes, planted, seeds = mapgen.batch_plan(count=256, lo=1000, hi=2_000_000, frac_cycle=0.4, seed=4)
+    gs = [mapgen.batch_graph(int(s), bool(p), int(sd)) for s, p, sd in zip(sizes, planted, seeds)]
+    h = pkg.map_batch_create([(g.n, g.rowptr, g.colidx, pkg.pack_bits(g.acc)) for g in gs])
+    try:
+        total = sum(g.n for g in gs)
+        out = torch.empty(total, dtype=torch.int32, device="cuda")
+        res = pkg.map_batch_run(h, len(gs), map_out=out)
+        out = out.cpu().numpy().view(np.uint32)
+    finally:
+        pkg.map_destroy(h)
+    assert [r.verdict for r in res] == [int(p) for p in planted]
+    offs = np.concatenate([[0], np.cumsum([g.n for g in gs])])
+    order = np.argsort(sizes)
+    sample = sorted(set(int(order[i]) for i in np.linspace(0, len(gs) - 1, 10).astype(int)))
+    for i in sample:
+        want = oracle.run_graph(gs[i])
+        r = res[i]
+        assert (r.verdict, r.witness, r.outer, r.rounds, r.relaxations) == (
+            want.verdict, want.witness, want.outer, want.rounds, want.relaxations), i
+        assert np.array_equal(out[offs[i]:offs[i + 1]], want.map), i
