@@ -41,10 +41,22 @@ def check_lasso(g, prefix, cycle, witness, init):
         assert all(is_edge(g, a, b) for a, b in zip(path, path[1:]))
 
 
-def lasso_case(pkg, g, init=0, lengths=True):
+def ancestor(g, v, steps):
+    """A vertex that reaches v: walk back along edges (the first edge into the current vertex)."""
+    for _ in range(steps):
+        j = np.flatnonzero(g.colidx == v)
+        if j.size == 0:
+            break
+        v = int(np.searchsorted(g.rowptr, j[0], side="right")) - 1
+    return v
+
+
+def lasso_case(pkg, g, init=0, lengths=True, back=None):
     with pkg.Graph(g.n, g.rowptr, g.colidx, g.acc) as h:
         r = h.run()
         assert r.verdict == 1 and g.acc[r.witness]
+        if back is not None:  # the initial vertex: `back` steps up the witness's ancestry
+            init = ancestor(g, r.witness, back)
         prefix, cycle = h.lasso(r.witness, init=pkg.MAP_NONE if init is None else init)
         check_lasso(g, prefix, cycle, r.witness, init)
         if lengths:
@@ -88,15 +100,26 @@ def test_workloads(pkg, name):
     g = {"random_16k": lambda: mapgen.random_16k("cycle"),
          "product_8x7": mapgen.product_8x7,
          "layered_4m": lambda: mapgen.layered_graph(1 << 22, 250, seed=3, plant=True)}[name]()
-    lasso_case(pkg, g, init=0)
+    lasso_case(pkg, g, back=25)
     lasso_case(pkg, g, init=None)
+
+
+def test_unreachable_initial_vertex(pkg):
+    """product 8x7 is deterministic (out-degree 1): vertex 0 does not reach the witness."""
+    g = mapgen.product_8x7()
+    with pkg.Graph(g.n, g.rowptr, g.colidx, g.acc) as h:
+        r = h.run()
+        assert oracle.bfs_dist(g.n, g.rowptr, g.colidx, 0)[r.witness] < 0
+        with pytest.raises(pkg.MapError) as e:
+            h.lasso(r.witness, init=0)
+        assert e.value.code == pkg.MAP_ERR_ARG
 
 
 def test_layered_64m_planted_lasso_is_valid(pkg):
     """Full size: 2^26 vertices, 4,000 layers, one planted back edge; the lasso is checked for
     validity (the oracle's BFS at this size is left to the 4M-vertex case)."""
     g = mapgen.layered_graph(1 << 26, 4000, seed=3, plant=True)
-    lasso_case(pkg, g, init=0, lengths=False)
+    lasso_case(pkg, g, lengths=False, back=10)
 
 
 def test_errors(pkg):
