@@ -253,6 +253,37 @@ MAP_API int map_autotune(map_graph *g, uint32_t sched, map_tune_result *out);
 MAP_API int map_lasso(map_graph *g, uint32_t init, uint32_t witness, uint32_t *path, uint32_t cap,
                       uint32_t *prefix_len, uint32_t *cycle_len);
 
+/*
+ * map_create_reduced -- like map_create, over the part of the graph that can
+ * hold an accepting cycle (Section 2 of the paper: the matrix lists only the
+ * states of components that contain accepting states).
+ *   part   NULL, or n component labels (host or device), e.g. the strongly
+ *          connected component of the property automaton each product state
+ *          projects to; only edges whose ends share a label are kept.  The
+ *          caller guarantees that every cycle of the graph lies within one
+ *          label (true for automaton components); NULL = one label.
+ * Kept: every vertex reachable from an accepting vertex and reaching one (by
+ * zero or more kept edges) -- every accepting cycle lies on such vertices, so
+ * the verdict is that of the whole graph.  The handle holds the subgraph they
+ * induce, renumbered in increasing order (the order on accepting vertices is
+ * kept); map_run results (witness, map vector) use the new numbering, and
+ * map_graph_vertex_ids gives the original id of each vertex.  With no
+ * accepting vertex the handle holds one isolated non-accepting vertex whose
+ * original id is MAP_NONE.  The reduction runs on the device; the full graph
+ * lives on the device only while the call runs.
+ */
+MAP_API int map_create_reduced(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const uint32_t *acc_bits,
+                               const uint32_t *part, void *cuda_stream, map_graph **out);
+
+/* map_graph_vertex_ids -- the original id of each of the graph's n vertices
+ * into ids (host or device): the identity except for reduced graphs. */
+MAP_API int map_graph_vertex_ids(const map_graph *g, uint32_t *ids);
+
+/* map_graph_csr -- the graph as the handle holds it: rowptr (n + 1 entries),
+ * colidx (m), acc_bits (ceil(n / 32) words, the accepting set at the start of
+ * every run); each may be NULL, host or device.  Not while a run is in flight. */
+MAP_API int map_graph_csr(const map_graph *g, uint32_t *rowptr, uint32_t *colidx, uint32_t *acc_bits);
+
 /* map_graph_info -- n and m of a graph (either pointer may be NULL). */
 MAP_API int map_graph_info(const map_graph *g, uint32_t *n, uint64_t *m);
 

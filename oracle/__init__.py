@@ -126,14 +126,15 @@ def run_graph(g, **kw) -> OracleResult:
 # the oracle fixes what is: the lengths.  Plain breadth-first search.
 # ---------------------------------------------------------------------------
 
-def bfs_dist(n, rowptr, colidx, source):
-    """Edge count of a shortest path source -> v along rows (successors) for every v (an int64
-    array); -1 if none.  Level by level: the unseen successors of level d form level d + 1."""
+def _levels(n, rowptr, colidx, sources):
+    """Edge count of a shortest path from the nearest source to every v along rows (-1 if none).
+    Level by level: the unseen successors of level d form level d + 1."""
     rowptr = np.asarray(rowptr, np.int64)
     colidx = np.asarray(colidx, np.int64)
     dist = np.full(n, -1, np.int64)
-    dist[source] = 0
-    level, front = 0, np.array([source], np.int64)
+    front = np.unique(np.asarray(sources, np.int64))
+    dist[front] = 0
+    level = 0
     while front.size:
         level += 1
         b, e = rowptr[front], rowptr[front + 1]
@@ -144,6 +145,12 @@ def bfs_dist(n, rowptr, colidx, source):
         dist[new] = level
         front = new
     return dist
+
+
+def bfs_dist(n, rowptr, colidx, source):
+    """Edge count of a shortest path source -> v along rows (successors) for every v (an int64
+    array); -1 if none."""
+    return _levels(n, rowptr, colidx, [source])
 
 
 def lasso_lengths(n, rowptr, colidx, witness, init=None):
@@ -164,3 +171,38 @@ def lasso_lengths(n, rowptr, colidx, witness, init=None):
         pre = int(bfs_dist(n, rowptr, colidx, init)[witness])
         pre = None if pre < 0 else pre
     return pre, cyc
+
+
+# ---------------------------------------------------------------------------
+# Accepting-part reduction.  Section 2 of the paper: the matrix lists only the
+# states of components that contain accepting states (components of the
+# property automaton, after Lafuente).  Stated on the graph: with optional
+# component labels part[v] (edges between different labels dropped), keep the
+# vertices reachable from an accepting vertex and reaching an accepting vertex
+# (paths of zero or more edges); the result is the subgraph they induce, its
+# vertices renumbered in increasing order of their original ids.
+# ---------------------------------------------------------------------------
+
+def _csr_from_edges(n, src, dst):
+    """CSR with rows by src; a row keeps the edges in their given order (stable sort)."""
+    order = np.argsort(src, kind="stable")
+    rowptr = np.concatenate([[0], np.cumsum(np.bincount(src, minlength=n))]).astype(np.int64)
+    return rowptr, dst[order]
+
+
+def reduce_graph(n, rowptr, colidx, acc, part=None):
+    """(ids, rowptr', colidx', acc') of the reduced graph: ids[i] = original id of vertex i."""
+    rowptr = np.asarray(rowptr, np.int64)
+    colidx = np.asarray(colidx, np.int64)
+    acc = np.asarray(acc).astype(bool)
+    src = np.repeat(np.arange(n, dtype=np.int64), np.diff(rowptr))  # the row of every edge
+    ok = np.ones(len(colidx), bool) if part is None else (np.asarray(part)[src] == np.asarray(part)[colidx])
+    seeds = np.flatnonzero(acc)
+    fwd = _levels(n, *_csr_from_edges(n, src[ok], colidx[ok]), seeds) >= 0  # reached from A
+    bwd = _levels(n, *_csr_from_edges(n, colidx[ok], src[ok]), seeds) >= 0  # reaching A
+    keep = fwd & bwd
+    ids = np.flatnonzero(keep)
+    new = np.cumsum(keep) - 1  # new id of each kept vertex
+    e = ok & keep[src] & keep[colidx]  # edges of the induced subgraph, in CSR order
+    rowptr2 = np.concatenate([[0], np.cumsum(np.bincount(new[src[e]], minlength=len(ids)))]).astype(np.uint32)
+    return ids.astype(np.uint32), rowptr2, new[colidx[e]].astype(np.uint32), acc[ids].astype(np.uint8)

@@ -33,7 +33,7 @@ STATUS_NAMES = ["MAP_OK", "MAP_ERR_ARG", "MAP_ERR_CSR", "MAP_ERR_OOM", "MAP_ERR_
 # exported symbols of include/map.h (checked by the tests)
 EXPORTS = ["map_create", "map_run", "map_destroy", "map_graph_info", "map_last_error", "map_run_static",
            "map_batch_create", "map_batch_run", "map_server_create", "map_submit", "map_poll", "map_server_destroy",
-           "map_autotune", "map_lasso"]
+           "map_autotune", "map_lasso", "map_create_reduced", "map_graph_vertex_ids", "map_graph_csr"]
 MAP_STATIC_MAX_N = 65536
 MAP_STATIC_MAX_M = 524288
 
@@ -144,9 +144,12 @@ def load(path: str = LIB_PATH):
     lib.map_server_destroy.argtypes = [vp]
     lib.map_autotune.argtypes = [vp, u32, ctypes.POINTER(TuneResult)]
     lib.map_lasso.argtypes = [vp, u32, u32, vp, u32, ctypes.POINTER(u32), ctypes.POINTER(u32)]
+    lib.map_create_reduced.argtypes = [u32, vp, vp, vp, vp, vp, ctypes.POINTER(vp)]
+    lib.map_graph_vertex_ids.argtypes = [vp, vp]
+    lib.map_graph_csr.argtypes = [vp, vp, vp, vp]
     for f in ("map_create", "map_run", "map_destroy", "map_graph_info", "map_run_static", "map_batch_create",
               "map_batch_run", "map_server_create", "map_submit", "map_poll", "map_server_destroy", "map_autotune",
-              "map_lasso"):
+              "map_lasso", "map_create_reduced", "map_graph_vertex_ids", "map_graph_csr"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -185,6 +188,52 @@ def map_create(n: int, rowptr, colidx, acc_bits, stream=None):
     if rc != MAP_OK:
         raise MapError(rc, "map_create", last_error())
     return h
+
+
+def map_create_reduced(n: int, rowptr, colidx, acc_bits, part=None, stream=None):
+    """Create the graph restricted to the vertices that can lie on an accepting cycle (see
+    include/map.h); results use the reduced numbering, map_graph_vertex_ids maps it back."""
+    lib = load()
+    rp, k1 = _ptr(rowptr)
+    ci, k2 = _ptr(colidx)
+    ab, k3 = _ptr(acc_bits)
+    pt, k4 = _ptr(part)
+    h = ctypes.c_void_p()
+    rc = lib.map_create_reduced(n, rp, ci, ab, pt, _stream_handle(stream), ctypes.byref(h))
+    if rc != MAP_OK:
+        raise MapError(rc, "map_create_reduced", last_error())
+    return h
+
+
+def map_graph_info(handle):
+    """(n, m) of a handle."""
+    n, m = ctypes.c_uint32(), ctypes.c_uint64()
+    rc = load().map_graph_info(handle, ctypes.byref(n), ctypes.byref(m))
+    if rc != MAP_OK:
+        raise MapError(rc, "map_graph_info", last_error())
+    return n.value, m.value
+
+
+def map_graph_vertex_ids(handle) -> np.ndarray:
+    """Original id of each vertex of the handle (identity unless it was reduced)."""
+    n, _ = map_graph_info(handle)
+    ids = np.empty(n, np.uint32)
+    rc = load().map_graph_vertex_ids(handle, ids.ctypes.data)
+    if rc != MAP_OK:
+        raise MapError(rc, "map_graph_vertex_ids", last_error())
+    return ids
+
+
+def map_graph_csr(handle):
+    """(rowptr, colidx, acc_bits) as the handle holds them, as host arrays."""
+    n, m = map_graph_info(handle)
+    rp = np.empty(n + 1, np.uint32)
+    ci = np.empty(max(m, 1), np.uint32)
+    ab = np.empty((n + 31) // 32, np.uint32)
+    rc = load().map_graph_csr(handle, rp.ctypes.data, ci.ctypes.data, ab.ctypes.data)
+    if rc != MAP_OK:
+        raise MapError(rc, "map_graph_csr", last_error())
+    return rp, ci[:m], ab
 
 
 def map_destroy(handle) -> None:

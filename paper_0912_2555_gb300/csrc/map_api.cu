@@ -95,6 +95,7 @@ struct map_graph {
     uint32_t *flist = nullptr; // 3n: frontier rows of a round, by round mod 3
     uint4 *rec = nullptr;      // n: per-vertex round state (snapshots, list and frontier flags)
     uint32_t *touched = nullptr, *xbuf = nullptr;
+    uint32_t *ids = nullptr; // reduced graphs: the original id of each vertex (else NULL: identity)
     bool dirty = false; // a run stopped early: per-round state may be stale
     uint32_t *hist = nullptr; // rounds per outer iteration
     uint32_t hist_cap = 0;
@@ -131,6 +132,7 @@ void free_graph(map_graph *g)
     for (void *p : dev)
         if (p) cudaFreeAsync(p, g->stream); // stream-ordered: no device-wide synchronisation
     if (g->comp) cudaFreeAsync(g->comp, g->stream);
+    if (g->ids) cudaFreeAsync(g->ids, g->stream);
     if (g->cs) cudaFreeAsync(g->cs, g->stream);
     if (g->chist) cudaFreeAsync(g->chist, g->stream);
     free(g->h_cs);
@@ -151,6 +153,14 @@ int grid_for(const map_graph *g, uint64_t items, int G)
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     return (int)blocks;
+}
+
+// stream-ordered allocation of `words` u32 plus 16 bytes of slack
+int ck_alloc(uint32_t **p, uint64_t words, cudaStream_t s)
+{
+    *p = nullptr;
+    CK(cudaMallocAsync((void **)p, (words + 4) * sizeof(uint32_t), s));
+    return MAP_OK;
 }
 
 // inclusive scan of x[0..len) in place (multi-level tiles of 1024)
@@ -861,6 +871,168 @@ int map_lasso(map_graph *g, uint32_t init, uint32_t witness, uint32_t *path, uin
     uint32_t k = 0; // witness -> ... -> witness
     if ((rc = bfs_path(g, witness, witness, path + used, cap - used, &k))) return rc;
     *cycle_len = k;
+    return MAP_OK;
+}
+
+// ---------------------------------------------------- reduction and export --
+
+namespace {
+
+int launch_reach(map_graph *g, const uint32_t *ptr, const uint32_t *col, const uint32_t *part, uint32_t *mark,
+                 uint32_t bit, uint32_t *q)
+{
+    cudaStream_t s = g->stream;
+    Ctl *c = g->ctl;
+    // queue counters, barrier and status of this sweep
+    for (mapk::Cnt32 *x : {&c->lcnt[0], &c->lcnt[1], &c->lcnt[2], &c->bar_count, &c->bar_gen})
+        CK(cudaMemsetAsync(&x->v, 0, 4, s));
+    CK(cudaMemsetAsync(&c->status, 0, 4, s));
+    mapk::k_reach_seed<<<grid_for(g, g->n, 1), 256, 0, s>>>(g->n, g->acc0, mark, bit, q, &c->lcnt[0].v);
+    CK(cudaGetLastError());
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mapk::k_reach, 256, 0));
+    if (occ < 1) occ = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)std::min<uint64_t>(((uint64_t)g->n + 255) / 256, (uint64_t)g->sms * occ));
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, mapk::k_reach, g->n, ptr, col, part, mark, bit, q, c));
+    return MAP_OK;
+}
+
+// the reduced graph of g (see map_create_reduced); part: device labels or NULL
+int reduce_graph(map_graph *g, const uint32_t *part, map_graph **out)
+{
+    cudaStream_t s = g->stream;
+    const uint32_t n = g->n;
+    uint32_t *mark = g->xbuf, *rank = g->touched, *q = g->list; // list: 3n entries
+    CK(cudaMemsetAsync(mark, 0, (size_t)n * 4, s));
+    int rc;
+    if ((rc = launch_reach(g, g->rowptr, g->colidx, part, mark, 1u, q)) ||   // reached from an accepting vertex
+        (rc = launch_reach(g, g->rrowptr, g->rcol, part, mark, 2u, q)))      // reaching one
+        return rc;
+    if ((rc = read_ctl(g))) return rc;
+    if (g->h_ctl->status) return fail(MAP_ERR_TIMEOUT, "map_create_reduced: a reachability sweep gave up waiting");
+    mapk::k_keep<<<grid_for(g, n, 1), 256, 0, s>>>(n, mark, rank);
+    CK(cudaGetLastError());
+    if ((rc = scan_inclusive(rank, n, s))) return rc;
+    uint32_t n2 = 0;
+    CK(cudaMemcpyAsync(&n2, rank + n - 1, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (n2 == 0) { // no accepting vertex: one isolated, non-accepting vertex that stands for nothing
+        const uint32_t rp0[2] = {0, 0}, acc0 = 0;
+        if ((rc = map_create(1, rp0, nullptr, &acc0, s, out))) return rc;
+        if ((rc = ck_alloc(&(*out)->ids, 1, s)) == MAP_OK) {
+            mapk::k_fill<<<1, 32, 0, s>>>((*out)->ids, 1, MAP_NONE);
+            if (cudaGetLastError() != cudaSuccess) rc = fail(MAP_ERR_CUDA, "map_create_reduced: fill");
+        }
+        if (rc) {
+            free_graph(*out);
+            *out = nullptr;
+        }
+        return rc;
+    }
+    const uint32_t W2 = (n2 + 31) / 32;
+    uint32_t *rp = nullptr, *col2 = nullptr, *ids = nullptr, *acc2 = nullptr;
+    auto done = [&](int r) {
+        for (uint32_t *p : {rp, col2, acc2}) if (p) cudaFreeAsync(p, s);
+        if (r != MAP_OK && ids) cudaFreeAsync(ids, s);
+        return r;
+    };
+    if ((rc = ck_alloc(&rp, (uint64_t)n2 + 1, s)) || (rc = ck_alloc(&ids, n2, s)) || (rc = ck_alloc(&acc2, W2, s)))
+        return done(rc);
+    if (cudaMemsetAsync(rp, 0, 4, s) || cudaMemsetAsync(acc2, 0, (size_t)W2 * 4, s))
+        return done(fail(MAP_ERR_CUDA, "map_create_reduced: memset"));
+    mapk::k_reduce_rows<0><<<grid_for(g, n, 1), 256, 0, s>>>(n, g->rowptr, g->colidx, part, mark, rank, g->acc0, rp,
+                                                             nullptr, nullptr, nullptr);
+    if (cudaGetLastError()) return done(fail(MAP_ERR_CUDA, "map_create_reduced: row lengths"));
+    if ((rc = scan_inclusive(rp + 1, n2, s))) return done(rc);
+    uint32_t m2 = 0;
+    if (cudaMemcpyAsync(&m2, rp + n2, 4, cudaMemcpyDeviceToHost, s) || cudaStreamSynchronize(s))
+        return done(fail(MAP_ERR_CUDA, "map_create_reduced: edge count"));
+    if ((rc = ck_alloc(&col2, m2, s))) return done(rc);
+    mapk::k_reduce_rows<1><<<grid_for(g, n, 1), 256, 0, s>>>(n, g->rowptr, g->colidx, part, mark, rank, g->acc0, rp,
+                                                             col2, ids, acc2);
+    if (cudaGetLastError()) return done(fail(MAP_ERR_CUDA, "map_create_reduced: rows"));
+    if ((rc = map_create(n2, rp, col2, acc2, s, out))) return done(rc);
+    (*out)->ids = ids;
+    return done(MAP_OK);
+}
+
+} // namespace
+
+int map_create_reduced(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const uint32_t *acc_bits,
+                       const uint32_t *part, void *cuda_stream, map_graph **out)
+{
+    g_err.clear();
+    if (!out) return fail(MAP_ERR_ARG, "map_create_reduced: out is NULL");
+    *out = nullptr;
+    map_graph *full = nullptr;
+    int rc = map_create(n, rowptr, colidx, acc_bits, cuda_stream, &full);
+    if (rc) return rc;
+    cudaStream_t s = full->stream;
+    uint32_t *part_dev = nullptr;
+    if (part && !is_device_ptr(part)) { // labels to the device
+        if ((rc = ck_alloc(&part_dev, n, s)) == MAP_OK &&
+            cudaMemcpyAsync(part_dev, part, (size_t)n * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            rc = fail(MAP_ERR_CUDA, "map_create_reduced: copy of part");
+        if (rc) {
+            if (part_dev) cudaFreeAsync(part_dev, s);
+            free_graph(full);
+            return rc;
+        }
+    }
+    rc = reduce_graph(full, part_dev ? part_dev : part, out);
+    if (part_dev) cudaFreeAsync(part_dev, s);
+    free_graph(full);
+    if (rc == MAP_OK && cudaStreamSynchronize(s) != cudaSuccess) {
+        free_graph(*out);
+        *out = nullptr;
+        return fail(MAP_ERR_CUDA, "map_create_reduced: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    return rc;
+}
+
+int map_graph_vertex_ids(const map_graph *g, uint32_t *ids)
+{
+    g_err.clear();
+    if (!g || !ids) return fail(MAP_ERR_ARG, "map_graph_vertex_ids: NULL argument");
+    cudaStream_t s = g->stream;
+    if (g->ids) {
+        CK(cudaMemcpyAsync(ids, g->ids, (size_t)g->n * 4, cudaMemcpyDefault, s));
+    } else if (is_device_ptr(ids)) {
+        mapk::k_iota<<<grid_for(g, g->n, 1), 256, 0, s>>>(g->n, ids);
+        CK(cudaGetLastError());
+    } else {
+        for (uint32_t v = 0; v < g->n; ++v) ids[v] = v;
+    }
+    CK(cudaStreamSynchronize(s));
+    return MAP_OK;
+}
+
+int map_graph_csr(const map_graph *g, uint32_t *rowptr, uint32_t *colidx, uint32_t *acc_bits)
+{
+    g_err.clear();
+    if (!g) return fail(MAP_ERR_ARG, "map_graph_csr: NULL graph");
+    cudaStream_t s = g->stream;
+    if (rowptr) CK(cudaMemcpyAsync(rowptr, g->rowptr, ((size_t)g->n + 1) * 4, cudaMemcpyDefault, s));
+    if (acc_bits) CK(cudaMemcpyAsync(acc_bits, g->acc0, (size_t)g->words * 4, cudaMemcpyDefault, s));
+    if (colidx && g->m) {
+        uint32_t *tmp = nullptr;
+        int rc = ck_alloc(&tmp, g->m, s);
+        if (rc) return rc;
+        mapk::k_unflag<<<grid_for(g, g->m, 1), 256, 0, s>>>(g->m, g->colidx, tmp);
+        const cudaError_t e1 = cudaGetLastError();
+        const cudaError_t e2 = e1 ? e1 : cudaMemcpyAsync(colidx, tmp, g->m * 4, cudaMemcpyDefault, s);
+        cudaFreeAsync(tmp, s);
+        CK(e2);
+    }
+    CK(cudaStreamSynchronize(s));
     return MAP_OK;
 }
 

@@ -1124,6 +1124,139 @@ __global__ void k_walk_back(const uint32_t *__restrict__ parent, uint32_t source
     *len = k;
 }
 
+// ------------------------------------------------ accepting-part reduction --
+//
+// The paper builds its matrix only over the states in components that hold
+// accepting states (the property automaton's components, after Lafuente).
+// Every accepting cycle lies on a path from an accepting vertex to an
+// accepting vertex, inside one component when the caller labels vertices by
+// component (part[v]).  Kept = vertices reachable from an accepting vertex
+// and reaching one (by >= 0 edges whose ends share a label); the reduced
+// graph is the subgraph they induce, renumbered in increasing order.
+
+// seeds: every accepting vertex gets `bit` in mark[] and is queued
+__global__ void k_reach_seed(uint32_t n, const uint32_t *__restrict__ acc0, uint32_t *mark, uint32_t bit, uint32_t *q,
+                             unsigned int *cnt)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < n; base += stride) { // warp-uniform
+        const uint64_t v = base + threadIdx.x;
+        const bool a = v < n && ((__ldg(acc0 + (v >> 5)) >> (v & 31u)) & 1u);
+        if (a) mark[v] |= bit;
+        const unsigned mask = __ballot_sync(0xFFFFFFFFu, a);
+        if (!mask) continue;
+        unsigned b = 0;
+        if (lane_id() == 0) b = atomicAdd(cnt, __popc(mask));
+        b = __shfl_sync(0xFFFFFFFFu, b, 0);
+        if (a) q[b + __popc(mask & ((1u << lane_id()) - 1u))] = (uint32_t)v;
+    }
+}
+
+// level-synchronous reachability from the queued seeds, all levels in one
+// cooperative launch: lists by level mod 3 (q + (l % 3) * n), counters
+// ctl->lcnt[l % 3].  Along rows of (ptr, col) -- successors for the forward
+// sweep, readers for the backward one -- masking bit 31 of col.
+__global__ void __launch_bounds__(256) k_reach(uint32_t n, const uint32_t *__restrict__ ptr,
+                                               const uint32_t *__restrict__ col, const uint32_t *__restrict__ part,
+                                               uint32_t *mark, uint32_t bit, uint32_t *q, Ctl *ctl)
+{
+    __shared__ uint32_t s_buf[8][SB_ENTRIES];
+    __shared__ uint32_t s_cnt[8][1];
+    __shared__ uint32_t s_base[1];
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint32_t status = ST_OK;
+    for (uint32_t l = 0; l <= n; ++l) {
+        const uint32_t nf = *(volatile uint32_t *)&ctl->lcnt[l % 3].v;
+        if (nf == 0) break;
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctl->lcnt[(l + 2) % 3].v = 0; // read in level l - 1
+        const uint32_t *qin = q + (uint64_t)(l % 3) * n;
+        uint32_t *qout = q + (uint64_t)((l + 1) % 3) * n;
+        uint32_t *const dst[1][2] = {{qout, nullptr}};
+        unsigned int *const ctr[1] = {&ctl->lcnt[(l + 1) % 3].v};
+        Stage<1> st{&s_buf[warp][0], {0}};
+        for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + warp * 32; base < nf; base += stride) {
+            const uint64_t i = base + lane;
+            uint32_t u = 0, b = 0, e = 0;
+            if (i < nf) {
+                u = qin[i];
+                b = __ldg(ptr + u);
+                e = __ldg(ptr + u + 1);
+            }
+            const uint32_t pu = (part && i < nf) ? __ldg(part + u) : 0;
+            const uint32_t len = e - b, most = __reduce_max_sync(0xFFFFFFFFu, len);
+            for (uint32_t k = 0; k < most; ++k) {
+                bool fresh = false;
+                uint32_t v = 0;
+                if (k < len) {
+                    v = __ldg(col + b + k) & 0x7FFFFFFFu;
+                    if ((!part || __ldg(part + v) == pu) && !(*(volatile uint32_t *)(mark + v) & bit))
+                        fresh = !(atomicOr(mark + v, bit) & bit);
+                }
+                stage_append<1>(st, 0, fresh, v, dst, ctr);
+            }
+        }
+        stage_flush_block<1>(st, s_cnt, s_base, dst, ctr);
+        if (!grid_barrier(ctl)) {
+            status = ST_TIMEOUT;
+            break;
+        }
+    }
+    if (status != ST_OK && blockIdx.x == 0 && threadIdx.x == 0) ctl->status = status;
+}
+
+// keep[v] = both marks (3), as 0/1 words for the scan
+__global__ void k_keep(uint32_t n, const uint32_t *__restrict__ mark, uint32_t *keep)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        keep[v] = (mark[v] & 3u) == 3u ? 1u : 0u;
+}
+
+// rank = inclusive scan of keep: kept v becomes rank[v] - 1.  pass 0: the row
+// lengths of the reduced graph into rp[1 + new id]; pass 1: the rows into col_out
+// (in the original order), the original ids and the accepting bits.
+template <int PASS>
+__global__ void k_reduce_rows(uint32_t n, const uint32_t *__restrict__ rowptr, const uint32_t *__restrict__ col,
+                              const uint32_t *__restrict__ part, const uint32_t *__restrict__ mark,
+                              const uint32_t *__restrict__ rank, const uint32_t *__restrict__ acc0, uint32_t *rp,
+                              uint32_t *col_out, uint32_t *ids, uint32_t *acc_out)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
+        if ((mark[u] & 3u) != 3u) continue;
+        const uint32_t nu = rank[u] - 1, pu = part ? __ldg(part + u) : 0;
+        const uint32_t b = __ldg(rowptr + u), e = __ldg(rowptr + u + 1);
+        uint32_t k = PASS ? rp[nu] : 0;
+        for (uint32_t j = b; j < e; ++j) {
+            const uint32_t v = __ldg(col + j) & 0x7FFFFFFFu;
+            if ((mark[v] & 3u) != 3u || (part && __ldg(part + v) != pu)) continue;
+            if (PASS) col_out[k] = rank[v] - 1;
+            ++k;
+        }
+        if (!PASS) {
+            rp[1 + (uint64_t)nu] = k;
+        } else {
+            ids[nu] = (uint32_t)u;
+            if ((__ldg(acc0 + (u >> 5)) >> (u & 31u)) & 1u) atomicOr(acc_out + (nu >> 5), 1u << (nu & 31u));
+        }
+    }
+}
+
+__global__ void k_iota(uint32_t n, uint32_t *x)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) x[v] = (uint32_t)v;
+}
+
+// colidx without the accepting flags (export)
+__global__ void k_unflag(uint64_t m, const uint32_t *__restrict__ col, uint32_t *out)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride)
+        out[j] = __ldg(col + j) & 0x7FFFFFFFu;
+}
+
 // ---------------------------------------------------------------- set-up --
 
 // CSR validation: rowptr non-decreasing, every colidx < n.
