@@ -284,6 +284,30 @@ MAP_API int map_graph_vertex_ids(const map_graph *g, uint32_t *ids);
  * every run); each may be NULL, host or device.  Not while a run is in flight. */
 MAP_API int map_graph_csr(const map_graph *g, uint32_t *rowptr, uint32_t *colidx, uint32_t *acc_bits);
 
+/*
+ * On-the-fly detection (Section 2 of the paper: one thread builds the matrix
+ * while another repeatedly runs the detection on the part built so far, so a
+ * cycle in that part is found before the state space is complete).
+ * Vertices are numbered in the order they become known; their rows are
+ * filled in the same order.  A row that is not yet filled is empty, so every
+ * run sees a subgraph of the final graph: a cycle it reports is a cycle of
+ * the final graph.
+ *
+ * map_grow_create -- n known vertices (accepting bits acc_bits, host or
+ * device), none expanded yet.
+ * map_append -- adds n_add vertices (n .. n + n_add - 1, bits acc_bits_add,
+ * LSB-first from the first new vertex; host or device) and fills the rows of
+ * the next k unexpanded vertices (rowptr_add: k + 1 offsets starting at 0;
+ * colidx_add: rowptr_add[k] targets, each below the new vertex count).  The
+ * resident graph stays on the device; only the chunk is copied from the
+ * host.  On any error the handle is unchanged.  Also works on graphs from
+ * map_create (all of their rows count as expanded).  Not for batched or
+ * reduced graphs; not while a run is in flight on the handle.
+ */
+MAP_API int map_grow_create(uint32_t n, const uint32_t *acc_bits, void *cuda_stream, map_graph **out);
+MAP_API int map_append(map_graph *g, uint32_t n_add, const uint32_t *acc_bits_add, uint32_t k,
+                       const uint32_t *rowptr_add, const uint32_t *colidx_add);
+
 /* map_graph_info -- n and m of a graph (either pointer may be NULL). */
 MAP_API int map_graph_info(const map_graph *g, uint32_t *n, uint64_t *m);
 

@@ -255,3 +255,42 @@ def tiny_graph(seed: int, n: int, max_deg: int = 4, acc_p: float = 0.3, self_loo
         rows.append(r)
     acc = (rng.random(n) < acc_p).astype(np.uint8)
     return from_lists(rows, acc, f"tiny-{seed}-{n}")
+
+
+# ------------------------------------------------------ on-the-fly streams --
+
+def discovery_order(g: Graph, start: int = 0):
+    """The part of g reachable from `start`, renumbered in breadth-first discovery order (the order
+    an explicit-state generator numbers states in), and known[R] = the vertices known once rows
+    0 .. R-1 are expanded (R = 0 .. n).  Returns (graph, known)."""
+    rowptr = g.rowptr.astype(np.int64)
+    colidx = g.colidx.astype(np.int64)
+    newid = np.full(g.n, -1, np.int64)
+    newid[start] = 0
+    order = [np.array([start], np.int64)]
+    count, front = 1, order[0]
+    while front.size:
+        b, e = rowptr[front], rowptr[front + 1]
+        cnt = e - b
+        succ = colidx[np.repeat(b - (np.cumsum(cnt) - cnt), cnt) + np.arange(int(cnt.sum()))]
+        cand = succ[newid[succ] < 0]
+        _, first = np.unique(cand, return_index=True)
+        fresh = cand[np.sort(first)]  # first occurrences, in queue order
+        newid[fresh] = count + np.arange(fresh.size)
+        count += fresh.size
+        order.append(fresh)
+        front = fresh
+    order = np.concatenate(order)
+    deg = (rowptr[order + 1] - rowptr[order])
+    rp = np.concatenate([[0], np.cumsum(deg)]).astype(np.uint32)
+    src_pos = np.repeat(rowptr[order] - (np.cumsum(deg) - deg), deg) + np.arange(int(deg.sum()))
+    ci = newid[colidx[src_pos]].astype(np.uint32)
+    out = Graph(n=len(order), rowptr=rp, colidx=ci, acc=g.acc[order].astype(np.uint8),
+                name=f"{g.name}-discovery", meta=dict(g.meta, start=start, order="bfs-discovery"))
+    # known after R rows: the start, the expanded rows and every target seen so far
+    known = np.maximum(np.arange(out.n + 1, dtype=np.int64), 1)
+    if len(ci):
+        seen = np.maximum.accumulate(ci.astype(np.int64)) + 1  # after each edge
+        R = np.flatnonzero(rp > 0)
+        known[R] = np.maximum(known[R], seen[rp[R].astype(np.int64) - 1])
+    return out, known

@@ -33,7 +33,8 @@ STATUS_NAMES = ["MAP_OK", "MAP_ERR_ARG", "MAP_ERR_CSR", "MAP_ERR_OOM", "MAP_ERR_
 # exported symbols of include/map.h (checked by the tests)
 EXPORTS = ["map_create", "map_run", "map_destroy", "map_graph_info", "map_last_error", "map_run_static",
            "map_batch_create", "map_batch_run", "map_server_create", "map_submit", "map_poll", "map_server_destroy",
-           "map_autotune", "map_lasso", "map_create_reduced", "map_graph_vertex_ids", "map_graph_csr"]
+           "map_autotune", "map_lasso", "map_create_reduced", "map_graph_vertex_ids", "map_graph_csr",
+           "map_grow_create", "map_append"]
 MAP_STATIC_MAX_N = 65536
 MAP_STATIC_MAX_M = 524288
 
@@ -147,9 +148,12 @@ def load(path: str = LIB_PATH):
     lib.map_create_reduced.argtypes = [u32, vp, vp, vp, vp, vp, ctypes.POINTER(vp)]
     lib.map_graph_vertex_ids.argtypes = [vp, vp]
     lib.map_graph_csr.argtypes = [vp, vp, vp, vp]
+    lib.map_grow_create.argtypes = [u32, vp, vp, ctypes.POINTER(vp)]
+    lib.map_append.argtypes = [vp, u32, vp, u32, vp, vp]
     for f in ("map_create", "map_run", "map_destroy", "map_graph_info", "map_run_static", "map_batch_create",
               "map_batch_run", "map_server_create", "map_submit", "map_poll", "map_server_destroy", "map_autotune",
-              "map_lasso", "map_create_reduced", "map_graph_vertex_ids", "map_graph_csr"):
+              "map_lasso", "map_create_reduced", "map_graph_vertex_ids", "map_graph_csr", "map_grow_create",
+              "map_append"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -203,6 +207,27 @@ def map_create_reduced(n: int, rowptr, colidx, acc_bits, part=None, stream=None)
     if rc != MAP_OK:
         raise MapError(rc, "map_create_reduced", last_error())
     return h
+
+
+def map_grow_create(n: int, acc_bits, stream=None):
+    """A growing graph of n known vertices, none expanded (see include/map.h)."""
+    ab, k = _ptr(acc_bits)
+    h = ctypes.c_void_p()
+    rc = load().map_grow_create(n, ab, _stream_handle(stream), ctypes.byref(h))
+    if rc != MAP_OK:
+        raise MapError(rc, "map_grow_create", last_error())
+    return h
+
+
+def map_append(handle, n_add: int, acc_bits_add, rowptr_add=None, colidx_add=None):
+    """Add n_add known vertices and the rows of the next len(rowptr_add) - 1 unexpanded ones."""
+    k = 0 if rowptr_add is None else len(rowptr_add) - 1
+    ab, k1 = _ptr(acc_bits_add)
+    rp, k2 = _ptr(rowptr_add)
+    ci, k3 = _ptr(colidx_add)
+    rc = load().map_append(handle, n_add, ab, k, rp, ci)
+    if rc != MAP_OK:
+        raise MapError(rc, "map_append", last_error())
 
 
 def map_graph_info(handle):

@@ -96,6 +96,7 @@ struct map_graph {
     uint4 *rec = nullptr;      // n: per-vertex round state (snapshots, list and frontier flags)
     uint32_t *touched = nullptr, *xbuf = nullptr;
     uint32_t *ids = nullptr; // reduced graphs: the original id of each vertex (else NULL: identity)
+    uint32_t rows = 0;       // rows expanded so far (growing graphs); the rest are empty
     bool dirty = false; // a run stopped early: per-round state may be stale
     uint32_t *hist = nullptr; // rounds per outer iteration
     uint32_t hist_cap = 0;
@@ -422,6 +423,7 @@ int create_graph(uint32_t n, uint64_t m, cudaStream_t s, const char *who, Upload
     if (!g) return fail(MAP_ERR_OOM, "%s: host allocation failed", who);
     g->n = n;
     g->m = m;
+    g->rows = n;
     g->words = (n + 31) / 32;
     g->stream = s;
     g->G = pick_group(n, m);
@@ -996,6 +998,95 @@ int map_create_reduced(uint32_t n, const uint32_t *rowptr, const uint32_t *colid
         return fail(MAP_ERR_CUDA, "map_create_reduced: %s", cudaGetErrorString(cudaGetLastError()));
     }
     return rc;
+}
+
+int map_grow_create(uint32_t n, const uint32_t *acc_bits, void *cuda_stream, map_graph **out)
+{
+    g_err.clear();
+    if (!out) return fail(MAP_ERR_ARG, "map_grow_create: out is NULL");
+    *out = nullptr;
+    if (n == 0 || n >= 0x7FFFFFFFu) return fail(MAP_ERR_ARG, "map_grow_create: n = %u out of range [1, 2^31-1)", n);
+    if (!acc_bits) return fail(MAP_ERR_ARG, "map_grow_create: acc_bits is required");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const int rc = create_graph(n, 0, s, "map_grow_create",
+                                [&](map_graph *g, uint32_t **acc) -> int {
+                                    CK(cudaMemsetAsync(g->rowptr, 0, ((size_t)n + 1) * 4, s));
+                                    *acc = g->acc;
+                                    CK(cudaMemcpyAsync(g->acc, acc_bits, (size_t)g->words * 4, cudaMemcpyDefault, s));
+                                    return MAP_OK;
+                                },
+                                out);
+    if (rc == MAP_OK) (*out)->rows = 0;
+    return rc;
+}
+
+int map_append(map_graph *g, uint32_t n_add, const uint32_t *acc_bits_add, uint32_t k, const uint32_t *rowptr_add,
+               const uint32_t *colidx_add)
+{
+    g_err.clear();
+    if (!g) return fail(MAP_ERR_ARG, "map_append: NULL graph");
+    if (g->comp || g->ids) return fail(MAP_ERR_ARG, "map_append: not for batched or reduced graphs");
+    const uint64_t n2 = (uint64_t)g->n + n_add;
+    if (n2 >= 0x7FFFFFFFu) return fail(MAP_ERR_ARG, "map_append: %llu vertices out of range", (unsigned long long)n2);
+    if ((uint64_t)g->rows + k > n2)
+        return fail(MAP_ERR_ARG, "map_append: %u rows for %llu unexpanded vertices", k,
+                    (unsigned long long)(n2 - g->rows));
+    if ((n_add && !acc_bits_add) || (k && !rowptr_add)) return fail(MAP_ERR_ARG, "map_append: NULL argument");
+    cudaStream_t s = g->stream;
+    uint32_t ends[2] = {0, 0}; // chunk offsets: first and last
+    if (k) {
+        if (is_device_ptr(rowptr_add)) {
+            CK(cudaMemcpyAsync(&ends[0], rowptr_add, 4, cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(&ends[1], rowptr_add + k, 4, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+        } else {
+            ends[0] = rowptr_add[0];
+            ends[1] = rowptr_add[k];
+        }
+    }
+    if (ends[0] != 0) return fail(MAP_ERR_CSR, "map_append: rowptr_add[0] = %u, expected 0", ends[0]);
+    const uint64_t madd = ends[1], m0 = g->m, m2 = m0 + madd;
+    if (madd && !colidx_add) return fail(MAP_ERR_ARG, "map_append: colidx_add is NULL but the rows hold %llu edges",
+                                         (unsigned long long)madd);
+    if (m2 > 0xFFFFFFFFull) return fail(MAP_ERR_ARG, "map_append: %llu edges out of range", (unsigned long long)m2);
+    const uint32_t r = g->rows, n0 = g->n;
+    const auto kind = [](const void *p) { return is_device_ptr(p) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; };
+    map_graph *ng = nullptr;
+    int rc = create_graph(
+        (uint32_t)n2, m2, s, "map_append",
+        [&](map_graph *x, uint32_t **acc) -> int {
+            // the resident part stays on the device; only the chunk crosses from the host
+            CK(cudaMemcpyAsync(x->rowptr, g->rowptr, ((size_t)r + 1) * 4, cudaMemcpyDeviceToDevice, s));
+            if (k) CK(cudaMemcpyAsync(x->rowptr + r, rowptr_add, ((size_t)k + 1) * 4, kind(rowptr_add), s));
+            mapk::k_grow_rowptr<<<grid_for(x, n2 - r + 1, 1), 256, 0, s>>>(x->rowptr, r, k, (uint32_t)n2, (uint32_t)m0,
+                                                                          (uint32_t)m2);
+            CK(cudaGetLastError());
+            if (m0) {
+                mapk::k_unflag<<<grid_for(x, m0, 1), 256, 0, s>>>(m0, g->colidx, x->colidx);
+                CK(cudaGetLastError());
+            }
+            if (madd) CK(cudaMemcpyAsync(x->colidx + m0, colidx_add, madd * 4, kind(colidx_add), s));
+            const uint32_t *add = acc_bits_add;
+            uint32_t *tmp = nullptr;
+            if (n_add && !is_device_ptr(add)) {
+                int rc2 = ck_alloc(&tmp, (n_add + 31) / 32, s);
+                if (rc2) return rc2;
+                CK(cudaMemcpyAsync(tmp, add, (size_t)((n_add + 31) / 32) * 4, cudaMemcpyHostToDevice, s));
+                add = tmp;
+            }
+            mapk::k_grow_acc<<<grid_for(x, x->words, 1), 256, 0, s>>>(x->acc, x->words, g->acc0, n0, add, n_add);
+            const cudaError_t e = cudaGetLastError();
+            if (tmp) cudaFreeAsync(tmp, s);
+            CK(e);
+            *acc = x->acc;
+            return MAP_OK;
+        },
+        &ng);
+    if (rc) return rc;
+    ng->rows = r + k;
+    std::swap(*g, *ng); // the caller's handle now holds the grown graph
+    free_graph(ng);
+    return MAP_OK;
 }
 
 int map_graph_vertex_ids(const map_graph *g, uint32_t *ids)

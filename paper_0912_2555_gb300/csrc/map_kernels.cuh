@@ -1257,6 +1257,41 @@ __global__ void k_unflag(uint64_t m, const uint32_t *__restrict__ col, uint32_t 
         out[j] = __ldg(col + j) & 0x7FFFFFFFu;
 }
 
+// ------------------------------------------------------- on-the-fly growth --
+//
+// A growing graph (the paper's detection on the part of the matrix computed so
+// far): rows [0, r) are expanded, rows [r, n) still empty.  An append copies
+// the next k rows to rowptr[r .. r + k] (relative to the chunk) and adds n_add
+// vertices; these kernels shift the chunk to the end of the edge array and
+// assemble the accepting bitmap.
+
+// rowptr[r .. r + k] hold the chunk's offsets: add m0; rows past them are empty
+__global__ void k_grow_rowptr(uint32_t *rowptr, uint32_t r, uint32_t k, uint32_t n2, uint32_t m0, uint32_t m2)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)r + blockIdx.x * blockDim.x + threadIdx.x; i <= n2; i += stride)
+        rowptr[i] = (k && i - r <= k) ? rowptr[i] + m0 : m2;
+}
+
+// out (ceil(n2 / 32) words) = bits [0, n0) of old, then bits [0, n_add) of add
+__global__ void k_grow_acc(uint32_t *out, uint32_t words2, const uint32_t *__restrict__ old, uint32_t n0,
+                           const uint32_t *__restrict__ add, uint32_t n_add)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t n2 = (uint64_t)n0 + n_add;
+    for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words2; w += stride) {
+        uint32_t x = 0;
+        for (uint32_t t = 0; t < 32; ++t) {
+            const uint64_t b = w * 32 + t;
+            uint32_t bit = 0;
+            if (b < n0) bit = (__ldg(old + (b >> 5)) >> (b & 31u)) & 1u;
+            else if (b < n2) bit = (__ldg(add + ((b - n0) >> 5)) >> ((b - n0) & 31u)) & 1u;
+            x |= bit << t;
+        }
+        out[w] = x;
+    }
+}
+
 // ---------------------------------------------------------------- set-up --
 
 // CSR validation: rowptr non-decreasing, every colidx < n.

@@ -150,3 +150,20 @@ def test_outer_limit():
     g = mapgen.from_lists([[1], [2], []], [1, 1, 1])
     r = oracle.run_graph(g, max_outer=2)
     assert r.status == oracle.LIMIT and r.outer == 2
+
+
+def test_discovery_order_is_a_bfs_numbering():
+    """Input plumbing for the on-the-fly tests: a renumbering of the reachable part in which
+    breadth-first distance never decreases and every vertex is known before its row is expanded."""
+    g = mapgen.random_graph(3000, 1, 4, 0.05, seed=11)
+    d, known = mapgen.discovery_order(g, start=5)
+    dist = oracle.bfs_dist(g.n, g.rowptr, g.colidx, 5)
+    assert d.n == int(np.count_nonzero(dist >= 0))
+    dd = oracle.bfs_dist(d.n, d.rowptr, d.colidx, 0)
+    assert np.all(np.diff(dd) >= 0) and np.all(dd >= 0)
+    assert sorted(np.diff(d.rowptr.astype(np.int64))) == sorted(
+        np.diff(g.rowptr.astype(np.int64))[dist >= 0])
+    for R in range(d.n + 1):
+        top = int(d.colidx[:d.rowptr[R]].max()) + 1 if d.rowptr[R] else 1
+        assert known[R] == max(R, 1, top)
+    assert known[-1] == d.n
