@@ -107,9 +107,12 @@ def test_append_to_a_created_graph_and_errors(pkg):
         pkg.map_append(h, 2, pkg.pack_bits([0, 1]), np.array([0, 1, 2], np.uint32), np.array([3, 2], np.uint32))
         rp, ci, ab = pkg.map_graph_csr(h)
         assert list(rp) == [0, 1, 2, 3, 4] and list(ci) == [1, 0, 3, 2] and ab[0] == 0b1001
-        r = pkg.map_run(h)
-        assert (r.verdict, r.witness) == (1, 3)
-        for args, code in [((0, None, np.array([1, 1], np.uint32), np.array([0], np.uint32)), pkg.MAP_ERR_CSR),
+        out = np.empty(4, np.uint32)
+        r = pkg.map_run(h, map_out=out)
+        want = oracle.run(4, rp, ci, [1, 0, 0, 1])  # 0 and 3 are self-mapped: the smaller is the witness
+        assert (r.verdict, r.witness, want.witness) == (1, 0, 0) and np.array_equal(out, want.map)
+        for args, code in [((1, pkg.pack_bits([0]), np.array([1, 1], np.uint32), np.array([0], np.uint32)),
+                            pkg.MAP_ERR_CSR),
                            ((1, pkg.pack_bits([0]), np.array([0, 1], np.uint32), np.array([9], np.uint32)),
                             pkg.MAP_ERR_CSR),
                            ((0, None, np.array([0, 1], np.uint32), np.array([0], np.uint32)), pkg.MAP_ERR_ARG)]:
@@ -119,7 +122,7 @@ def test_append_to_a_created_graph_and_errors(pkg):
         # the handle is unchanged by the failed appends
         rp2, ci2, _ = pkg.map_graph_csr(h)
         assert np.array_equal(rp, rp2) and np.array_equal(ci, ci2)
-        assert pkg.map_run(h).witness == 3
+        assert pkg.map_run(h).witness == 0
     finally:
         pkg.map_destroy(h)
     hb = pkg.map_batch_create([(g.n, g.rowptr, g.colidx, pkg.pack_bits(g.acc))])
