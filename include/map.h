@@ -342,7 +342,7 @@ MAP_API int map_graph_info(const map_graph *g, uint32_t *n, uint64_t *m);
  */
 #define MAP_STATIC_MAX_N 65536u
 #define MAP_STATIC_MAX_M 524288u
-#define MAP_STATIC_SCRATCH_BYTES 10523648u
+#define MAP_STATIC_SCRATCH_BYTES 10532096u
 MAP_API int map_run_static(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const uint32_t *acc_bits,
                            const map_opts *opts, map_result *res, uint32_t *map_out, void *cuda_stream);
 

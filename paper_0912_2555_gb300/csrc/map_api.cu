@@ -95,6 +95,7 @@ struct map_graph {
     uint32_t *flist = nullptr; // 3n: frontier rows of a round, by round mod 3
     uint4 *rec = nullptr;      // n: per-vertex round state (snapshots, list and frontier flags)
     uint32_t *touched = nullptr, *xbuf = nullptr;
+    uint32_t *stale = nullptr; // words: vertices whose mval the next dense round must reset
     uint32_t *ids = nullptr; // reduced graphs: the original id of each vertex (else NULL: identity)
     uint32_t rows = 0;       // rows expanded so far (growing graphs); the rest are empty
     bool dirty = false; // a run stopped early: per-round state may be stale
@@ -134,6 +135,7 @@ void free_graph(map_graph *g)
         if (p) cudaFreeAsync(p, g->stream); // stream-ordered: no device-wide synchronisation
     if (g->comp) cudaFreeAsync(g->comp, g->stream);
     if (g->ids) cudaFreeAsync(g->ids, g->stream);
+    if (g->stale) cudaFreeAsync(g->stale, g->stream);
     if (g->cs) cudaFreeAsync(g->cs, g->stream);
     if (g->chist) cudaFreeAsync(g->chist, g->stream);
     free(g->h_cs);
@@ -226,6 +228,7 @@ mapk::Dev dev_of(const map_graph *g)
     }
     d.rec = g->rec;
     d.touched = g->touched;
+    d.stale = g->comp ? nullptr : g->stale;
     d.ctl = g->ctl;
     d.comp = g->comp;
     d.cs = g->cs;
@@ -463,7 +466,7 @@ int create_graph(uint32_t n, uint64_t m, cudaStream_t s, const char *who, Upload
         (rc = alloc(&g->elog, n)) || (rc = alloc(&g->acc0, W)) ||
         (rc = alloc(&g->acc, W)) || (rc = alloc(&g->mval, n)) || (rc = alloc(&g->list, 3 * (uint64_t)n)) ||
         (rc = alloc(&g->flist, 3 * (uint64_t)n)) || (rc = alloc((uint32_t **)&g->rec, 4 * (uint64_t)n)) ||
-        (rc = alloc(&g->touched, n)) || (rc = alloc(&g->xbuf, n)) ||
+        (rc = alloc(&g->touched, n)) || (rc = alloc(&g->xbuf, n)) || (rc = alloc(&g->stale, W)) ||
         (rc = alloc(&g->hist, g->hist_cap))) {
         free_graph(g);
         return rc;
@@ -500,7 +503,8 @@ int create_graph(uint32_t n, uint64_t m, cudaStream_t s, const char *who, Upload
     }
     if ((rc = ck(cudaMemsetAsync(g->colidx + m, 0, 16, s), "pad")) ||
         (rc = ck(cudaMemsetAsync(g->mval, 0, ((size_t)n + 4) * 4, s), "memset mval")) ||
-        (rc = ck(cudaMemsetAsync(g->rec, 0, (size_t)n * 16, s), "memset rec"))) {
+        (rc = ck(cudaMemsetAsync(g->rec, 0, (size_t)n * 16, s), "memset rec")) ||
+        (rc = ck(cudaMemsetAsync(g->stale, 0, ((size_t)W + 4) * 4, s), "memset stale"))) {
         free_graph(g);
         return rc;
     }
@@ -1296,7 +1300,8 @@ constexpr uint64_t ST_RPOS = ST_RCOL + st_pad(ST_MAX_M + 4);
 constexpr uint64_t ST_ELOG = ST_RPOS + st_pad(ST_MAX_M + 4);
 constexpr uint64_t ST_ACC0 = ST_ELOG + st_pad(ST_MAX_N + 4);
 constexpr uint64_t ST_ACC = ST_ACC0 + st_pad(ST_MAX_W + 4);
-constexpr uint64_t ST_MVAL = ST_ACC + st_pad(ST_MAX_W + 4);
+constexpr uint64_t ST_STALE = ST_ACC + st_pad(ST_MAX_W + 4);
+constexpr uint64_t ST_MVAL = ST_STALE + st_pad(ST_MAX_W + 4);
 constexpr uint64_t ST_LIST = ST_MVAL + st_pad(ST_MAX_N + 4);
 constexpr uint64_t ST_FLIST = ST_LIST + st_pad(3 * ST_MAX_N);
 constexpr uint64_t ST_REC = ST_FLIST + st_pad(3 * ST_MAX_N);
@@ -1422,6 +1427,7 @@ extern "C" int map_run_static(uint32_t n, const uint32_t *rowptr, const uint32_t
     g.elog = base + ST_ELOG;
     g.acc0 = base + ST_ACC0;
     g.acc = base + ST_ACC;
+    g.stale = base + ST_STALE;
     g.mval = base + ST_MVAL;
     g.list = base + ST_LIST;
     g.flist = base + ST_FLIST;
@@ -1443,6 +1449,7 @@ extern "C" int map_run_static(uint32_t n, const uint32_t *rowptr, const uint32_t
     CK(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
     CK(cudaMemsetAsync(g.mval, 0, ((size_t)n + 4) * 4, s));
     CK(cudaMemsetAsync(g.rec, 0, (size_t)n * 16, s));
+    CK(cudaMemsetAsync(g.stale, 0, ((size_t)W + 4) * 4, s));
     CK(cudaMemsetAsync(g.rrowptr, 0, ((size_t)n + 1) * 4, s));
     mapk::k_validate<<<grid_for(&g, m > n ? m : n, 1), 256, 0, s>>>(n, g.rowptr, m, g.colidx, &ctl->bad);
     mapk::k_acc_init<<<grid_for(&g, W, 1), 256, 0, s>>>(n, g.acc, g.acc0, &ctl->elim.v);

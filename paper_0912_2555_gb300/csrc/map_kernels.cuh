@@ -137,6 +137,7 @@ struct Dev {
     uint32_t *list[3], *flist[3];
     uint4 *rec; // .x / .y / .z: snap[0..2]; .w: flags
     uint32_t *touched;
+    uint32_t *stale; // single graphs: bit v = mval[v] holds a value of an earlier outer iteration (NULL: batched)
     Ctl *ctl;
 };
 
@@ -515,9 +516,13 @@ __global__ void k_run_begin(Ctl *c, Handles hd)
 // the tile's rowptr slice (fetched one tile ahead into registers) goes to a
 // warp-private shared slice; the tile's edge span is streamed with 128-bit
 // loads (WT_UNROLL per lane in flight); an edge whose target is accepting finds
-// its row by binary search in the slice and does a shared-memory atomicMax; the tile's values are written out coalesced
-// (this also resets the previous iteration's values).  Every row that got a
-// value goes to list[1] (with its value in snap[1]) and to the touched list.
+// its row by binary search in the slice and does a shared-memory atomicMax.
+// The first dense round of a run writes the tile's values out coalesced (this
+// also resets whatever the previous run left).  Later ones write only the rows
+// that got a value or still hold one from the previous outer iteration (bit v
+// of the stale bitmap, set by k_check for every touched vertex), so mval costs
+// n / 4 bitmap bytes per round instead of 4n.  Every row that got a value goes
+// to list[1] (with its value in snap[1]) and to the touched list.
 constexpr int DT_THREADS = 256;
 constexpr int WT_WARPS = DT_THREADS / 32;
 constexpr int WT_ROWS = 128;
@@ -549,6 +554,8 @@ __global__ void __launch_bounds__(DT_THREADS, MAPGPU_DENSE_MIN_BLOCKS) k_dense(c
     uint32_t *rp = s_rp[warp], *best = s_best[warp];
     const uint32_t ntiles = (n + WT_ROWS - 1) / WT_ROWS;
     const uint32_t nw = gridDim.x * WT_WARPS;
+    // sparse write-back from the second outer iteration of a run on
+    const bool sparse = d.stale && *(volatile uint32_t *)&ctl->outer > 1;
 #pragma unroll
     for (int k = 0; k < 4; ++k) best[lane * 4 + k] = 0;
 
@@ -623,12 +630,22 @@ __global__ void __launch_bounds__(DT_THREADS, MAPGPU_DENSE_MIN_BLOCKS) k_dense(c
 #pragma unroll
             for (int k = 0; k < 4; ++k)
                 if (bs[k] == 0xFFFFFFFFu) bs[k] = 0;
+        } else if (sparse) { // rows [4 lane, 4 lane + 4) are bits 4 (lane % 8) .. of word 4 t + lane / 8
+            const uint32_t wi = t * 4 + (lane >> 3);
+            const uint32_t old4 = wi < d.words ? (d.stale[wi] >> ((lane & 7u) * 4)) & 0xFu : 0u;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (lane * 4 + k < rows && (bs[k] || ((old4 >> k) & 1u))) d.mval[r0 + lane * 4 + k] = bs[k];
         } else if (lane * 4 + 3 < rows) {
             reinterpret_cast<uint4 *>(d.mval + r0)[lane] = b4;
         } else {
 #pragma unroll
             for (int k = 0; k < 4; ++k)
                 if (lane * 4 + k < rows) d.mval[r0 + lane * 4 + k] = bs[k];
+        }
+        if (d.stale) {
+            __syncwarp(); // every lane has read its bits
+            if (lane < 4 && t * 4 + lane < d.words) d.stale[t * 4 + lane] = 0;
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -977,9 +994,9 @@ __global__ void __launch_bounds__(256) k_check(const Dev d, Handles hd)
     // warp-uniform loop (batched runs aggregate per graph within the warp)
     for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < nt; base += nthreads) {
         const uint64_t i = base + lane_id();
-        uint32_t c = 0xFFFFFFFFu, removed = 0;
+        uint32_t c = 0xFFFFFFFFu, removed = 0, v = 0;
         if (i < nt) {
-            const uint32_t v = __ldg(d.touched + i);
+            v = __ldg(d.touched + i);
             const uint32_t x = __ldg(d.mval + v);
             const uint32_t u = x - 1; // x != 0 for a touched vertex
             if (d.comp) c = __ldg(d.comp + v);
@@ -998,6 +1015,12 @@ __global__ void __launch_bounds__(256) k_check(const Dev d, Handles hd)
                     for (uint32_t j = b; j < e; ++j) d.colidx_w[__ldg(d.rpos + j)] = u;
                 }
             }
+        }
+        if (d.stale) { // v holds a value now: the next dense round resets it (one atomic per word in the warp)
+            const uint32_t wd = i < nt ? v >> 5 : 0xFFFFFFFFu;
+            const unsigned same = __match_any_sync(0xFFFFFFFFu, wd);
+            const uint32_t bits = __reduce_or_sync(same, i < nt ? 1u << (v & 31u) : 0u);
+            if (wd != 0xFFFFFFFFu && lane_id() == (unsigned)(__ffs(same) - 1)) atomicOr(d.stale + wd, bits);
         }
         if (d.comp) { // per graph: touched vertices and removals, one atomic per graph in the warp
             const unsigned same = __match_any_sync(0xFFFFFFFFu, c);
