@@ -368,6 +368,7 @@ def main():
     # later ones read the bitmap (n / 8) and write only the rows that get or lose a value (not
     # counted: a lower bound, about 1 % of the rows on this graph)
     outer = prof[0].outer
+    words = (g.n + 31) // 32
     stream_bytes = 4 * (g.n + 1) + 4 * g.m + g.n // 8
     run_dense_bytes = outer * stream_bytes + 4 * g.n + (outer - 1) * (g.n // 8)
     dense_bytes = run_dense_bytes / outer  # average per launch
