@@ -154,6 +154,24 @@ __device__ __forceinline__ uint32_t *pick3(uint32_t p, uint32_t *const (&a)[3])
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
+// asynchronous global -> shared copies (cp.async): 16 bytes (src_bytes < 16: the rest is
+// zero-filled), 4 bytes; a commit closes a group, wait<N> leaves at most N groups in flight
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, uint32_t src_bytes)
+{
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
+{
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ bool acc_bit(const uint32_t *__restrict__ acc, uint32_t u)
 {
     return (__ldg(acc + (u >> 5)) >> (u & 31u)) & 1u;
@@ -520,8 +538,10 @@ __global__ void k_run_begin(Ctl *c, Handles hd)
 // The first dense round of a run writes the tile's values out coalesced (this
 // also resets whatever the previous run left).  Later ones write only the rows
 // that got a value or still hold one from the previous outer iteration (bit v
-// of the stale bitmap, set by k_check for every touched vertex), so mval costs
-// n / 4 bitmap bytes per round instead of 4n.  Every row that got a value goes
+// of the stale bitmap, fetched a tile ahead), so mval costs n / 4 bitmap bytes
+// per round instead of 4n.  The round rewrites each tile's bitmap words with
+// the rows that got a value; the push rounds add the vertices they raise from
+// "no value".  Every row that got a value goes
 // to list[1] (with its value in snap[1]) and to the touched list.
 constexpr int DT_THREADS = 256;
 constexpr int WT_WARPS = DT_THREADS / 32;
@@ -535,7 +555,8 @@ constexpr size_t DT_SMEM = 0; // static shared memory only
 
 __global__ void __launch_bounds__(DT_THREADS, MAPGPU_DENSE_MIN_BLOCKS) k_dense(const Dev d, Handles hd)
 {
-    __shared__ __align__(16) uint32_t s_rp[WT_WARPS][WT_ROWS + 4];
+    // per warp, two buffers: the tile's rowptr slice [0, WT_ROWS], its stale words at WT_ROWS + 4
+    __shared__ __align__(16) uint32_t s_rp[2][WT_WARPS][WT_ROWS + 8];
     __shared__ __align__(16) uint32_t s_best[WT_WARPS][WT_ROWS];
     __shared__ uint32_t s_stage[WT_WARPS][SB_ENTRIES];
     __shared__ uint32_t s_cnt[WT_WARPS][1], s_base[1];
@@ -551,7 +572,7 @@ __global__ void __launch_bounds__(DT_THREADS, MAPGPU_DENSE_MIN_BLOCKS) k_dense(c
     const uint32_t *__restrict__ rowptr = d.rowptr;
     const uint32_t *__restrict__ colidx = d.colidx;
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
-    uint32_t *rp = s_rp[warp], *best = s_best[warp];
+    uint32_t *best = s_best[warp];
     const uint32_t ntiles = (n + WT_ROWS - 1) / WT_ROWS;
     const uint32_t nw = gridDim.x * WT_WARPS;
     // sparse write-back from the second outer iteration of a run on
@@ -559,29 +580,35 @@ __global__ void __launch_bounds__(DT_THREADS, MAPGPU_DENSE_MIN_BLOCKS) k_dense(c
 #pragma unroll
     for (int k = 0; k < 4; ++k) best[lane * 4 + k] = 0;
 
-    // rowptr words r0 + 4 lane .. + 3 of tile t (only words that exist: <= r0 + rows + 3)
-    auto load_rp = [&](uint32_t t, uint4 &q, uint32_t &last) {
+    // tile t into buffer b by asynchronous copies (nothing held in registers while in flight):
+    // rowptr words r0 + 4 lane .. + 3 (lanes past the tile's last row copy nothing and fill
+    // zeros), rowptr[r0 + WT_ROWS] of a full tile, and in sparse mode the tile's 4 stale words
+    auto issue = [&](uint32_t t, uint32_t b) {
         const uint32_t r0 = t * WT_ROWS, rows = min((uint32_t)WT_ROWS, n - r0);
-        q = lane * 4 <= rows ? __ldg(reinterpret_cast<const uint4 *>(rowptr + r0) + lane) : make_uint4(0, 0, 0, 0);
-        last = (lane == 0 && rows == WT_ROWS) ? __ldg(rowptr + r0 + WT_ROWS) : 0;
+        uint32_t *dst = s_rp[b][warp];
+        const bool in = lane * 4 <= rows;
+        cp_async16(dst + 4 * lane, rowptr + r0 + (in ? 4 * lane : 0), in ? 16u : 0u);
+        if (lane == 0 && rows == WT_ROWS) cp_async4(dst + WT_ROWS, rowptr + r0 + WT_ROWS);
+        if (lane == 1 && sparse) cp_async16(dst + WT_ROWS + 4, d.stale + 4 * (uint64_t)t, 16u);
+        cp_async_commit();
     };
-    uint32_t t = blockIdx.x * WT_WARPS + warp;
-    uint4 q = make_uint4(0, 0, 0, 0);
-    uint32_t qlast = 0;
-    if (t < ntiles) load_rp(t, q, qlast);
-    for (; t < ntiles; t += nw) {
+    uint32_t t = blockIdx.x * WT_WARPS + warp, buf = 0;
+    if (t < ntiles) issue(t, 0);
+    for (; t < ntiles; t += nw, buf ^= 1u) {
         const uint32_t r0 = t * WT_ROWS, rows = min((uint32_t)WT_ROWS, n - r0);
+        if (t + nw < ntiles) { // the next tile's slice goes in flight; wait for this one's
+            issue(t + nw, buf ^ 1u);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncwarp();
         if (d.comp) { // batched: a tile inside one frozen graph is skipped whole
             const uint32_t c0 = __ldg(d.comp + r0), c1 = __ldg(d.comp + r0 + rows - 1);
-            if (c0 == c1 && !*(volatile uint32_t *)&d.cs[c0].active) {
-                if (t + nw < ntiles) load_rp(t + nw, q, qlast);
-                continue;
-            }
+            if (c0 == c1 && !*(volatile uint32_t *)&d.cs[c0].active) continue;
         }
-        reinterpret_cast<uint4 *>(rp)[lane] = q;
-        if (lane == 0 && rows == WT_ROWS) rp[WT_ROWS] = qlast;
-        if (t + nw < ntiles) load_rp(t + nw, q, qlast); // next tile's slice, in flight meanwhile
-        __syncwarp();
+        const uint32_t *rp = s_rp[buf][warp];
+        const uint32_t stale4 = sparse ? (rp[WT_ROWS + 4 + (lane >> 3)] >> ((lane & 7u) * 4)) & 0xFu : 0u;
         const uint32_t E0 = rp[0], E1 = rp[rows];
         for (uint32_t cs = E0 & ~3u; cs < E1; cs += 32 * 4 * WT_UNROLL) {
             uint4 w[WT_UNROLL];
@@ -630,12 +657,10 @@ __global__ void __launch_bounds__(DT_THREADS, MAPGPU_DENSE_MIN_BLOCKS) k_dense(c
 #pragma unroll
             for (int k = 0; k < 4; ++k)
                 if (bs[k] == 0xFFFFFFFFu) bs[k] = 0;
-        } else if (sparse) { // rows [4 lane, 4 lane + 4) are bits 4 (lane % 8) .. of word 4 t + lane / 8
-            const uint32_t wi = t * 4 + (lane >> 3);
-            const uint32_t old4 = wi < d.words ? (d.stale[wi] >> ((lane & 7u) * 4)) & 0xFu : 0u;
+        } else if (sparse) {
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                if (lane * 4 + k < rows && (bs[k] || ((old4 >> k) & 1u))) d.mval[r0 + lane * 4 + k] = bs[k];
+                if (lane * 4 + k < rows && (bs[k] || ((stale4 >> k) & 1u))) d.mval[r0 + lane * 4 + k] = bs[k];
         } else if (lane * 4 + 3 < rows) {
             reinterpret_cast<uint4 *>(d.mval + r0)[lane] = b4;
         } else {
@@ -643,9 +668,15 @@ __global__ void __launch_bounds__(DT_THREADS, MAPGPU_DENSE_MIN_BLOCKS) k_dense(c
             for (int k = 0; k < 4; ++k)
                 if (lane * 4 + k < rows) d.mval[r0 + lane * 4 + k] = bs[k];
         }
-        if (d.stale) {
-            __syncwarp(); // every lane has read its bits
-            if (lane < 4 && t * 4 + lane < d.words) d.stale[t * 4 + lane] = 0;
+        if (d.stale) { // the tile's bitmap words: the rows that hold a value now
+            uint32_t got4 = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) got4 |= (bs[k] != 0u) << k;
+            uint32_t word = got4 << ((lane & 7u) * 4);
+            word |= __shfl_xor_sync(0xFFFFFFFFu, word, 1);
+            word |= __shfl_xor_sync(0xFFFFFFFFu, word, 2);
+            word |= __shfl_xor_sync(0xFFFFFFFFu, word, 4);
+            if ((lane & 7u) == 0 && t * 4 + (lane >> 3) < d.words) d.stale[t * 4 + (lane >> 3)] = word;
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -947,6 +978,8 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
                     stage_append<3>(st, 0, act[j] && !(fold[j] & FB(p_out)), w[j], dst, ctr);
                     stage_append<3>(st, 1, raised && !(cold[j] & CB(p_out)), w[j], dst, ctr);
                     stage_append<3>(st, 2, raised && mold[j] == 0, w[j], dst, ctr);
+                    if (raised && mold[j] == 0 && d.stale) // the next dense round resets it
+                        atomicOr(d.stale + (w[j] >> 5), 1u << (w[j] & 31u));
                 }
             }
             __syncthreads(); // before the shared arrays are refilled
@@ -994,9 +1027,9 @@ __global__ void __launch_bounds__(256) k_check(const Dev d, Handles hd)
     // warp-uniform loop (batched runs aggregate per graph within the warp)
     for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < nt; base += nthreads) {
         const uint64_t i = base + lane_id();
-        uint32_t c = 0xFFFFFFFFu, removed = 0, v = 0;
+        uint32_t c = 0xFFFFFFFFu, removed = 0;
         if (i < nt) {
-            v = __ldg(d.touched + i);
+            const uint32_t v = __ldg(d.touched + i);
             const uint32_t x = __ldg(d.mval + v);
             const uint32_t u = x - 1; // x != 0 for a touched vertex
             if (d.comp) c = __ldg(d.comp + v);
@@ -1015,12 +1048,6 @@ __global__ void __launch_bounds__(256) k_check(const Dev d, Handles hd)
                     for (uint32_t j = b; j < e; ++j) d.colidx_w[__ldg(d.rpos + j)] = u;
                 }
             }
-        }
-        if (d.stale) { // v holds a value now: the next dense round resets it (one atomic per word in the warp)
-            const uint32_t wd = i < nt ? v >> 5 : 0xFFFFFFFFu;
-            const unsigned same = __match_any_sync(0xFFFFFFFFu, wd);
-            const uint32_t bits = __reduce_or_sync(same, i < nt ? 1u << (v & 31u) : 0u);
-            if (wd != 0xFFFFFFFFu && lane_id() == (unsigned)(__ffs(same) - 1)) atomicOr(d.stale + wd, bits);
         }
         if (d.comp) { // per graph: touched vertices and removals, one atomic per graph in the warp
             const unsigned same = __match_any_sync(0xFFFFFFFFu, c);
