@@ -619,6 +619,8 @@ __global__ void __launch_bounds__(DT_THREADS, MAPGPU_DENSE_MIN_BLOCKS) k_dense(c
             }
 #pragma unroll
             for (int j = 0; j < WT_UNROLL; ++j) {
+                // almost every entry points to a non-accepting vertex: one test per 128-bit load
+                if (((w[j].x | w[j].y | w[j].z | w[j].w) >> 31) == 0u) continue;
                 const uint32_t ebase = cs + (j * 32 + lane) * 4;
                 const uint32_t cs4[4] = {w[j].x, w[j].y, w[j].z, w[j].w};
 #pragma unroll
