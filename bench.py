@@ -6,7 +6,9 @@ fix-point, self-map test, elimination) over the 2^26-vertex layered no-cycle gra
 layers, 1 % accepting, accepting vertices on no cycle), inputs resident in HBM.
 
     metric  MAP edge relaxations/s, GTEPS = (m x outer iterations) / device time
-            (every fix-point examines every edge at least once)
+            (every fix-point examines every edge at least once), timed on the asynchronous
+            in-place schedule (same maps, verdict and outer count as the synchronous one, which
+            is timed after it and reported as `other_schedule` with its canonical counts)
     e2e     the same metric through the C ABI from pinned host buffers: map_create
             (host-to-device copy, validation, transpose) + map_run + map output
             device-to-host + map_destroy, every step
@@ -293,7 +295,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--sched", type=int, default=0, help="0 = synchronous rounds (canonical), 1 = asynchronous")
+    ap.add_argument("--sched", type=int, default=1,
+                    help="timed schedule: 1 = asynchronous in-place sweeps (default), 0 = synchronous rounds; "
+                         "the other schedule is timed after it and reported beside it")
     ap.add_argument("--cpu-outer", type=int, default=3, help="outer iterations in the CPU-oracle sample")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -356,6 +360,27 @@ def main():
         dist.barrier()
     ms = e0.elapsed_time(e1)
     value, ms, _ = replica_value(ms, sum(r.edges_total for r in results), device="cuda")
+
+    # the other schedule on the same graph and steps, reported beside the headline (both give the
+    # same maps, verdict and outer count; only the synchronous one has the canonical round counts)
+    other = 1 - args.sched
+    for _ in range(3):
+        pkg.map_run(h, sched=other, map_out=out)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ores = [pkg.map_run(h, sched=other, map_out=out) for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ovalue, oms, _ = replica_value(e0.elapsed_time(e1), sum(r.edges_total for r in ores), device="cuda")
+    other_line = {"sched": "sync" if other == 0 else "async", "value": ovalue, "unit": "GTEPS",
+                  "ms_per_step": oms / args.steps, "rounds_per_run": sum(ores[0].rounds),
+                  "relaxations_per_run": ores[0].relaxations, "canonical_counts": bool(ores[0].inner_canonical),
+                  "same_result": (ores[0].verdict, ores[0].witness, ores[0].outer) == (r0.verdict, r0.witness,
+                                                                                       r0.outer)}
 
     # roofline of the dominant kernel (the dense round): algorithmic bytes per launch over its
     # CUDA-event time.  Events cannot sit inside the graph's loop bodies, so this pass runs
@@ -422,11 +447,12 @@ def main():
                            l2="inputs larger than L2 (CSR 1.34 GB vs 129 MB L2); no flush",
                            parallelism="replicas" if ws > 1 else "single GPU"),
             "roofline": roofline, "run_roofline": run_roofline, "phases": phases, "e2e": e2e,
+            "other_schedule": other_line,
             "gpu_launches": sum(r.launches for r in results),
             "clocks": clk.summary()}
     pkg.map_destroy(h)
     if not args.no_batch and args.n is None and ws == 1:
-        line["batched"] = batched_leg(pkg, np, torch, stream, sched=args.sched)
+        line["batched"] = batched_leg(pkg, np, torch, stream, sched=0)  # canonical counts compared too
     if not args.no_serve and args.n is None and ws == 1:
         line["serving"] = serving_leg(pkg, np)
     if rank == 0 and ws == 1 and not args.no_cpu:

@@ -104,7 +104,9 @@ typedef struct {
     uint32_t outer_iters;     /* outer iterations executed (0 if no vertex is accepting) */
     uint32_t inner_canonical; /* 1 if inner_iters counts synchronous rounds (SYNC), 0 for ASYNC sweeps */
     uint64_t inner_iters;     /* rounds (or sweeps) summed over outer iterations */
-    uint64_t relaxations;     /* edges examined, summed over rounds */
+    uint64_t relaxations;     /* edges examined.  SYNC (canonical): the row lengths of every
+                                 round's frontier (round 1: all m); ASYNC: m per outer
+                                 iteration plus one per push (batched ASYNC runs: frontier) */
     uint64_t edges_total;     /* m x outer_iters: the edges a fix-point must examine at least once */
     double device_ms;         /* stream time of the whole run (CUDA events) */
     double dense_ms;          /* with MAP_FLAG_PROFILE: summed time of the dense-round kernel */
@@ -113,7 +115,8 @@ typedef struct {
     uint64_t launches;        /* kernel launches issued by this run */
     double round_ms;          /* with MAP_FLAG_PROFILE: summed time of the rounds after the first */
     double check_ms;          /* with MAP_FLAG_PROFILE: summed time of the self-map test + elimination */
-    uint64_t frontier_rows;   /* frontier rows summed over the rounds after the first */
+    uint64_t frontier_rows;   /* frontier rows summed over the rounds after the first (single-
+                                 graph ASYNC runs: the vertices that pushed) */
     uint32_t status;          /* map_status of this graph's run (batched runs report one per graph) */
     uint32_t reserved;
 } map_result;

@@ -641,6 +641,12 @@ __global__ void __launch_bounds__(DT_THREADS, MAPGPU_DENSE_MIN_BLOCKS) k_dense(c
         __syncwarp();
         const uint4 b4 = reinterpret_cast<const uint4 *>(best)[lane];
         uint32_t bs[4] = {b4.x, b4.y, b4.z, b4.w};
+        // sparse mode: a tile with no value now and none left from the previous iteration (most
+        // tiles) has nothing to write, append or mark, and its best[] slice is still zero
+        if (sparse && !__any_sync(0xFFFFFFFFu, (b4.x | b4.y | b4.z | b4.w | stale4) != 0u)) {
+            __syncwarp(); // every lane is done with this buffer before it is refilled
+            continue;
+        }
         if (d.comp) { // batched: rows of frozen graphs keep their values; record the change
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -860,6 +866,9 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
     const bool early = vc->early_exit && !d.comp;
     if (early && vc->self_seen.v) nl = 0; // the dense round already found a self-mapped vertex
     if (nl && max_inner < 2) status = ST_LIMIT;
+    // the frontier (rows reading a changed vertex) gives the canonical relaxation count of the
+    // synchronous schedule; a single-graph asynchronous run counts its pushes instead
+    const bool track = SYNC || d.comp;
     while (nl && status == ST_OK) {
         const uint32_t rr = r + 1; // this round
         const uint32_t p_in = (rr - 1) % 3, p_out = rr % 3, p_free = (rr + 1) % 3;
@@ -888,7 +897,7 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
         st.buf = s_stage[threadIdx.x >> 5];
         st.cnt[0] = st.cnt[1] = st.cnt[2] = 0;
         // the previous round's frontier: clear its flags, count its relaxations
-        relax += clear_frontier(pick3(p_in, d.flist), vc->fcnt[p_in].v, p_in, d.rec, d.rowptr, d);
+        if (track) relax += clear_frontier(pick3(p_in, d.flist), vc->fcnt[p_in].v, p_in, d.rec, d.rowptr, d);
 
         // chunks of RC_ENTRIES listed vertices per block (RC_E per thread, loaded
         // together); their (vertex, reader) pairs are spread evenly over the block's
@@ -930,6 +939,7 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
             }
             __syncthreads();
             const uint32_t total = s_incl[RC_ENTRIES - 1];
+            if (!track && threadIdx.x == 0) relax += total; // pushes of this chunk
             for (uint32_t p0 = 0; p0 < total; p0 += 256 * RC_P) {
                 uint32_t w[RC_P], ob[RC_P], fold[RC_P], mold[RC_P];
                 bool act[RC_P];
@@ -956,7 +966,7 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
                     fold[j] = FB(p_out);
                     mold[j] = 0xFFFFFFFFu;
                     if (act[j]) {
-                        fold[j] = atomicOr(rec_flags(d.rec + w[j]), FB(p_out));
+                        if (track) fold[j] = atomicOr(rec_flags(d.rec + w[j]), FB(p_out));
                         mold[j] = atomicMax(d.mval + w[j], ob[j]);
                     }
                 }
@@ -993,8 +1003,8 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
             break;
         }
         r = rr;
-        nl = vc->lcnt[p_out].v; // changed in this round
-        frows += vc->fcnt[p_out].v;
+        frows += track ? vc->fcnt[p_out].v : nl; // frontier rows, or the vertices that pushed
+        nl = vc->lcnt[p_out].v;                  // changed in this round
         if (early && nl && vc->self_seen.v) { // stop here: the cycle test will find the vertex
             nl = 0;
             if (lead) vc->early_hit = 1;
@@ -1003,7 +1013,7 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
         else if (nl && r + 1 > max_inner) status = ST_LIMIT;
     }
     // the last round's frontier: clear its flags, count its relaxations
-    if (r > 1) relax += clear_frontier(pick3(r % 3, d.flist), vc->fcnt[r % 3].v, r % 3, d.rec, d.rowptr, d);
+    if (r > 1 && track) relax += clear_frontier(pick3(r % 3, d.flist), vc->fcnt[r % 3].v, r % 3, d.rec, d.rowptr, d);
     block_add_u64(relax, (unsigned long long *)&ctl->relax.v);
     if (lead) {
         vc->k = r;
