@@ -37,11 +37,11 @@ METRIC = "MAP edge relaxations/s (GTEPS)"
 
 
 # DRAM traffic of one k_dense launch from the ncu capture summarised in
-# profiles/k_dense_layered-2p24.md (dram__bytes_read.sum + dram__bytes_write.sum on the 2^24-vertex
-# case, whose algorithmic bytes are 402,663,176); valid only for the kernel source it was taken on
+# profiles/k_dense_layered-2p24.md (dram__bytes_read.sum + dram__bytes_write.sum of one sparse-write
+# launch on the 2^24-vertex case, whose algorithmic bytes are 339,748,616); valid only for the kernel source it was taken on
 # (a hash of the kernel file up to the end of the dense-round section).
-DENSE_TRAFFIC = {"kernel_file_sha256_16": "d9c42e105ec7f753", "bytes": 392_964_352,
-                 "algorithmic_bytes": 402_663_176, "case": "layered 2^24 vertices, m = 67,111,361"}
+DENSE_TRAFFIC = {"kernel_file_sha256_16": "29fc0b7ad9440a13", "bytes": 350_538_496,
+                 "algorithmic_bytes": 339_748_616, "case": "layered 2^24 vertices, m = 67,111,361, outer iteration 4"}
 
 
 def _dense_traffic(dense_bytes):
