@@ -64,12 +64,24 @@ bool is_device_ptr(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+int pick_group(uint32_t n, uint64_t m)
+{
+    const double avg = n ? (double)m / n : 0.0;
+    if (avg < 1.5) return 1;
+    if (avg < 3.0) return 2;
+    if (avg < 6.0) return 4;
+    if (avg < 12.0) return 8;
+    if (avg < 24.0) return 16;
+    return 32;
+}
+
 } // namespace
 
 struct map_graph {
     uint32_t n = 0;
     uint64_t m = 0;
     uint32_t words = 0;
+    int G = 4;
     int sms = 0;
     int dense_grid = 0;  // blocks of the dense-round kernel
     int rounds_grid = 0; // blocks of the cooperative fix-point kernel (all resident)
@@ -176,6 +188,15 @@ int scan_inclusive(uint32_t *x, uint64_t len, cudaStream_t s)
     return MAP_OK;
 }
 
+#define DISPATCH_G(G, CALL)                                                                                        \
+    switch (G) {                                                                                                   \
+    case 1: { constexpr int GG = 1; CALL; } break;                                                                 \
+    case 2: { constexpr int GG = 2; CALL; } break;                                                                 \
+    case 4: { constexpr int GG = 4; CALL; } break;                                                                 \
+    case 8: { constexpr int GG = 8; CALL; } break;                                                                 \
+    case 16: { constexpr int GG = 16; CALL; } break;                                                               \
+    default: { constexpr int GG = 32; CALL; } break;                                                               \
+    }
 
 int read_ctl(map_graph *g)
 {
@@ -408,6 +429,7 @@ int create_graph(uint32_t n, uint64_t m, cudaStream_t s, const char *who, Upload
     g->rows = n;
     g->words = (n + 31) / 32;
     g->stream = s;
+    g->G = pick_group(n, m);
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev);
@@ -513,8 +535,8 @@ int create_graph(uint32_t n, uint64_t m, cudaStream_t s, const char *who, Upload
         free_graph(g);
         return rc;
     }
-    mapk::k_transpose_tiles<<<grid_for(g, (n + mapk::TT_ROWS - 1) / mapk::TT_ROWS, 32), 256, 0, s>>>(
-        n, g->rowptr, g->colidx, g->list, g->rcol, g->rpos);
+    DISPATCH_G(g->G, (mapk::k_transpose<GG><<<grid_for(g, n, GG), 256, 0, s>>>(n, g->rowptr, g->colidx, g->list,
+                                                                              g->rcol, g->rpos)));
     // the accepting flag of each target into bit 31 of its entry (restored after every run)
     mapk::k_pack_flags<<<grid_for(g, m, 1), 256, 0, s>>>(m, g->colidx, g->acc0);
     if ((rc = ck(cudaGetLastError(), "transpose")) || (rc = ck(cudaStreamSynchronize(s), "create sync"))) {
@@ -1382,6 +1404,7 @@ extern "C" int map_run_static(uint32_t n, const uint32_t *rowptr, const uint32_t
     g.m = m;
     g.words = (n + 31) / 32;
     g.stream = s;
+    g.G = pick_group(n, m);
     int dev = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&g.sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1440,8 +1463,8 @@ extern "C" int map_run_static(uint32_t n, const uint32_t *rowptr, const uint32_t
     CK(cudaGetLastError());
     if ((rc = static_scan(g.rrowptr, (uint64_t)n + 1, sums, s))) return rc;
     CK(cudaMemcpyAsync(g.list, g.rrowptr, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
-    mapk::k_transpose_tiles<<<grid_for(&g, (n + mapk::TT_ROWS - 1) / mapk::TT_ROWS, 32), 256, 0, s>>>(
-        n, g.rowptr, g.colidx, g.list, g.rcol, g.rpos);
+    DISPATCH_G(g.G, (mapk::k_transpose<GG><<<grid_for(&g, n, GG), 256, 0, s>>>(n, g.rowptr, g.colidx, g.list,
+                                                                             g.rcol, g.rpos)));
     mapk::k_pack_flags<<<grid_for(&g, m, 1), 256, 0, s>>>(m, g.colidx, g.acc);
     CK(cudaGetLastError());
 

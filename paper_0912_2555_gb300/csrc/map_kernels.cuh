@@ -1413,54 +1413,23 @@ __global__ void k_scan_add(uint32_t *x, uint64_t len, const uint32_t *__restrict
     if (blockIdx.x > 0 && i < len) x[i] += sums[blockIdx.x - 1];
 }
 
-// Transpose scatter: every entry i of row w appends w (and i) to the reader list
-// of its target u, at cursor[u]++.  Warp tiles of TT_ROWS rows: the tile's rowptr
-// slice goes to shared memory and the lanes take the tile's edges TT_U at a time
-// each, so that TT_U cursor atomics per lane are in flight together; an edge's
-// row is found by binary search in the slice.  (Reader lists come out in no
-// particular order; nothing depends on it.)
-constexpr int TT_ROWS = 128, TT_U = 4;
-
-__global__ void __launch_bounds__(256) k_transpose_tiles(uint32_t n, const uint32_t *__restrict__ rowptr,
-                                                         const uint32_t *__restrict__ colidx, uint32_t *cursor,
-                                                         uint32_t *rcol, uint32_t *rpos)
+// transpose scatter: the group of row w appends w (and the entry's position) to
+// the reader list of each u in row w
+template <int G>
+__global__ void __launch_bounds__(256) k_transpose(uint32_t n, const uint32_t *__restrict__ rowptr,
+                                                   const uint32_t *__restrict__ colidx, uint32_t *cursor,
+                                                   uint32_t *rcol, uint32_t *rpos)
 {
-    __shared__ uint32_t s_rp[8][TT_ROWS + 1];
-    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
-    uint32_t *rp = s_rp[warp];
-    const uint32_t ntiles = (n + TT_ROWS - 1) / TT_ROWS;
-    for (uint32_t t = blockIdx.x * 8 + warp; t < ntiles; t += gridDim.x * 8) {
-        const uint32_t r0 = t * TT_ROWS, rows = min((uint32_t)TT_ROWS, n - r0);
-        for (uint32_t k = lane; k <= rows; k += 32) rp[k] = __ldg(rowptr + r0 + k);
-        __syncwarp();
-        const uint32_t E0 = rp[0], E1 = rp[rows];
-        for (uint32_t c = E0; c < E1; c += 32 * TT_U) {
-            uint32_t u[TT_U], w[TT_U], slot[TT_U];
-#pragma unroll
-            for (int j = 0; j < TT_U; ++j) {
-                const uint32_t e = c + j * 32 + lane;
-                u[j] = e < E1 ? __ldg(colidx + e) : 0u;
-                uint32_t lo = 0, hi = rows; // rp[lo] <= e < rp[hi]: the row of e is the last such lo
-                while (hi - lo > 1) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (rp[mid] <= e) lo = mid;
-                    else hi = mid;
-                }
-                w[j] = r0 + lo;
-            }
-#pragma unroll
-            for (int j = 0; j < TT_U; ++j)
-                if (c + j * 32 + lane < E1) slot[j] = atomicAdd(cursor + u[j], 1u);
-#pragma unroll
-            for (int j = 0; j < TT_U; ++j) {
-                const uint32_t e = c + j * 32 + lane;
-                if (e < E1) {
-                    rcol[slot[j]] = w[j];
-                    rpos[slot[j]] = e;
-                }
-            }
+    const unsigned glane = threadIdx.x & (G - 1);
+    const uint64_t groups = (uint64_t)gridDim.x * blockDim.x / G;
+    for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; w < n; w += groups) {
+        const uint32_t b = __ldg(rowptr + w), e = __ldg(rowptr + w + 1);
+        for (uint32_t i = b + glane; i < e; i += G) {
+            const uint32_t u = __ldg(colidx + i);
+            const uint32_t slot = atomicAdd(cursor + u, 1u);
+            rcol[slot] = (uint32_t)w;
+            rpos[slot] = i;
         }
-        __syncwarp();
     }
 }
 
