@@ -1630,8 +1630,11 @@ void server_worker(map_server *sv, cudaStream_t stream)
         map_graph *g = nullptr;
         int rc = map_create(job->n, rp, ci, ab, stream, &g);
         if (rc == MAP_OK) {
+            // the whole run as one CUDA graph (building it costs well under a millisecond); the
+            // map comes back by DMA into the staging buffer (map_create has consumed the inputs)
             job->map.resize(job->n);
-            rc = run_impl(g, &job->opts, &job->res, job->map.data(), true);
+            rc = run_impl(g, &job->opts, &job->res, stage ? stage : job->map.data());
+            if (stage && rc == MAP_OK) memcpy(job->map.data(), stage, (size_t)job->n * 4);
             job->res.status = (uint32_t)rc;
             map_destroy(g);
         }
