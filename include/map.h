@@ -194,7 +194,9 @@ MAP_API int map_batch_run(map_graph *g, const map_opts *opts, map_result *result
 /*
  * Serving: verification jobs submitted over time and run with continuous
  * admission.  The server has max_slots worker threads, each with its own CUDA
- * stream.  A job is copied at submission and queued; the oldest queued job is
+ * stream.  A job is copied at submission, into the server's pinned staging
+ * memory (a quarter of hbm_budget_bytes, at most 2 GiB; pageable memory when it
+ * is full, which only costs speed), and queued; the oldest queued job is
  * started as soon as a worker is free and its device footprint (about
  * 4 * (3m + 18n) bytes) fits into what is left of hbm_budget_bytes (a job
  * larger than the whole budget runs when nothing else does).  Jobs that arrive
@@ -208,7 +210,8 @@ MAP_API int map_batch_run(map_graph *g, const map_opts *opts, map_result *result
  *   *job_id identifies the job.
  * map_poll     -- MAP_ERR_NOT_READY while the job is queued or running;
  *   otherwise the job's status, with res and (optional) map_out (n entries,
- *   host memory) filled, and the job is released (poll it once).
+ *   host memory) filled, and the job and its staging memory are released (poll
+ *   it once).
  * map_server_destroy -- finishes the jobs already admitted and queued, then
  *   frees everything; unpolled results are discarded.
  * The server's calls may come from any host threads.

@@ -15,6 +15,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -1534,11 +1535,66 @@ extern "C" int map_run_static(uint32_t n, const uint32_t *rowptr, const uint32_t
 
 namespace {
 
+// Pinned host arena of a server: a job's inputs are copied in once at submission
+// (into memory that is already mapped and pinned, so the copy to the device is a
+// DMA transfer from there) and its map comes back into the same slot.  First fit
+// over a free list of 256-byte pieces, used under the server's lock.
+struct PinnedArena {
+    uint8_t *base = nullptr;
+    std::map<size_t, size_t> free; // offset -> bytes
+    static size_t round(size_t b) { return (b + 255) & ~size_t(255); }
+    void init(size_t bytes)
+    {
+        if (bytes && cudaMallocHost((void **)&base, bytes) == cudaSuccess) {
+            free[0] = bytes;
+        } else {
+            cudaGetLastError();
+            base = nullptr;
+        }
+    }
+    uint32_t *alloc(size_t bytes)
+    {
+        if (!base) return nullptr;
+        bytes = round(bytes);
+        for (auto it = free.begin(); it != free.end(); ++it) {
+            if (it->second < bytes) continue;
+            const size_t off = it->first, rest = it->second - bytes;
+            free.erase(it);
+            if (rest) free[off + bytes] = rest;
+            return reinterpret_cast<uint32_t *>(base + off);
+        }
+        return nullptr;
+    }
+    void release(uint32_t *p, size_t bytes)
+    {
+        const size_t off = reinterpret_cast<uint8_t *>(p) - base;
+        auto it = free.emplace(off, round(bytes)).first;
+        auto nx = std::next(it);
+        if (nx != free.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free.erase(nx);
+        }
+        if (it != free.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free.erase(it);
+            }
+        }
+    }
+    ~PinnedArena()
+    {
+        if (base) cudaFreeHost(base);
+    }
+};
+
 struct ServerJob {
     uint64_t id = 0;
     uint32_t n = 0;
     uint64_t m = 0;
-    std::vector<uint32_t> rowptr, colidx, acc;
+    uint32_t *pin = nullptr; // arena slot: rowptr, colidx, accepting words; later the map
+    size_t pin_bytes = 0;
+    std::vector<uint32_t> rowptr, colidx, acc; // inputs when the arena had no room
     map_opts opts{};
     size_t footprint = 0;
     bool done = false;
@@ -1552,7 +1608,7 @@ struct ServerJob {
 size_t graph_footprint(uint64_t n, uint64_t m)
 {
     const uint64_t W = (n + 31) / 32;
-    const uint64_t words = 2 * (n + 5) + 3 * (m + 4) + 2 * (W + 4) + (n + 4) + 2 * 3 * (n + 4) + 4 * (n + 4) +
+    const uint64_t words = 2 * (n + 5) + 3 * (m + 4) + 3 * (W + 4) + (n + 4) + 2 * 3 * (n + 4) + 4 * (n + 4) +
                            3 * (n + 4) + (1u << 16);
     return (size_t)words * 4 + sizeof(Ctl) + (1u << 20);
 }
@@ -1571,6 +1627,7 @@ struct map_server {
     std::unordered_map<uint64_t, ServerJob *> jobs;
     std::vector<std::thread> workers;
     std::vector<cudaStream_t> streams;
+    PinnedArena arena;
 };
 
 namespace {
@@ -1603,10 +1660,10 @@ void server_worker(map_server *sv, cudaStream_t stream)
             sv->queue.pop_front();
             sv->used += job->footprint;
         }
-        // the job's inputs into this worker's pinned staging buffer (grown when needed), so
-        // that the copies to the device are asynchronous DMA transfers
+        // a job outside the arena: its inputs into this worker's pinned staging buffer (grown
+        // when needed), so that the copies to the device are asynchronous DMA transfers
         const size_t words = (size_t)job->n + 1 + job->m + job->acc.size();
-        if (words > stage_words) {
+        if (!job->pin && words > stage_words) {
             if (stage) cudaFreeHost(stage);
             stage = nullptr;
             stage_words = 0;
@@ -1614,7 +1671,11 @@ void server_worker(map_server *sv, cudaStream_t stream)
             else cudaGetLastError();
         }
         const uint32_t *rp = job->rowptr.data(), *ci = job->m ? job->colidx.data() : nullptr, *ab = job->acc.data();
-        if (stage) {
+        if (job->pin) { // already in pinned memory
+            rp = job->pin;
+            ci = job->m ? job->pin + job->n + 1 : nullptr;
+            ab = job->pin + job->n + 1 + job->m;
+        } else if (stage) {
             uint32_t *p = stage;
             memcpy(p, rp, ((size_t)job->n + 1) * 4);
             rp = p;
@@ -1632,9 +1693,13 @@ void server_worker(map_server *sv, cudaStream_t stream)
         if (rc == MAP_OK) {
             // the whole run as one CUDA graph (building it costs well under a millisecond); the
             // map comes back by DMA into the staging buffer (map_create has consumed the inputs)
-            job->map.resize(job->n);
-            rc = run_impl(g, &job->opts, &job->res, stage ? stage : job->map.data());
-            if (stage && rc == MAP_OK) memcpy(job->map.data(), stage, (size_t)job->n * 4);
+            if (job->pin) { // into the job's arena slot, read out by map_poll
+                rc = run_impl(g, &job->opts, &job->res, job->pin);
+            } else {
+                job->map.resize(job->n);
+                rc = run_impl(g, &job->opts, &job->res, stage ? stage : job->map.data());
+                if (stage && rc == MAP_OK) memcpy(job->map.data(), stage, (size_t)job->n * 4);
+            }
             job->res.status = (uint32_t)rc;
             map_destroy(g);
         }
@@ -1672,6 +1737,8 @@ int map_server_create(size_t hbm_budget_bytes, uint32_t max_slots, map_server **
         hbm_budget_bytes = free_b / 2;
     }
     sv->budget = hbm_budget_bytes;
+    // pinned staging for queued and finished jobs: a quarter of the device budget, at most 2 GiB
+    sv->arena.init(std::min<size_t>(hbm_budget_bytes / 4, (size_t)2 << 30));
     for (uint32_t i = 0; i < max_slots; ++i) {
         cudaStream_t st;
         cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
@@ -1700,15 +1767,27 @@ int map_submit(map_server *sv, uint32_t n, const uint32_t *rowptr, const uint32_
     if (m > 0 && !colidx) return fail(MAP_ERR_ARG, "map_submit: colidx is NULL");
     ServerJob *job = new (std::nothrow) ServerJob;
     if (!job) return fail(MAP_ERR_OOM, "map_submit: host allocation failed");
-    try {
-        job->n = n;
-        job->m = m;
-        job->rowptr.assign(rowptr, rowptr + (size_t)n + 1);
-        job->colidx.assign(colidx, colidx + m);
-        job->acc.assign(acc_bits, acc_bits + (n + 31) / 32);
-    } catch (...) {
-        delete job;
-        return fail(MAP_ERR_OOM, "map_submit: host allocation failed");
+    job->n = n;
+    job->m = m;
+    const size_t W = (n + 31) / 32, bytes = ((size_t)n + 1 + m + W) * 4;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        job->pin = sv->arena.alloc(bytes);
+    }
+    if (job->pin) { // one copy, into pinned memory
+        job->pin_bytes = bytes;
+        memcpy(job->pin, rowptr, ((size_t)n + 1) * 4);
+        if (m) memcpy(job->pin + n + 1, colidx, m * 4);
+        memcpy(job->pin + n + 1 + m, acc_bits, W * 4);
+    } else {
+        try {
+            job->rowptr.assign(rowptr, rowptr + (size_t)n + 1);
+            job->colidx.assign(colidx, colidx + m);
+            job->acc.assign(acc_bits, acc_bits + W);
+        } catch (...) {
+            delete job;
+            return fail(MAP_ERR_OOM, "map_submit: host allocation failed");
+        }
     }
     if (opts) job->opts = *opts;
     job->opts.rounds_out = nullptr;
@@ -1739,7 +1818,11 @@ int map_poll(map_server *sv, uint64_t job_id, map_result *res, uint32_t *map_out
         sv->jobs.erase(it);
     }
     if (res) *res = job->res;
-    if (map_out && job->status == MAP_OK) memcpy(map_out, job->map.data(), (size_t)job->n * 4);
+    if (map_out && job->status == MAP_OK) memcpy(map_out, job->pin ? job->pin : job->map.data(), (size_t)job->n * 4);
+    if (job->pin) {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->arena.release(job->pin, job->pin_bytes);
+    }
     const int rc = job->status;
     if (rc != MAP_OK) fail(rc, "%s", job->err.c_str());
     delete job;
