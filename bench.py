@@ -186,6 +186,45 @@ def cpu_baseline(g, outer):
                       f"including the oracle's own set-up)"}
 
 
+def configs_leg(pkg, np, torch, stream, steps=10):
+    """The two other single-graph workloads, resident in HBM, both schedules: the 16,384-vertex
+    random graph (both variants; latency-bound, reported in microseconds per run) and the
+    8 x 7 lock-step process product (2 x 7^8 vertices; GTEPS)."""
+    import mapgen
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(g):
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
+        h = pkg.map_create(g.n, dev(g.rowptr), dev(g.colidx), dev(pkg.pack_bits(g.acc)), stream)
+        out = {}
+        try:
+            for sched, name in ((1, "async"), (0, "sync")):
+                for _ in range(3):
+                    r = pkg.map_run(h, sched=sched)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                for _ in range(steps):
+                    r = pkg.map_run(h, sched=sched)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / steps
+                out[name] = {"us_per_run": ms * 1e3, "gteps": g.m * r.outer / (ms / 1e3) / 1e9,
+                             "verdict": r.verdict, "witness": r.witness, "outer": r.outer,
+                             "rounds": sum(r.rounds)}
+        finally:
+            pkg.map_destroy(h)
+        return out
+
+    res = {}
+    for variant in ("cycle", "nocycle"):
+        g = mapgen.random_16k(variant)
+        res[f"random-16k-{variant}"] = dict(n=g.n, m=g.m, **timed(g))
+    g = mapgen.product_8x7()
+    res["product-8x7"] = dict(n=g.n, m=g.m, **timed(g))
+    return res
+
+
 def batched_leg(pkg, np, torch, stream, count=256, steps=2, sched=0):
     """256 graphs (sizes log-uniform in [1e3, 2e6], 40 % with a planted accepting cycle, layered
     recipe) in one batched run, against the same 256 graphs run one after another with map_run.
@@ -452,6 +491,7 @@ def main():
             "clocks": clk.summary()}
     pkg.map_destroy(h)
     if not args.no_batch and args.n is None and ws == 1:
+        line["configs"] = configs_leg(pkg, np, torch, stream)
         line["batched"] = batched_leg(pkg, np, torch, stream, sched=0)  # canonical counts compared too
     if not args.no_serve and args.n is None and ws == 1:
         line["serving"] = serving_leg(pkg, np)
