@@ -69,7 +69,7 @@ struct Ctl {
     Cnt32 bar_count;       // grid barrier of k_rounds: arrivals
     Cnt32 bar_gen;         // ... and generation
     Cnt32 stop_req;        // k_rounds: block 0 asks every block to stop after the next barrier
-    Cnt32 self_seen;       // early exit: some vertex became its own map value
+    Cnt32 self_seen;       // smallest vertex seen to become its own map value (NONE: none yet)
     // fix-point loop
     uint32_t k;            // rounds completed in the current outer iteration
     // outer loop
@@ -371,6 +371,9 @@ __device__ void epilogue_check(Ctl *c, Handles hd)
     if (outer - 1 < v->hist_cap) c->rounds_hist[outer - 1] = k;
     v->inner_total = v->inner_total + k;
     uint32_t go = 1;
+    // early exit: a vertex that received its own value lies on an accepting cycle, even if a
+    // later push of the same round raised it past that value (values only grow)
+    if (v->early_exit && v->self_seen.v < v->witness.v) v->witness.v = v->self_seen.v;
     if (v->status != ST_OK) {
         go = 0; // a limit was hit inside the fix-point loop
     } else if (v->witness.v != NONE) {
@@ -505,7 +508,7 @@ __global__ void k_run_begin(Ctl *c, Handles hd)
     v->frontier_rows.v = 0;
     v->bar_count.v = 0;
     v->stop_req.v = 0;
-    v->self_seen.v = 0;
+    v->self_seen.v = NONE;
     v->early_hit = 0;
     v->k = 0;
     v->status = ST_OK;
@@ -693,7 +696,7 @@ __global__ void __launch_bounds__(DT_THREADS, MAPGPU_DENSE_MIN_BLOCKS) k_dense(c
             if (got) {
                 best[lane * 4 + k] = 0;
                 *rec_snap(d.rec + v, 1) = bs[k];
-                if (bs[k] == v + 1) ctl->self_seen.v = 1; // v reaches itself: an accepting cycle
+                if (bs[k] == v + 1) atomicMin(&ctl->self_seen.v, v); // v reaches itself: an accepting cycle
             }
             stage_append<1>(st, 0, got, v, dst, ctr);
         }
@@ -867,7 +870,7 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
     uint32_t nl = vc->lcnt[1].v; // vertices that got a value in the dense round
     uint32_t r = 1;              // rounds completed
     const bool early = vc->early_exit && !d.comp;
-    if (early && vc->self_seen.v) nl = 0; // the dense round already found a self-mapped vertex
+    if (early && vc->self_seen.v != NONE) nl = 0; // the dense round already found a self-mapped vertex
     if (nl && max_inner < 2) status = ST_LIMIT;
     // the frontier (rows reading a changed vertex) gives the canonical relaxation count of the
     // synchronous schedule; a single-graph asynchronous run counts its pushes instead
@@ -998,7 +1001,7 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
 #pragma unroll
                 for (int j = 0; j < RC_P; ++j) {
                     const bool raised = act[j] && ob[j] > mold[j];
-                    if (raised && ob[j] == w[j] + 1) ctl->self_seen.v = 1; // w reaches itself
+                    if (raised && ob[j] == w[j] + 1) atomicMin(&ctl->self_seen.v, w[j]); // w reaches itself
                     if (raised && d.comp) { // batched: this graph changed in this round
                         const uint32_t c = __ldg(d.comp + w[j]);
                         if (*(volatile uint32_t *)&d.cs[c].last_change < rr) atomicMax(&d.cs[c].last_change, rr);
@@ -1023,7 +1026,7 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
                         }
                         bool take = false;
                         if (r2) {
-                            if (cob == x + 1) ctl->self_seen.v = 1;
+                            if (cob == x + 1) atomicMin(&ctl->self_seen.v, x);
                             if (nx == NONE && depth < CH_DEPTH)
                                 take = __ldg(d.rrowptr + x + 1) - __ldg(d.rrowptr + x) <= CH_DEG;
                         }
@@ -1059,7 +1062,7 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
         r = rr;
         frows += track ? vc->fcnt[p_out].v : nl; // frontier rows, or the vertices that pushed
         nl = vc->lcnt[p_out].v;                  // changed in this round
-        if (early && nl && vc->self_seen.v) { // stop here: the cycle test will find the vertex
+        if (early && nl && vc->self_seen.v != NONE) { // stop here: the recorded vertex is the witness
             nl = 0;
             if (lead) vc->early_hit = 1;
         }
