@@ -840,9 +840,6 @@ __device__ __forceinline__ bool grid_barrier(Ctl *ctl)
 constexpr int RC_E = 1;                 // listed vertices per thread and chunk
 constexpr int RC_ENTRIES = 256 * RC_E;  // per block and chunk
 constexpr int RC_P = 1;                 // push pairs per thread and step
-// asynchronous schedule, single graph: a lane chases a raised vertex with at most CH_DEG
-// readers, and at most CH_DEPTH further vertices per pushed pair
-constexpr uint32_t CH_DEG = 4, CH_DEPTH = 64;
 
 // The fix-point loop of one outer iteration: rounds 2, 3, ... until a round
 // changes nothing.  Round r reads list[(r-1) % 3] and appends to list[r % 3];
@@ -875,7 +872,6 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
     // the frontier (rows reading a changed vertex) gives the canonical relaxation count of the
     // synchronous schedule; a single-graph asynchronous run counts its pushes instead
     const bool track = SYNC || d.comp;
-    const bool chase = !SYNC && !d.comp;
     while (nl && status == ST_OK) {
         const uint32_t rr = r + 1; // this round
         const uint32_t p_in = (rr - 1) % 3, p_out = rr % 3, p_free = (rr + 1) % 3;
@@ -977,25 +973,13 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
                         mold[j] = atomicMax(d.mval + w[j], ob[j]);
                     }
                 }
-                // asynchronous single graph: a raised vertex with few readers is chased (pushed
-                // on by this lane right away) instead of being listed for the next round
-                uint32_t cw = NONE, cob = 0, cj = 0, ce = 0;
                 uint32_t cold[RC_P];
 #pragma unroll
                 for (int j = 0; j < RC_P; ++j) {
                     cold[j] = CB(p_out);
                     if (act[j] && ob[j] > mold[j]) { // raised; the record's sector is in L2 by now
                         if (SYNC) atomicMax(rec_snap(d.rec + w[j], p_out), ob[j]);
-                        if (chase && j == 0) {
-                            const uint32_t b0 = __ldg(d.rrowptr + w[j]), e0 = __ldg(d.rrowptr + w[j] + 1);
-                            if (e0 - b0 <= CH_DEG) {
-                                cw = w[j];
-                                cob = acc_bit(d.acc, cw) ? max(ob[j], cw + 1) : ob[j];
-                                cj = b0;
-                                ce = e0;
-                            }
-                        }
-                        if (cw == NONE) cold[j] = atomicOr(rec_flags(d.rec + w[j]), CB(p_out));
+                        cold[j] = atomicOr(rec_flags(d.rec + w[j]), CB(p_out));
                     }
                 }
 #pragma unroll
@@ -1011,44 +995,6 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
                     stage_append<3>(st, 2, raised && mold[j] == 0, w[j], dst, ctr);
                     if (raised && mold[j] == 0 && d.stale) // the next dense round resets it
                         atomicOr(d.stale + (w[j] >> 5), 1u << (w[j] & 31u));
-                }
-                if (chase) { // warp-uniform: one push per chasing lane and step
-                    uint32_t nx = NONE, depth = 0;
-                    while (__any_sync(0xFFFFFFFFu, cw != NONE)) {
-                        bool r2 = false;
-                        uint32_t x = 0, mx = 0;
-                        if (cw != NONE && cj < ce) {
-                            x = __ldg(d.rcol + cj);
-                            ++cj;
-                            ++relax;
-                            mx = atomicMax(d.mval + x, cob);
-                            r2 = cob > mx;
-                        }
-                        bool take = false;
-                        if (r2) {
-                            if (cob == x + 1) atomicMin(&ctl->self_seen.v, x);
-                            if (nx == NONE && depth < CH_DEPTH)
-                                take = __ldg(d.rrowptr + x + 1) - __ldg(d.rrowptr + x) <= CH_DEG;
-                        }
-                        const bool lx = r2 && !take;
-                        const uint32_t cx = lx ? atomicOr(rec_flags(d.rec + x), CB(p_out)) : CB(p_out);
-                        stage_append<3>(st, 1, lx && !(cx & CB(p_out)), x, dst, ctr);
-                        stage_append<3>(st, 2, r2 && mx == 0, x, dst, ctr);
-                        if (r2 && mx == 0 && d.stale) atomicOr(d.stale + (x >> 5), 1u << (x & 31u));
-                        if (take) nx = x;
-                        if (cw != NONE && cj >= ce) { // cw's readers are done: on to the next vertex
-                            if (nx != NONE) {
-                                cob = acc_bit(d.acc, nx) ? max(cob, nx + 1) : cob;
-                                cw = nx;
-                                cj = __ldg(d.rrowptr + nx);
-                                ce = __ldg(d.rrowptr + nx + 1);
-                                nx = NONE;
-                                ++depth;
-                            } else {
-                                cw = NONE;
-                            }
-                        }
-                    }
                 }
             }
             __syncthreads(); // before the shared arrays are refilled
