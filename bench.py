@@ -40,7 +40,7 @@ METRIC = "MAP edge relaxations/s (GTEPS)"
 # profiles/k_dense_layered-2p24.md (dram__bytes_read.sum + dram__bytes_write.sum of one sparse-write
 # launch on the 2^24-vertex case, whose algorithmic bytes are 339,748,616); valid only for the kernel source it was taken on
 # (a hash of the kernel file up to the end of the dense-round section).
-DENSE_TRAFFIC = {"kernel_file_sha256_16": "29fc0b7ad9440a13", "bytes": 350_538_496,
+DENSE_TRAFFIC = {"kernel_file_sha256_16": "eee78e80cd55c45e", "bytes": 351_072_000,
                  "algorithmic_bytes": 339_748_616, "case": "layered 2^24 vertices, m = 67,111,361, outer iteration 4"}
 
 
@@ -339,7 +339,7 @@ def main():
                          "the other schedule is timed after it and reported beside it")
     ap.add_argument("--cpu-outer", type=int, default=3, help="outer iterations in the CPU-oracle sample")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--n", type=int, default=None, help="override vertex count (smaller runs, not the bench line)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched leg (256 graphs)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg (Poisson arrivals)")
@@ -461,16 +461,21 @@ def main():
     # end to end through the C ABI from pinned host buffers
     hp = [torch.from_numpy(x.view(np.int32)).pin_memory() for x in (g.rowptr, g.colidx, pkg.pack_bits(g.acc))]
     hout = torch.empty(g.n, dtype=torch.int32).pin_memory()
+
+    def e2e_step():
+        h2 = pkg.map_create(g.n, hp[0], hp[1], hp[2], stream)
+        try:
+            return pkg.map_run(h2, sched=args.sched, map_out=hout)
+        finally:
+            pkg.map_destroy(h2)
+
+    if args.e2e_steps:
+        e2e_step()  # warm-up: the device memory pool grows to hold a second copy of the graph
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_edges = 0
     for _ in range(args.e2e_steps):
-        h2 = pkg.map_create(g.n, hp[0], hp[1], hp[2], stream)
-        try:
-            r2 = pkg.map_run(h2, sched=args.sched, map_out=hout)
-        finally:
-            pkg.map_destroy(h2)
-        e2e_edges += r2.edges_total
+        e2e_edges += e2e_step().edges_total
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e = None if args.e2e_steps == 0 else {"value": e2e_edges / e2e_s / 1e9 * ws, "unit": "GTEPS",
