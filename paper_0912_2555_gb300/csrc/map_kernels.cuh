@@ -840,6 +840,10 @@ __device__ __forceinline__ bool grid_barrier(Ctl *ctl)
 constexpr int RC_E = 1;                 // listed vertices per thread and chunk
 constexpr int RC_ENTRIES = 256 * RC_E;  // per block and chunk
 constexpr int RC_P = 1;                 // push pairs per thread and step
+#ifndef MAPGPU_LC_PASSES
+#define MAPGPU_LC_PASSES 4 // asynchronous schedule: block-local passes over a block's own raised vertices per round
+#endif
+constexpr uint32_t LC_PASSES = MAPGPU_LC_PASSES;
 
 // The fix-point loop of one outer iteration: rounds 2, 3, ... until a round
 // changes nothing.  Round r reads list[(r-1) % 3] and appends to list[r % 3];
@@ -855,6 +859,7 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
     __shared__ uint32_t s_stage[8][3 * SB_ENTRIES];
     __shared__ uint32_t s_cnt[8][3], s_base[3];
     __shared__ uint32_t s_incl[RC_ENTRIES], s_o[RC_ENTRIES], s_b[RC_ENTRIES], s_scan[8];
+    __shared__ uint32_t s_loc[8 * SB_ENTRIES], s_lc[8]; // block-local continuation
     __shared__ uint32_t *s_dst[3][2];
     __shared__ unsigned int *s_ctr[3];
     Ctl *ctl = d.ctl;
@@ -872,6 +877,7 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
     // the frontier (rows reading a changed vertex) gives the canonical relaxation count of the
     // synchronous schedule; a single-graph asynchronous run counts its pushes instead
     const bool track = SYNC || d.comp;
+    const bool local = !SYNC && !d.comp;
     while (nl && status == ST_OK) {
         const uint32_t rr = r + 1; // this round
         const uint32_t p_in = (rr - 1) % 3, p_out = rr % 3, p_free = (rr + 1) % 3;
@@ -909,7 +915,32 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
         // every block takes an even contiguous share of the list
         const uint64_t per = (nl + gridDim.x - 1) / gridDim.x;
         const uint64_t beg = (uint64_t)blockIdx.x * per, end = min((uint64_t)nl, beg + per);
-        for (uint64_t c0 = beg; c0 < end; c0 += RC_ENTRIES) {
+        // asynchronous single graph: once its share of the list is done, the block goes on with
+        // the vertices it raised itself that are still in its staging buffers (up to LC_PASSES
+        // passes), so that values travel several edges per round without a grid barrier each
+        uint64_t c0 = beg, cend = end;
+        bool loc = false; // chunk entries from s_loc (this block's raised vertices) instead of the list
+        uint32_t lpass = 0;
+        for (;;) {
+            if (c0 >= cend) {
+                if (!local || lpass >= LC_PASSES) break;
+                const unsigned warp = threadIdx.x >> 5;
+                if (lane == 0) s_lc[warp] = st.cnt[1];
+                __syncthreads();
+                uint32_t off = 0, L = 0;
+                for (unsigned w = 0; w < 8; ++w) {
+                    off += w < warp ? s_lc[w] : 0u;
+                    L += s_lc[w];
+                }
+                for (uint32_t i = lane; i < st.cnt[1]; i += 32) s_loc[off + i] = st.buf[SB_ENTRIES + i];
+                st.cnt[1] = 0;
+                __syncthreads(); // s_loc complete; s_lc read by every thread
+                if (L == 0) break;
+                loc = true;
+                c0 = 0;
+                cend = L;
+                ++lpass;
+            }
             // each thread reads up to RC_E listed vertices and consumes their
             // snapshots and list flags (nothing else reads them in this round)
             uint32_t o[RC_E], b[RC_E], len[RC_E];
@@ -917,15 +948,15 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
             for (int k = 0; k < RC_E; ++k) {
                 const uint64_t i = c0 + threadIdx.x * RC_E + k;
                 o[k] = b[k] = len[k] = 0;
-                if (i < end) {
-                    const uint32_t u = __ldg(list + i);
+                if (i < cend) {
+                    const uint32_t u = loc ? s_loc[i] : __ldg(list + i);
                     const uint32_t mu = SYNC ? *(volatile uint32_t *)rec_snap(d.rec + u, p_in)
                                              : *(volatile uint32_t *)(d.mval + u);
                     o[k] = acc_bit(d.acc, u) ? max(mu, u + 1) : mu;
                     b[k] = __ldg(d.rrowptr + u);
                     len[k] = __ldg(d.rrowptr + u + 1) - b[k];
                     if (SYNC) *rec_snap(d.rec + u, p_in) = 0;
-                    atomicAnd(rec_flags(d.rec + u), ~CB(p_in));
+                    atomicAnd(rec_flags(d.rec + u), ~CB(loc ? p_out : p_in));
                 }
             }
             uint32_t tot = 0;
@@ -998,6 +1029,7 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
                 }
             }
             __syncthreads(); // before the shared arrays are refilled
+            c0 += RC_ENTRIES;
         }
         stage_flush_block<3>(st, s_cnt, s_base, dst, ctr);
         if (lead && timed_out(vc)) vc->stop_req.v = 1;
