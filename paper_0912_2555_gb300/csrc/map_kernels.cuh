@@ -844,6 +844,7 @@ constexpr int RC_P = 1;                 // push pairs per thread and step
 #define MAPGPU_LC_PASSES 4 // asynchronous schedule: block-local passes over a block's own raised vertices per round
 #endif
 constexpr uint32_t LC_PASSES = MAPGPU_LC_PASSES;
+constexpr uint32_t LC_CAP = 1024; // entries recorded per block and round (the rest only go through the list)
 
 // The fix-point loop of one outer iteration: rounds 2, 3, ... until a round
 // changes nothing.  Round r reads list[(r-1) % 3] and appends to list[r % 3];
@@ -859,7 +860,7 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
     __shared__ uint32_t s_stage[8][3 * SB_ENTRIES];
     __shared__ uint32_t s_cnt[8][3], s_base[3];
     __shared__ uint32_t s_incl[RC_ENTRIES], s_o[RC_ENTRIES], s_b[RC_ENTRIES], s_scan[8];
-    __shared__ uint32_t s_loc[8 * SB_ENTRIES], s_lc[8]; // block-local continuation
+    __shared__ uint32_t s_loc[LC_CAP], s_ln; // vertices this block listed in this round
     __shared__ uint32_t *s_dst[3][2];
     __shared__ unsigned int *s_ctr[3];
     Ctl *ctl = d.ctl;
@@ -915,30 +916,26 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
         // every block takes an even contiguous share of the list
         const uint64_t per = (nl + gridDim.x - 1) / gridDim.x;
         const uint64_t beg = (uint64_t)blockIdx.x * per, end = min((uint64_t)nl, beg + per);
-        // asynchronous single graph: once its share of the list is done, the block goes on with
-        // the vertices it raised itself that are still in its staging buffers (up to LC_PASSES
-        // passes), so that values travel several edges per round without a grid barrier each
+        // asynchronous single graph: once its share of the list is done, the block pushes again
+        // the live values of the vertices it listed itself in this round (recorded in s_loc), up
+        // to LC_PASSES passes, so that values travel several edges per round.  These extra pushes
+        // touch no list flag: every listed vertex still goes through the list to the next round.
+        if (local) {
+            if (threadIdx.x == 0) s_ln = 0;
+            __syncthreads();
+        }
         uint64_t c0 = beg, cend = end;
-        bool loc = false; // chunk entries from s_loc (this block's raised vertices) instead of the list
-        uint32_t lpass = 0;
+        bool loc = false; // chunk entries from s_loc instead of the list
+        uint32_t lpass = 0, qend = 0;
         for (;;) {
             if (c0 >= cend) {
                 if (!local || lpass >= LC_PASSES) break;
-                const unsigned warp = threadIdx.x >> 5;
-                if (lane == 0) s_lc[warp] = st.cnt[1];
-                __syncthreads();
-                uint32_t off = 0, L = 0;
-                for (unsigned w = 0; w < 8; ++w) {
-                    off += w < warp ? s_lc[w] : 0u;
-                    L += s_lc[w];
-                }
-                for (uint32_t i = lane; i < st.cnt[1]; i += 32) s_loc[off + i] = st.buf[SB_ENTRIES + i];
-                st.cnt[1] = 0;
-                __syncthreads(); // s_loc complete; s_lc read by every thread
-                if (L == 0) break;
+                const uint32_t q = min(s_ln, (uint32_t)LC_CAP); // s_ln is final: a barrier ended the last chunk
+                if (q == qend) break;
                 loc = true;
-                c0 = 0;
-                cend = L;
+                c0 = qend;
+                cend = q;
+                qend = q;
                 ++lpass;
             }
             // each thread reads up to RC_E listed vertices and consumes their
@@ -956,7 +953,7 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
                     b[k] = __ldg(d.rrowptr + u);
                     len[k] = __ldg(d.rrowptr + u + 1) - b[k];
                     if (SYNC) *rec_snap(d.rec + u, p_in) = 0;
-                    atomicAnd(rec_flags(d.rec + u), ~CB(loc ? p_out : p_in));
+                    if (!loc) atomicAnd(rec_flags(d.rec + u), ~CB(p_in));
                 }
             }
             uint32_t tot = 0;
@@ -1023,6 +1020,10 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
                     }
                     stage_append<3>(st, 0, act[j] && !(fold[j] & FB(p_out)), w[j], dst, ctr);
                     stage_append<3>(st, 1, raised && !(cold[j] & CB(p_out)), w[j], dst, ctr);
+                    if (local && raised && !(cold[j] & CB(p_out))) { // listed here: push it again in this round
+                        const uint32_t q = atomicAdd(&s_ln, 1u);
+                        if (q < LC_CAP) s_loc[q] = w[j];
+                    }
                     stage_append<3>(st, 2, raised && mold[j] == 0, w[j], dst, ctr);
                     if (raised && mold[j] == 0 && d.stale) // the next dense round resets it
                         atomicOr(d.stale + (w[j] >> 5), 1u << (w[j] & 31u));
