@@ -65,6 +65,58 @@ bool is_device_ptr(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Control-block mirrors in page-locked host memory.  A device-to-host copy into
+// pageable memory goes through the driver's staging buffer and, measured with
+// several host threads each running a graph on its own stream, kept their runs
+// from overlapping; copies into page-locked memory do not.  Allocating
+// page-locked memory synchronises the device, so the slots come from chunks that
+// are allocated once (the first time they run out) and are never given back;
+// a freed slot goes to a free list.
+class PinnedSlots {
+  public:
+    static constexpr size_t SLOT = (sizeof(Ctl) + 255) & ~size_t(255);
+    static constexpr int PER_CHUNK = 32;
+    // a slot, or nullptr if page-locked memory cannot be had (the caller then uses pageable memory)
+    void *get()
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        if (free_.empty()) {
+            uint8_t *chunk = nullptr;
+            if (cudaHostAlloc((void **)&chunk, SLOT * PER_CHUNK, cudaHostAllocPortable) != cudaSuccess) {
+                cudaGetLastError();
+                return nullptr;
+            }
+            for (int i = PER_CHUNK - 1; i >= 0; --i) free_.push_back(chunk + SLOT * i);
+        }
+        void *p = free_.back();
+        free_.pop_back();
+        return p;
+    }
+    void put(void *p)
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        free_.push_back(p);
+    }
+    // make sure `k` slots can be handed out without allocating
+    void reserve(size_t k)
+    {
+        std::vector<void *> got;
+        for (size_t i = 0; i < k; ++i)
+            if (void *p = get()) got.push_back(p);
+        for (void *p : got) put(p);
+    }
+
+  private:
+    std::mutex mu_;
+    std::vector<void *> free_;
+};
+
+PinnedSlots &ctl_slots()
+{
+    static PinnedSlots *pool = new PinnedSlots; // process lifetime (page-locked chunks are kept to exit)
+    return *pool;
+}
+
 int pick_group(uint32_t n, uint64_t m)
 {
     const double avg = n ? (double)m / n : 0.0;
@@ -87,6 +139,7 @@ struct map_graph {
     int dense_grid = 0;  // blocks of the dense-round kernel
     int rounds_grid = 0; // blocks of the cooperative fix-point kernel (all resident)
     int check_grid = 0;  // blocks of the self-map / elimination kernel
+    int occ_dense = 1, occ_rounds = 1; // resident blocks per SM of the dense-round and fix-point kernels
     cudaStream_t stream = nullptr;
     uint32_t *rowptr = nullptr, *colidx = nullptr, *rrowptr = nullptr, *rcol = nullptr;
     uint32_t *rpos = nullptr; // positions in colidx of the reader entries
@@ -103,7 +156,8 @@ struct map_graph {
     uint32_t *hist = nullptr; // rounds per outer iteration
     uint32_t hist_cap = 0;
     Ctl *ctl = nullptr;
-    Ctl *h_ctl = nullptr;        // pinned mirror
+    Ctl *h_ctl = nullptr;        // mirror of ctl: a page-locked slot (ctl_slots) or pageable memory
+    bool h_ctl_pinned = false;
     uint32_t *h_stage = nullptr; // pinned n words for traces / host output
     uint32_t *h_hist = nullptr;  // pinned mirror of hist
     uint32_t nacc0 = 0;
@@ -141,7 +195,8 @@ void free_graph(map_graph *g)
     if (g->chist) cudaFreeAsync(g->chist, g->stream);
     free(g->h_cs);
     free(g->h_chist);
-    free(g->h_ctl);
+    if (g->h_ctl_pinned) ctl_slots().put(g->h_ctl);
+    else free(g->h_ctl);
     free(g->h_stage);
     free(g->h_hist);
     for (auto &e : g->ev)
@@ -451,6 +506,8 @@ int create_graph(uint32_t n, uint64_t m, cudaStream_t s, const char *who, Upload
         if (v >= 1 && v < occ_r) occ_r = v;
     }
     g->rounds_grid = (int)std::min<uint64_t>(((uint64_t)n + 255) / 256, (uint64_t)g->sms * occ_r);
+    g->occ_dense = occ;
+    g->occ_rounds = occ_r;
     g->check_grid = (int)std::min<uint64_t>(((uint64_t)n + 255) / 256, (uint64_t)g->sms * 4);
     g->hist_cap = 1u << 16;
 
@@ -478,8 +535,15 @@ int create_graph(uint32_t n, uint64_t m, cudaStream_t s, const char *who, Upload
         return fail(e == cudaErrorMemoryAllocation ? MAP_ERR_OOM : MAP_ERR_CUDA, "%s: %s: %s", who, what,
                     cudaGetErrorString(e));
     };
-    // host mirrors in pageable memory (pinning or unpinning would synchronise the device)
-    g->h_ctl = static_cast<Ctl *>(aligned_alloc(128, sizeof(Ctl)));
+    // the control-block mirror in a page-locked slot (see PinnedSlots); the larger mirrors, used by
+    // traces and per-iteration round counts only, in pageable memory (pinning or unpinning them
+    // per graph would synchronise the device)
+    if (void *slot = ctl_slots().get()) {
+        g->h_ctl = static_cast<Ctl *>(slot);
+        g->h_ctl_pinned = true;
+    } else {
+        g->h_ctl = static_cast<Ctl *>(aligned_alloc(128, sizeof(Ctl)));
+    }
     g->h_stage = static_cast<uint32_t *>(malloc((size_t)n * 4 + 16));
     g->h_hist = static_cast<uint32_t *>(malloc((size_t)g->hist_cap * 4));
     if (!g->h_ctl || !g->h_stage || !g->h_hist) {
@@ -1619,6 +1683,7 @@ struct map_server {
     size_t budget = 0;
     size_t used = 0;
     int device = 0;
+    uint32_t slots = 1;
     bool stop = false;
     uint64_t next_id = 1;
     std::mutex mu;
@@ -1690,6 +1755,13 @@ void server_worker(map_server *sv, cudaStream_t stream)
         }
         map_graph *g = nullptr;
         int rc = map_create(job->n, rp, ci, ab, stream, &g);
+        if (rc == MAP_OK && sv->slots > 1) {
+            // the fix-point kernel is a cooperative launch: with every resident slot of the device
+            // (the single-graph shape) a job's rounds cannot run beside another job's.  Each worker's
+            // job takes an even share of the slots, so the rounds of all workers fit side by side.
+            const int share = std::max(1, (int)((int64_t)g->sms * g->occ_rounds / (int64_t)sv->slots));
+            g->rounds_grid = std::min(g->rounds_grid, share);
+        }
         if (rc == MAP_OK) {
             // the whole run as one CUDA graph (building it costs well under a millisecond); the
             // map comes back by DMA into the staging buffer (map_create has consumed the inputs)
@@ -1737,6 +1809,8 @@ int map_server_create(size_t hbm_budget_bytes, uint32_t max_slots, map_server **
         hbm_budget_bytes = free_b / 2;
     }
     sv->budget = hbm_budget_bytes;
+    sv->slots = max_slots;
+    ctl_slots().reserve(2 * (size_t)max_slots); // control-block mirrors for the workers' graphs, allocated now
     // pinned staging for queued and finished jobs: a quarter of the device budget, at most 2 GiB
     sv->arena.init(std::min<size_t>(hbm_budget_bytes / 4, (size_t)2 << 30));
     for (uint32_t i = 0; i < max_slots; ++i) {

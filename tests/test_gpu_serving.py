@@ -1,6 +1,8 @@
 """Serving with continuous admission: jobs submitted over time while others run, admitted as
 workers and the memory budget free up; every job's result must be exactly its result alone
-(checked against the oracle), whatever else is in flight."""
+(checked against the oracle), whatever else is in flight.  With several workers each job's
+cooperative fix-point kernel runs on a share of the device, so these cases also cover the
+smaller launch shapes (4, 3 and 8 workers)."""
 import threading
 import time
 
@@ -37,8 +39,8 @@ def _jobs():
     return gs
 
 
-@pytest.mark.parametrize("slots,budget", [(4, 0), (3, 8 << 20)])
-def test_jobs_in_flight_get_their_own_results(pkg, slots, budget):
+@pytest.mark.parametrize("slots,budget,sched", [(4, 0, 0), (3, 8 << 20, 0), (8, 0, 1)])
+def test_jobs_in_flight_get_their_own_results(pkg, slots, budget, sched):
     gs = _jobs()
     want = [oracle.run_graph(g) for g in gs]
     ids = [None] * len(gs)
@@ -47,7 +49,7 @@ def test_jobs_in_flight_get_their_own_results(pkg, slots, budget):
             rng = np.random.default_rng(1)
             for i in rng.permutation(len(gs)):
                 g = gs[i]
-                ids[i] = sv.submit(g.n, g.rowptr, g.colidx if g.m else None, pkg.pack_bits(g.acc))
+                ids[i] = sv.submit(g.n, g.rowptr, g.colidx if g.m else None, pkg.pack_bits(g.acc), sched=sched)
                 time.sleep(float(rng.exponential(0.002)))
         th = threading.Thread(target=submitter)
         th.start()
@@ -61,8 +63,11 @@ def test_jobs_in_flight_get_their_own_results(pkg, slots, budget):
             time.sleep(0.001)
     assert all(r is not None for r in results)
     for g, w, (r, mp) in zip(gs, want, results):
-        assert (r.verdict, r.witness, r.outer, r.relaxations, r.inner_iters) == (
-            w.verdict, w.witness, w.outer, w.relaxations, w.inner_total), g.name
+        assert (r.verdict, r.witness, r.outer) == (w.verdict, w.witness, w.outer), g.name
+        if sched == 0:  # canonical counts; asynchronous sweeps are at most the rounds
+            assert (r.relaxations, r.inner_iters) == (w.relaxations, w.inner_total), g.name
+        else:
+            assert r.inner_iters <= w.inner_total, g.name
         assert np.array_equal(mp, w.map), g.name
 
 
