@@ -79,6 +79,19 @@ enum { MAP_SCHED_SYNC = 0, MAP_SCHED_ASYNC = 1 };
                                   fix-point would give), the outer count may be smaller, and the round
                                   counts are no longer canonical.  Single graphs only. */
 
+#define MAP_FLAG_FRONTIER_START 4u /* round 1 of every outer iteration without the dense round.  Round 1
+                                  (Section 2: one product over the whole matrix from "no value" everywhere)
+                                  gives row v the largest accepting vertex in it, so only the rows that hold
+                                  a currently accepting vertex get a value.  With this flag each accepting
+                                  vertex u pushes u to the rows that hold it (its readers) instead of every
+                                  row being streamed; later rounds are unchanged.  Every map vector, the
+                                  verdict, the witness, the outer count and, under MAP_SCHED_SYNC, the round
+                                  and relaxation counts are the same as without it (relaxations stay the
+                                  canonical counts of the pull schedule); under MAP_SCHED_ASYNC relaxations
+                                  count the pushes actually made.  It pays when the accepting set is small
+                                  against the edges.  Single graphs only (refused by map_batch_run and
+                                  map_run_static). */
+
 /* Called after the fix-point of every outer iteration, before the cycle test
  * and the elimination: map[v] is map(v) of that iteration (MAP_NONE if none),
  * host memory valid during the call only; rounds is that iteration's round

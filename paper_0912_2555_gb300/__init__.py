@@ -27,6 +27,7 @@ MAP_NO_CYCLE, MAP_CYCLE = 0, 1
 MAP_SCHED_SYNC, MAP_SCHED_ASYNC = 0, 1
 MAP_FLAG_PROFILE = 1
 MAP_FLAG_EARLY_EXIT = 2
+MAP_FLAG_FRONTIER_START = 4
 STATUS_NAMES = ["MAP_OK", "MAP_ERR_ARG", "MAP_ERR_CSR", "MAP_ERR_OOM", "MAP_ERR_CUDA", "MAP_ERR_TIMEOUT",
                 "MAP_ERR_LIMIT", "MAP_ERR_NOT_READY", "MAP_ERR_BUSY"]
 

@@ -169,10 +169,16 @@ struct map_graph {
     uint32_t *chist = nullptr;       // rounds per outer iteration, CH_CAP per graph
     mapk::CompState *h_cs = nullptr; // pinned mirrors
     uint32_t *h_chist = nullptr;
-    // the whole run as one CUDA graph, per schedule (built on first use)
-    cudaGraph_t graph[2] = {nullptr, nullptr};
-    cudaGraphExec_t exec[2] = {nullptr, nullptr};
-    mapk::Handles handles[2] = {};
+    // frontier start: the initially accepting vertices (built on first use), and whether the
+    // launches being issued use it
+    uint32_t *alist = nullptr;
+    uint32_t na = 0;
+    bool fstart_on = false;
+    // the whole run as one CUDA graph, per schedule and start (built on first use): index
+    // sched + 2 * frontier start
+    cudaGraph_t graph[4] = {};
+    cudaGraphExec_t exec[4] = {};
+    mapk::Handles handles[4] = {};
 };
 
 namespace {
@@ -180,12 +186,13 @@ namespace {
 void free_graph(map_graph *g)
 {
     if (!g) return;
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 4; ++i) {
         if (g->exec[i]) cudaGraphExecDestroy(g->exec[i]);
         if (g->graph[i]) cudaGraphDestroy(g->graph[i]);
     }
     void *dev[] = {g->rowptr, g->colidx, g->rrowptr, g->rcol,    g->rpos, g->elog, g->acc0, g->acc,
-                   g->mval,   g->list,   g->flist,   g->rec,     g->touched, g->xbuf, g->hist, g->ctl};
+                   g->mval,   g->list,   g->flist,   g->rec,     g->touched, g->xbuf, g->hist, g->ctl,
+                   g->alist};
     for (void *p : dev)
         if (p) cudaFreeAsync(p, g->stream); // stream-ordered: no device-wide synchronisation
     if (g->comp) cudaFreeAsync(g->comp, g->stream);
@@ -286,6 +293,8 @@ mapk::Dev dev_of(const map_graph *g)
     d.touched = g->touched;
     d.stale = g->comp ? nullptr : g->stale;
     d.ctl = g->ctl;
+    d.alist = g->fstart_on ? g->alist : nullptr;
+    d.na = g->fstart_on ? g->na : 0;
     d.comp = g->comp;
     d.cs = g->cs;
     d.chist = g->chist;
@@ -301,7 +310,7 @@ int launch_dense(map_graph *g, cudaStream_t s, mapk::Handles hd)
 }
 
 // the fix-point loop: one cooperative launch (its grid barrier needs every block resident)
-int launch_rounds(map_graph *g, cudaStream_t s, bool sync_sched)
+int launch_rounds(map_graph *g, cudaStream_t s, bool sync_sched, mapk::Handles hd)
 {
     const mapk::Dev d = dev_of(g);
     cudaLaunchConfig_t cfg = {};
@@ -314,8 +323,8 @@ int launch_rounds(map_graph *g, cudaStream_t s, bool sync_sched)
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (sync_sched) CK(cudaLaunchKernelEx(&cfg, mapk::k_rounds<true>, d));
-    else CK(cudaLaunchKernelEx(&cfg, mapk::k_rounds<false>, d));
+    if (sync_sched) CK(cudaLaunchKernelEx(&cfg, mapk::k_rounds<true>, d, hd));
+    else CK(cudaLaunchKernelEx(&cfg, mapk::k_rounds<false>, d, hd));
     return MAP_OK;
 }
 
@@ -372,7 +381,8 @@ int add_while(cudaStream_t cs, unsigned long long handle, cudaGraph_t *body)
 
 int build_run_graph(map_graph *g, int sched)
 {
-    if (g->exec[sched]) return MAP_OK;
+    const int slot = sched + (g->fstart_on ? 2 : 0);
+    if (g->exec[slot]) return MAP_OK;
     const bool sync_sched = sched == MAP_SCHED_SYNC;
     cudaStream_t cs;
     CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -397,7 +407,9 @@ int build_run_graph(map_graph *g, int sched)
     GK(cudaGraphConditionalHandleCreate(&hd.outer, top, 0, cudaGraphCondAssignDefault));
     // top level: reset, run_begin, outer WHILE, export
     GK(cudaStreamBeginCaptureToGraph(cs, top, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    if ((rc = launch_reset(g, cs)) == MAP_OK) {
+    if ((rc = launch_reset(g, cs)) == MAP_OK && g->fstart_on) // no dense round resets the values
+        rc = cudaMemsetAsync(g->mval, 0, (size_t)g->n * 4, cs) == cudaSuccess ? MAP_OK : fail(MAP_ERR_CUDA, "memset");
+    if (rc == MAP_OK) {
         mapk::k_run_begin<<<1, 32, 0, cs>>>(g->ctl, hd);
         if (g->comp) mapk::k_batch_begin<<<(g->ncomp + 255) / 256, 256, 0, cs>>>(dev_of(g));
         rc = add_while(cs, hd.outer, &outer_body);
@@ -410,10 +422,11 @@ int build_run_graph(map_graph *g, int sched)
         if (rc) return fin(rc);
         GK(e);
     }
-    // outer body: dense round, fix-point loop, self-map test + elimination
+    // outer body: dense round (or, with the frontier start, round 1 inside the fix-point
+    // kernel), fix-point loop, self-map test + elimination
     GK(cudaStreamBeginCaptureToGraph(cs, outer_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    rc = launch_dense(g, cs, hd);
-    if (rc == MAP_OK) rc = launch_rounds(g, cs, sync_sched);
+    rc = g->fstart_on ? MAP_OK : launch_dense(g, cs, hd);
+    if (rc == MAP_OK) rc = launch_rounds(g, cs, sync_sched, hd);
     if (rc == MAP_OK) rc = launch_check(g, cs, hd);
     {
         cudaGraph_t got = nullptr;
@@ -424,9 +437,9 @@ int build_run_graph(map_graph *g, int sched)
     cudaGraphExec_t exec = nullptr;
     GK(cudaGraphInstantiate(&exec, top, 0));
 #undef GK
-    g->graph[sched] = top;
-    g->exec[sched] = exec;
-    g->handles[sched] = hd;
+    g->graph[slot] = top;
+    g->exec[slot] = exec;
+    g->handles[slot] = hd;
     cudaStreamDestroy(cs);
     return MAP_OK;
 }
@@ -678,6 +691,15 @@ static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint
     // the CUDA-graph driver runs the whole loop on the device; per-iteration
     // traces and per-kernel timing need the host-stepped driver (same kernels)
     const bool stepped = opts.trace != nullptr || profile || force_stepped;
+    if ((opts.flags & MAP_FLAG_FRONTIER_START) && g->comp)
+        return fail(MAP_ERR_ARG, "map_batch_run: MAP_FLAG_FRONTIER_START is for single graphs");
+    // frontier start (round 1 pushed from the accepting vertices); with none accepting no
+    // iteration runs and the dense-round graph does as well
+    const bool fstart = (opts.flags & MAP_FLAG_FRONTIER_START) && g->nacc0 > 0;
+    struct FstartOff { // the flag only holds for the launches of this run
+        map_graph *g;
+        ~FstartOff() { g->fstart_on = false; }
+    } fstart_off{g};
     memset(res, 0, sizeof *res);
     cudaStream_t s = g->stream;
     const uint32_t n = g->n;
@@ -700,6 +722,16 @@ static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint
 
     int rc = MAP_OK;
     float dense_ms = 0.f, round_ms = 0.f, check_ms = 0.f;
+    if (fstart && !g->alist) { // the initially accepting vertices, listed once per graph
+        uint32_t *al = nullptr;
+        CK(cudaMallocAsync((void **)&al, ((size_t)g->nacc0 + 4) * 4, s));
+        CK(cudaMemsetAsync(al + g->nacc0, 0, 4, s));
+        mapk::k_acc_list<<<grid_for(g, g->n, 1), 256, 0, s>>>(g->n, g->acc0, al, g->nacc0, al + g->nacc0);
+        CK(cudaGetLastError());
+        g->alist = al;
+        g->na = g->nacc0;
+    }
+    g->fstart_on = fstart;
     if (g->dirty) { // the previous run stopped early: clear the round state it may have left
         CK(cudaMemsetAsync(g->rec, 0, (size_t)n * 16, s));
     }
@@ -709,7 +741,7 @@ static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint
         *g->h_ctl = init;
         CK(cudaEventRecord(g->ev[0], s));
         CK(cudaMemcpyAsync(g->ctl, g->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
-        CK(cudaGraphLaunch(g->exec[opts.sched], s));
+        CK(cudaGraphLaunch(g->exec[opts.sched + (fstart ? 2 : 0)], s));
         CK(cudaEventRecord(g->ev[1], s));
         if ((rc = read_ctl(g))) return rc;
         res->launches = 0; // filled below from the counts
@@ -719,23 +751,26 @@ static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint
         CK(cudaEventRecord(g->ev[0], s));
         CK(cudaMemcpyAsync(g->ctl, g->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
         if ((rc = launch_reset(g, s))) return rc;
+        if (fstart) CK(cudaMemsetAsync(g->mval, 0, (size_t)n * 4, s)); // no dense round resets the values
         mapk::k_run_begin<<<1, 32, 0, s>>>(g->ctl, none);
         if (g->comp) mapk::k_batch_begin<<<(g->ncomp + 255) / 256, 256, 0, s>>>(dev_of(g));
         CK(cudaGetLastError());
         if ((rc = read_ctl(g))) return rc;
         while (g->h_ctl->outer_go) {
-            if (profile) CK(cudaEventRecord(g->ev[2], s));
-            if ((rc = launch_dense(g, s, none))) return rc;
-            if (profile) CK(cudaEventRecord(g->ev[3], s));
-            if ((rc = read_ctl(g))) return rc;
-            if (profile) {
-                float ms = 0.f;
-                CK(cudaEventElapsedTime(&ms, g->ev[2], g->ev[3]));
-                dense_ms += ms;
-                res->dense_launches++;
+            if (!fstart) {
+                if (profile) CK(cudaEventRecord(g->ev[2], s));
+                if ((rc = launch_dense(g, s, none))) return rc;
+                if (profile) CK(cudaEventRecord(g->ev[3], s));
+                if ((rc = read_ctl(g))) return rc;
+                if (profile) {
+                    float ms = 0.f;
+                    CK(cudaEventElapsedTime(&ms, g->ev[2], g->ev[3]));
+                    dense_ms += ms;
+                    res->dense_launches++;
+                }
             }
             if (profile) CK(cudaEventRecord(g->ev[4], s));
-            if ((rc = launch_rounds(g, s, sync_sched))) return rc;
+            if ((rc = launch_rounds(g, s, sync_sched, none))) return rc;
             if (profile) CK(cudaEventRecord(g->ev[5], s));
             if ((rc = read_ctl(g))) return rc;
             if (profile) {
@@ -782,8 +817,9 @@ static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint
     res->frontier_rows = c.frontier_rows.v;
     res->check_ms = check_ms;
     res->accepting_left = c.nacc;
-    // kernel launches: run_begin, restore, export, and per outer iteration dense, rounds, check
-    res->launches = 3 + 3ull * c.outer;
+    // kernel launches: run_begin, restore, export, and per outer iteration dense (not with the
+    // frontier start), rounds, check
+    res->launches = 3 + (fstart ? 2ull : 3ull) * c.outer;
     const uint32_t nh = std::min<uint32_t>(c.outer, g->hist_cap);
     if (opts.rounds_out && nh) {
         CK(cudaMemcpyAsync(g->h_hist, g->hist, (size_t)nh * 4, cudaMemcpyDeviceToHost, s));
@@ -819,7 +855,7 @@ static void set_shapes(map_graph *g, uint32_t dense_bps, uint32_t rounds_bps)
         1, std::min<uint64_t>((ntiles + mapk::WT_WARPS - 1) / mapk::WT_WARPS, (uint64_t)g->sms * dense_bps));
     g->rounds_grid = (int)std::max<uint64_t>(
         1, std::min<uint64_t>(((uint64_t)g->n + 255) / 256, (uint64_t)g->sms * rounds_bps));
-    for (int i = 0; i < 2; ++i) { // the captured graphs hold the old shapes
+    for (int i = 0; i < 4; ++i) { // the captured graphs hold the old shapes
         if (g->exec[i]) cudaGraphExecDestroy(g->exec[i]);
         if (g->graph[i]) cudaGraphDestroy(g->graph[i]);
         g->exec[i] = nullptr;
@@ -1443,8 +1479,8 @@ extern "C" int map_run_static(uint32_t n, const uint32_t *rowptr, const uint32_t
     memset(&opts, 0, sizeof opts);
     if (opts_in) opts = *opts_in;
     if (opts.sched > MAP_SCHED_ASYNC) return fail(MAP_ERR_ARG, "map_run_static: unknown schedule %u", opts.sched);
-    if (opts.trace || (opts.flags & MAP_FLAG_PROFILE))
-        return fail(MAP_ERR_ARG, "map_run_static: traces and profiling are not offered here");
+    if (opts.trace || (opts.flags & (MAP_FLAG_PROFILE | MAP_FLAG_FRONTIER_START)))
+        return fail(MAP_ERR_ARG, "map_run_static: traces, profiling and the frontier start are not offered here");
     const bool sync_sched = opts.sched == MAP_SCHED_SYNC;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     memset(res, 0, sizeof *res);
@@ -1556,7 +1592,7 @@ extern "C" int map_run_static(uint32_t n, const uint32_t *rowptr, const uint32_t
     if ((rc = static_read_ctl(&h, ctl, s))) return rc;
     uint64_t launches = 1;
     while (h.outer_go) {
-        if ((rc = launch_dense(&g, s, none)) || (rc = launch_rounds(&g, s, sync_sched)) ||
+        if ((rc = launch_dense(&g, s, none)) || (rc = launch_rounds(&g, s, sync_sched, none)) ||
             (rc = launch_check(&g, s, none)))
             return rc;
         launches += 3;

@@ -92,7 +92,8 @@ struct Ctl {
     uint32_t use_graph;    // epilogues set the conditional handles
     uint32_t early_exit;   // stop the fix-point loop at the first self-mapped vertex
     uint32_t early_hit;    // it did (the run's round state is then left dirty)
-    uint32_t pad[3];
+    uint32_t tprev;        // |touched| of the previous outer iteration (frontier start resets their values)
+    uint32_t pad[2];
 };
 
 struct Handles {
@@ -139,6 +140,10 @@ struct Dev {
     uint32_t *touched;
     uint32_t *stale; // single graphs: bit v = mval[v] holds a value of an earlier outer iteration (NULL: batched)
     Ctl *ctl;
+    // frontier start (single graphs): the initially accepting vertices; round 1 is pushed from
+    // those still accepting instead of the dense round (NULL: the dense round runs)
+    const uint32_t *alist;
+    uint32_t na;
 };
 
 __device__ __forceinline__ uint32_t CB(uint32_t p) { return 1u << p; } // in list[p]
@@ -400,6 +405,7 @@ __device__ void epilogue_check(Ctl *c, Handles hd)
         v->outer = outer + 1;
         v->lcnt[0].v = v->lcnt[1].v = v->lcnt[2].v = 0;
         v->fcnt[0].v = v->fcnt[1].v = v->fcnt[2].v = 0;
+        v->tprev = v->tcnt.v;
         v->tcnt.v = 0;
         v->elim.v = 0;
         v->k = 0;
@@ -505,6 +511,7 @@ __global__ void k_run_begin(Ctl *c, Handles hd)
     v->lcnt[0].v = v->lcnt[1].v = v->lcnt[2].v = 0;
     v->fcnt[0].v = v->fcnt[1].v = v->fcnt[2].v = 0;
     v->tcnt.v = 0;
+    v->tprev = 0;
     v->frontier_rows.v = 0;
     v->bar_count.v = 0;
     v->stop_req.v = 0;
@@ -740,6 +747,25 @@ __device__ __forceinline__ void warp_append(bool flag, uint32_t w, uint32_t *arr
     if (flag) arr[base + __popc(mask & ((1u << lane) - 1u))] = w;
 }
 
+// The initially accepting vertices (v < n with bit v of acc0), for the frontier
+// start; at most cap entries are written (cap = their count).
+__global__ void k_acc_list(uint32_t n, const uint32_t *__restrict__ acc0, uint32_t *list, uint32_t cap,
+                           unsigned int *cnt)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += stride) {
+        const uint64_t v = base + lane_id(); // warp-uniform loop
+        const bool a = v < n && acc_bit(acc0, (uint32_t)v);
+        const unsigned mask = __ballot_sync(0xFFFFFFFFu, a);
+        if (!mask) continue;
+        const unsigned lane = lane_id(), leader = __ffs(mask) - 1;
+        unsigned at = 0;
+        if (lane == leader) at = atomicAdd(cnt, (unsigned)__popc(mask));
+        at = __shfl_sync(0xFFFFFFFFu, at, leader) + __popc(mask & ((1u << lane) - 1u));
+        if (a && at < cap) list[at] = (uint32_t)v;
+    }
+}
+
 // clear the frontier flag FB(p) of the rows in flist[p] and return their row lengths
 __device__ __forceinline__ unsigned long long clear_frontier(const uint32_t *__restrict__ flist, uint32_t nf,
                                                              uint32_t p, uint4 *rec,
@@ -855,7 +881,7 @@ constexpr uint32_t LC_CAP = 1024; // entries recorded per block and round (the r
 #endif
 
 template <bool SYNC>
-__global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const Dev d)
+__global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const Dev d, Handles hd)
 {
     __shared__ uint32_t s_stage[8][3 * SB_ENTRIES];
     __shared__ uint32_t s_cnt[8][3], s_base[3];
@@ -873,8 +899,25 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
     uint32_t nl = vc->lcnt[1].v; // vertices that got a value in the dense round
     uint32_t r = 1;              // rounds completed
     const bool early = vc->early_exit && !d.comp;
+    // Frontier start: no dense round ran.  Round 1 gives every row the largest accepting id in
+    // it; only the rows that hold a currently accepting vertex get one, so here each accepting
+    // vertex u pushes u + 1 to its readers (the same values, from far fewer edges when the
+    // accepting set is small).  This kernel is then the loop body's first: it resets the
+    // values of the previous outer iteration (exactly its touched vertices) before round 1.
+    const bool fstart = d.alist != nullptr;
+    if (fstart) {
+        default_stop(ctl, hd.outer);
+        const uint32_t tp = vc->tprev;
+        const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tp; i += nthreads)
+            d.mval[__ldg(d.touched + i)] = 0;
+        if (!grid_barrier(ctl)) status = ST_TIMEOUT; // every reset is visible before any push
+        nl = d.na;
+        r = 0;
+        if (SYNC && lead) relax += vc->m; // canonical count: round 1 of the pull schedule relaxes every row
+    }
     if (early && vc->self_seen.v != NONE) nl = 0; // the dense round already found a self-mapped vertex
-    if (nl && max_inner < 2) status = ST_LIMIT;
+    if (!fstart && nl && max_inner < 2) status = ST_LIMIT;
     // the frontier (rows reading a changed vertex) gives the canonical relaxation count of the
     // synchronous schedule; a single-graph asynchronous run counts its pushes instead
     const bool track = SYNC || d.comp;
@@ -886,7 +929,8 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
             vc->lcnt[p_free].v = 0;
             vc->fcnt[p_free].v = 0;
         }
-        const uint32_t *__restrict__ list = pick3(p_in, d.list);
+        const bool first = rr == 1; // round 1 from the accepting vertices (frontier start only)
+        const uint32_t *__restrict__ list = first ? d.alist : pick3(p_in, d.list);
         uint32_t *const list_out = pick3(p_out, d.list);
         uint32_t *const flist_out = pick3(p_out, d.flist);
         // appends: 0 = this round's frontier, 1 = changed vertices, 2 = newly touched vertices.
@@ -907,7 +951,9 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
         st.buf = s_stage[threadIdx.x >> 5];
         st.cnt[0] = st.cnt[1] = st.cnt[2] = 0;
         // the previous round's frontier: clear its flags, count its relaxations
-        if (track) relax += clear_frontier(pick3(p_in, d.flist), vc->fcnt[p_in].v, p_in, d.rec, d.rowptr, d);
+        if (track && !first) relax += clear_frontier(pick3(p_in, d.flist), vc->fcnt[p_in].v, p_in, d.rec, d.rowptr, d);
+        // round 1 of a frontier start keeps no frontier: its relaxations are the canonical m
+        const bool trk = track && !first;
 
         // chunks of RC_ENTRIES listed vertices per block (RC_E per thread, loaded
         // together); their (vertex, reader) pairs are spread evenly over the block's
@@ -947,13 +993,15 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
                 o[k] = b[k] = len[k] = 0;
                 if (i < cend) {
                     const uint32_t u = loc ? s_loc[i] : __ldg(list + i);
-                    const uint32_t mu = SYNC ? *(volatile uint32_t *)rec_snap(d.rec + u, p_in)
+                    const bool listed = !loc && !(first && SYNC); // in list[p_in], with a snapshot (SYNC)
+                    const uint32_t mu = SYNC ? (listed ? *(volatile uint32_t *)rec_snap(d.rec + u, p_in) : 0u)
                                              : *(volatile uint32_t *)(d.mval + u);
-                    o[k] = acc_bit(d.acc, u) ? max(mu, u + 1) : mu;
+                    const bool acc_u = acc_bit(d.acc, u);
+                    o[k] = acc_u ? max(mu, u + 1) : mu;
                     b[k] = __ldg(d.rrowptr + u);
-                    len[k] = __ldg(d.rrowptr + u + 1) - b[k];
-                    if (SYNC) *rec_snap(d.rec + u, p_in) = 0;
-                    if (!loc) atomicAnd(rec_flags(d.rec + u), ~CB(p_in));
+                    len[k] = (first && !loc && !acc_u) ? 0u : __ldg(d.rrowptr + u + 1) - b[k]; // eliminated: nothing new
+                    if (SYNC && listed) *rec_snap(d.rec + u, p_in) = 0;
+                    if (listed && !first) atomicAnd(rec_flags(d.rec + u), ~CB(p_in));
                 }
             }
             uint32_t tot = 0;
@@ -997,7 +1045,7 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
                     fold[j] = FB(p_out);
                     mold[j] = 0xFFFFFFFFu;
                     if (act[j]) {
-                        if (track) fold[j] = atomicOr(rec_flags(d.rec + w[j]), FB(p_out));
+                        if (trk) fold[j] = atomicOr(rec_flags(d.rec + w[j]), FB(p_out));
                         mold[j] = atomicMax(d.mval + w[j], ob[j]);
                     }
                 }
@@ -1039,7 +1087,7 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
             break;
         }
         r = rr;
-        frows += track ? vc->fcnt[p_out].v : nl; // frontier rows, or the vertices that pushed
+        if (!first) frows += track ? vc->fcnt[p_out].v : nl; // frontier rows, or the vertices that pushed
         nl = vc->lcnt[p_out].v;                  // changed in this round
         if (early && nl && vc->self_seen.v != NONE) { // stop here: the recorded vertex is the witness
             nl = 0;

@@ -62,10 +62,10 @@ def gpu_run(pkg, g, sched=0, on_device=False, keep_trace=True, hash_trace=None, 
     return r, final
 
 
-def assert_graph_path(pkg, g, want, sched, on_device, per_outer):
+def assert_graph_path(pkg, g, want, sched, on_device, per_outer, flags=0):
     """The CUDA-graph driver (no trace): same verdict, counts and final map; with per_outer,
     the map of every outer iteration k from a run stopped by max_outer = k."""
-    got, final = gpu_run(pkg, g, sched, on_device, keep_trace=False)
+    got, final = gpu_run(pkg, g, sched, on_device, keep_trace=False, flags=flags)
     assert got.status == pkg.MAP_OK
     assert (got.verdict, got.witness, got.outer) == (want.verdict, want.witness, want.outer)
     assert np.array_equal(final, want.map)
@@ -73,19 +73,20 @@ def assert_graph_path(pkg, g, want, sched, on_device, per_outer):
         assert (got.rounds, got.relaxations, got.inner_iters) == (want.rounds, want.relaxations, want.inner_total)
     if per_outer:
         for k in range(1, want.outer):
-            r, fk = gpu_run(pkg, g, sched, on_device, keep_trace=False, max_outer=k, allow_limit=True)
+            r, fk = gpu_run(pkg, g, sched, on_device, keep_trace=False, max_outer=k, allow_limit=True, flags=flags)
             assert r.status == pkg.MAP_ERR_LIMIT and r.outer == k
             tr = want.trace[k - 1][1]
             assert (fk == tr).all() if not isinstance(tr, str) else digest(fk) == tr
 
 
-def assert_parity(pkg, g, sched=0, on_device=False, hashed=False, per_outer=None, want=None):
+def assert_parity(pkg, g, sched=0, on_device=False, hashed=False, per_outer=None, want=None, flags=0):
     if want is None:
         want = oracle.run_graph(g, keep_trace=not hashed, hash_trace=digest if hashed else None)
     if per_outer is None:
         per_outer = g.n <= 5000 and want.outer <= 20
-    assert_graph_path(pkg, g, want, sched, on_device, per_outer)
-    got, final = gpu_run(pkg, g, sched, on_device, keep_trace=not hashed, hash_trace=digest if hashed else None)
+    assert_graph_path(pkg, g, want, sched, on_device, per_outer, flags)
+    got, final = gpu_run(pkg, g, sched, on_device, keep_trace=not hashed, hash_trace=digest if hashed else None,
+                         flags=flags)
     assert got.status == pkg.MAP_OK
     assert (got.verdict, got.witness, got.outer) == (want.verdict, want.witness, want.outer)
     assert np.array_equal(final, want.map)
@@ -227,6 +228,10 @@ def test_layered_64m_full_size(pkg):
     assert got.verdict == 0 and got.outer > 10
     # the asynchronous schedule (the benchmark's): same maps at every outer iteration, fewer sweeps
     assert_parity(pkg, g, 1, on_device=True, hashed=True, per_outer=False, want=want)
+    # round 1 pushed from the accepting vertices instead of the dense round, both schedules
+    for sched in (0, 1):
+        assert_parity(pkg, g, sched, on_device=True, hashed=True, per_outer=False, want=want,
+                      flags=pkg.MAP_FLAG_FRONTIER_START)
 
 
 @pytest.mark.parametrize("sched", [0, 1])
