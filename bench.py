@@ -345,6 +345,9 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="override vertex count (smaller runs, not the bench line)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched leg (256 graphs)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg (Poisson arrivals)")
+    ap.add_argument("--start", default="dense", choices=["dense", "frontier"],
+                    help="round 1 of every outer iteration: the dense round over the whole matrix (default, the "
+                         "headline) or MAP_FLAG_FRONTIER_START on every step (profiling that path; no dense roofline)")
     args = ap.parse_args()
 
     if args.impl == "reference":
@@ -380,8 +383,10 @@ def main():
     out = torch.empty(g.n, dtype=torch.int32, device="cuda")
     h = pkg.map_create(g.n, rp, ci, ab, stream)
 
+    start_flags = pkg.MAP_FLAG_FRONTIER_START if args.start == "frontier" else 0
+
     def step(flags=0):
-        return pkg.map_run(h, sched=args.sched, flags=flags, map_out=out)
+        return pkg.map_run(h, sched=args.sched, flags=flags | start_flags, map_out=out)
 
     for _ in range(max(args.warmup, 3)):
         r0 = step()
@@ -406,12 +411,12 @@ def main():
     # same maps, verdict and outer count; only the synchronous one has the canonical round counts)
     other = 1 - args.sched
     for _ in range(3):
-        pkg.map_run(h, sched=other, map_out=out)
+        pkg.map_run(h, sched=other, flags=start_flags, map_out=out)
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
     e0.record(stream)
-    ores = [pkg.map_run(h, sched=other, map_out=out) for _ in range(args.steps)]
+    ores = [pkg.map_run(h, sched=other, flags=start_flags, map_out=out) for _ in range(args.steps)]
     e1.record(stream)
     torch.cuda.synchronize()
     if ws > 1:
@@ -490,7 +495,7 @@ def main():
     def e2e_step():
         h2 = pkg.map_create(g.n, hp[0], hp[1], hp[2], stream)
         try:
-            return pkg.map_run(h2, sched=args.sched, map_out=hout)
+            return pkg.map_run(h2, sched=args.sched, flags=start_flags, map_out=hout)
         finally:
             pkg.map_destroy(h2)
 
@@ -511,7 +516,7 @@ def main():
             "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": dict(WORKLOAD, n=g.n, m=g.m, layers=layers, sched="sync" if args.sched == 0 else "async",
-                           outer_iters=r0.outer, rounds_per_run=sum(r0.rounds),
+                           start=args.start, outer_iters=r0.outer, rounds_per_run=sum(r0.rounds),
                            relaxations_per_run=r0.relaxations, verdict=r0.verdict,
                            l2="inputs larger than L2 (CSR 1.34 GB vs 129 MB L2); no flush",
                            parallelism="replicas" if ws > 1 else "single GPU"),

@@ -867,7 +867,10 @@ constexpr int RC_E = 1;                 // listed vertices per thread and chunk
 constexpr int RC_ENTRIES = 256 * RC_E;  // per block and chunk
 constexpr int RC_P = 1;                 // push pairs per thread and step
 #ifndef MAPGPU_LC_PASSES
-#define MAPGPU_LC_PASSES 4 // asynchronous schedule: block-local passes over a block's own raised vertices per round
+#define MAPGPU_LC_PASSES 1 // asynchronous schedule: block-local passes over a block's own raised vertices per round
+                           // (measured on the 2^26 layered graph, ms per run for 0 / 1 / 2 / 4 / 8 passes:
+                           // 18.2 / 17.0 / 17.2 / 17.4 / 17.5 with the dense start, 9.5 / 8.4 / 8.6 / 8.9 / 9.0
+                           // with the frontier start)
 #endif
 constexpr uint32_t LC_PASSES = MAPGPU_LC_PASSES;
 constexpr uint32_t LC_CAP = 1024; // entries recorded per block and round (the rest only go through the list)
@@ -1136,12 +1139,14 @@ __global__ void __launch_bounds__(256) k_check(const Dev d, Handles hd)
             const uint32_t bit = 1u << (u & 31u);
             if (*(volatile uint32_t *)(d.acc + (u >> 5)) & bit) {
                 const uint32_t old = atomicAnd(d.acc + (u >> 5), ~bit);
-                if (old & bit) { // this thread removed u: clear u's flag in the matrix entries, log u
+                if (old & bit) { // this thread removed u
                     elim++;
                     removed = 1;
-                    d.elog[atomicAdd(&ctl->ecnt.v, 1u)] = u;
-                    const uint32_t b = __ldg(d.rrowptr + u), e = __ldg(d.rrowptr + u + 1);
-                    for (uint32_t j = b; j < e; ++j) d.colidx_w[__ldg(d.rpos + j)] = u;
+                    if (!d.alist) { // the dense round reads the flag in the matrix entries: clear it, log u
+                        d.elog[atomicAdd(&ctl->ecnt.v, 1u)] = u;
+                        const uint32_t b = __ldg(d.rrowptr + u), e = __ldg(d.rrowptr + u + 1);
+                        for (uint32_t j = b; j < e; ++j) d.colidx_w[__ldg(d.rpos + j)] = u;
+                    }
                 }
             }
         }

@@ -162,6 +162,21 @@ def test_ragged_and_degenerate(pkg):
     assert_parity(pkg, mapgen.from_lists([[] for _ in range(100)], np.ones(100, np.uint8)), 0)
 
 
+def test_long_rows_among_short_ones(pkg):
+    """Rows of 254-257 and 510 entries next to short and empty ones, in full and ragged
+    128-row tiles of the dense round, with and without accepting targets in them."""
+    rng = np.random.default_rng(11)
+    for n in (300, 128 * 5 + 3):
+        lens = rng.integers(0, 6, size=n)
+        for v, L in zip(rng.choice(n, size=8, replace=False), (254, 255, 256, 257, 510, 255, 0, 1)):
+            lens[v] = L
+        rows = [[int(x) for x in rng.integers(0, n, size=int(L))] for L in lens]
+        acc = (rng.random(n) < 0.04).astype(np.uint8)
+        g = mapgen.from_lists(rows, acc)
+        assert_parity(pkg, g, 0)
+        assert_parity(pkg, g, 1)
+
+
 def test_layered_medium(pkg):
     g = mapgen.layered_graph(1 << 20, 62, seed=3)
     assert_parity(pkg, g, 0, on_device=True)
