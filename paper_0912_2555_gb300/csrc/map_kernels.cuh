@@ -557,7 +557,20 @@ constexpr int DT_THREADS = 256;
 constexpr int WT_WARPS = DT_THREADS / 32;
 constexpr int WT_ROWS = 128;
 constexpr int WT_UNROLL = 4;
+constexpr uint32_t WT_Q = 64; // queued accepting-target entries per warp (more are applied on the spot)
 constexpr size_t DT_SMEM = 0; // static shared memory only
+
+// the row of entry e in a tile: the last r < rows with rp[r] <= e (rp[0] <= e < rp[rows])
+__device__ __forceinline__ uint32_t tile_row_of(const uint32_t *rp, uint32_t rows, uint32_t e)
+{
+    uint32_t lo = 0, hi = rows;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (rp[mid] <= e) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
 
 #ifndef MAPGPU_DENSE_MIN_BLOCKS
 #define MAPGPU_DENSE_MIN_BLOCKS 6 // resident blocks per SM the register budget is sized for (measured best)
@@ -568,6 +581,9 @@ __global__ void __launch_bounds__(DT_THREADS, MAPGPU_DENSE_MIN_BLOCKS) k_dense(c
     // per warp, two buffers: the tile's rowptr slice [0, WT_ROWS], its stale words at WT_ROWS + 4
     __shared__ __align__(16) uint32_t s_rp[2][WT_WARPS][WT_ROWS + 8];
     __shared__ __align__(16) uint32_t s_best[WT_WARPS][WT_ROWS];
+    // entries of the tile whose target is accepting (position, offered value), queued while the
+    // span streams and applied afterwards with one lane per entry
+    __shared__ uint32_t s_qe[WT_WARPS][WT_Q], s_qv[WT_WARPS][WT_Q], s_qn[WT_WARPS];
     __shared__ uint32_t s_stage[WT_WARPS][SB_ENTRIES];
     __shared__ uint32_t s_cnt[WT_WARPS][1], s_base[1];
     Ctl *ctl = d.ctl;
@@ -589,6 +605,7 @@ __global__ void __launch_bounds__(DT_THREADS, MAPGPU_DENSE_MIN_BLOCKS) k_dense(c
     const bool sparse = d.stale && *(volatile uint32_t *)&ctl->outer > 1;
 #pragma unroll
     for (int k = 0; k < 4; ++k) best[lane * 4 + k] = 0;
+    if (lane == 0) s_qn[warp] = 0;
 
     // tile t into buffer b by asynchronous copies (nothing held in registers while in flight):
     // rowptr words r0 + 4 lane .. + 3 (lanes past the tile's last row copy nothing and fill
@@ -636,17 +653,25 @@ __global__ void __launch_bounds__(DT_THREADS, MAPGPU_DENSE_MIN_BLOCKS) k_dense(c
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const uint32_t e = ebase + k, c = cs4[k];
-                    if ((c >> 31) && e >= E0 && e < E1) { // the target is accepting
-                        uint32_t lo = 0, hi = rows; // rp[lo] <= e < rp[hi]: the row of e is the last such lo
-                        while (hi - lo > 1) {
-                            const uint32_t mid = (lo + hi) >> 1;
-                            if (rp[mid] <= e) lo = mid;
-                            else hi = mid;
+                    if ((c >> 31) && e >= E0 && e < E1) { // the target is accepting: queue the entry
+                        const uint32_t q = atomicAdd(&s_qn[warp], 1u);
+                        if (q < WT_Q) {
+                            s_qe[warp][q] = e;
+                            s_qv[warp][q] = (c & 0x7FFFFFFFu) + 1u;
+                        } else { // queue full: apply it here
+                            atomicMax(&best[tile_row_of(rp, rows, e)], (c & 0x7FFFFFFFu) + 1u);
                         }
-                        atomicMax(&best[lo], (c & 0x7FFFFFFFu) + 1u);
                     }
                 }
             }
+        }
+        __syncwarp();
+        { // the queued entries, one lane each: find the row, raise its best value
+            const uint32_t nq = min(s_qn[warp], WT_Q);
+            for (uint32_t i = lane; i < nq; i += 32)
+                atomicMax(&best[tile_row_of(rp, rows, s_qe[warp][i])], s_qv[warp][i]);
+            __syncwarp();
+            if (lane == 0) s_qn[warp] = 0;
         }
         __syncwarp();
         const uint4 b4 = reinterpret_cast<const uint4 *>(best)[lane];
