@@ -92,6 +92,10 @@ enum { MAP_SCHED_SYNC = 0, MAP_SCHED_ASYNC = 1 };
                                   against the edges.  Single graphs only (refused by map_batch_run and
                                   map_run_static). */
 
+#define MAP_FLAG_DENSE_START 8u /* the dense round, even on a handle that map_autotune set to the frontier
+                                   start (without either flag a handle starts the way map_autotune chose,
+                                   by default with the dense round).  Both start flags together: MAP_ERR_ARG. */
+
 /* Called after the fix-point of every outer iteration, before the cycle test
  * and the elimination: map[v] is map(v) of that iteration (MAP_NONE if none),
  * host memory valid during the call only; rounds is that iteration's round
@@ -241,8 +245,13 @@ MAP_API int map_server_destroy(map_server *sv);
  * measurement.  The dense-round kernel and the fix-point kernel are timed with
  * CUDA events on full runs of this very graph, at several numbers of resident
  * blocks per SM (up to each kernel's occupancy limit).  The fastest shape of
- * each is kept for later runs of the handle.  It takes about a dozen runs;
- * results are unaffected (only the launch shapes change).
+ * each is kept for later runs of the handle.  For a single graph it then times
+ * whole runs with the dense start and with the frontier start
+ * (MAP_FLAG_FRONTIER_START) and keeps the faster one as the handle's start
+ * (MAP_FLAG_DENSE_START / MAP_FLAG_FRONTIER_START still force either).  It
+ * takes about sixteen runs; results are unaffected (launch shapes and the start
+ * do not change any map vector, verdict, witness or outer count, nor the
+ * counts of the synchronous schedule).
  */
 typedef struct {
     uint32_t dense_blocks_per_sm;  /* chosen shape of the dense-round kernel */
@@ -250,7 +259,9 @@ typedef struct {
     double dense_ms;               /* its dense-round time per run at that shape */
     double rounds_ms;              /* its fix-point time per run at that shape */
     uint32_t trials;               /* runs made */
-    uint32_t reserved;
+    uint32_t frontier_start;       /* 1: the handle now starts with the frontier start (single graphs) */
+    double dense_start_ms;         /* run time with the dense start (0 for a batch) */
+    double frontier_start_ms;      /* run time with the frontier start (0 for a batch) */
 } map_tune_result;
 MAP_API int map_autotune(map_graph *g, uint32_t sched, map_tune_result *out);
 

@@ -28,6 +28,7 @@ MAP_SCHED_SYNC, MAP_SCHED_ASYNC = 0, 1
 MAP_FLAG_PROFILE = 1
 MAP_FLAG_EARLY_EXIT = 2
 MAP_FLAG_FRONTIER_START = 4
+MAP_FLAG_DENSE_START = 8
 STATUS_NAMES = ["MAP_OK", "MAP_ERR_ARG", "MAP_ERR_CSR", "MAP_ERR_OOM", "MAP_ERR_CUDA", "MAP_ERR_TIMEOUT",
                 "MAP_ERR_LIMIT", "MAP_ERR_NOT_READY", "MAP_ERR_BUSY"]
 
@@ -87,7 +88,9 @@ class TuneResult(ctypes.Structure):
         ("dense_ms", ctypes.c_double),
         ("rounds_ms", ctypes.c_double),
         ("trials", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32),
+        ("frontier_start", ctypes.c_uint32),
+        ("dense_start_ms", ctypes.c_double),
+        ("frontier_start_ms", ctypes.c_double),
     ]
 
 
@@ -99,7 +102,9 @@ def map_autotune(handle, sched: int = MAP_SCHED_SYNC) -> dict:
     if rc != MAP_OK:
         raise MapError(rc, "map_autotune", last_error())
     return {"dense_blocks_per_sm": t.dense_blocks_per_sm, "rounds_blocks_per_sm": t.rounds_blocks_per_sm,
-            "dense_ms": t.dense_ms, "rounds_ms": t.rounds_ms, "trials": t.trials}
+            "dense_ms": t.dense_ms, "rounds_ms": t.rounds_ms, "trials": t.trials,
+            "frontier_start": bool(t.frontier_start), "dense_start_ms": t.dense_start_ms,
+            "frontier_start_ms": t.frontier_start_ms}
 
 
 def map_lasso(handle, witness: int, init: int = MAP_NONE, cap: int = 1 << 20):

@@ -174,6 +174,7 @@ struct map_graph {
     uint32_t *alist = nullptr;
     uint32_t na = 0;
     bool fstart_on = false;
+    bool tuned_fstart = false; // map_autotune found the frontier start faster on this graph
     // the whole run as one CUDA graph, per schedule and start (built on first use): index
     // sched + 2 * frontier start
     cudaGraph_t graph[4] = {};
@@ -425,9 +426,9 @@ int build_run_graph(map_graph *g, int sched)
     // outer body: dense round (or, with the frontier start, round 1 inside the fix-point
     // kernel), fix-point loop, self-map test + elimination
     GK(cudaStreamBeginCaptureToGraph(cs, outer_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    // (in a graph the fix-point kernel ends with the self-map test and the elimination itself)
     rc = g->fstart_on ? MAP_OK : launch_dense(g, cs, hd);
     if (rc == MAP_OK) rc = launch_rounds(g, cs, sync_sched, hd);
-    if (rc == MAP_OK) rc = launch_check(g, cs, hd);
     {
         cudaGraph_t got = nullptr;
         cudaError_t e = cudaStreamEndCapture(cs, &got);
@@ -691,11 +692,16 @@ static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint
     // the CUDA-graph driver runs the whole loop on the device; per-iteration
     // traces and per-kernel timing need the host-stepped driver (same kernels)
     const bool stepped = opts.trace != nullptr || profile || force_stepped;
+    if ((opts.flags & MAP_FLAG_FRONTIER_START) && (opts.flags & MAP_FLAG_DENSE_START))
+        return fail(MAP_ERR_ARG, "map_run: MAP_FLAG_FRONTIER_START and MAP_FLAG_DENSE_START together");
     if ((opts.flags & MAP_FLAG_FRONTIER_START) && g->comp)
         return fail(MAP_ERR_ARG, "map_batch_run: MAP_FLAG_FRONTIER_START is for single graphs");
-    // frontier start (round 1 pushed from the accepting vertices); with none accepting no
-    // iteration runs and the dense-round graph does as well
-    const bool fstart = (opts.flags & MAP_FLAG_FRONTIER_START) && g->nacc0 > 0;
+    // frontier start (round 1 pushed from the accepting vertices): asked for, or chosen by
+    // map_autotune and not overridden; with none accepting no iteration runs and the
+    // dense-round graph does as well
+    const bool fstart = ((opts.flags & MAP_FLAG_FRONTIER_START) ||
+                         (g->tuned_fstart && !(opts.flags & MAP_FLAG_DENSE_START))) &&
+                        g->nacc0 > 0 && !g->comp;
     struct FstartOff { // the flag only holds for the launches of this run
         map_graph *g;
         ~FstartOff() { g->fstart_on = false; }
@@ -818,8 +824,8 @@ static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint
     res->check_ms = check_ms;
     res->accepting_left = c.nacc;
     // kernel launches: run_begin, restore, export, and per outer iteration dense (not with the
-    // frontier start), rounds, check
-    res->launches = 3 + (fstart ? 2ull : 3ull) * c.outer;
+    // frontier start), rounds and (stepped from the host) check
+    res->launches = 3 + ((fstart ? 1ull : 2ull) + (stepped ? 1ull : 0ull)) * c.outer;
     const uint32_t nh = std::min<uint32_t>(c.outer, g->hist_cap);
     if (opts.rounds_out && nh) {
         CK(cudaMemcpyAsync(g->h_hist, g->hist, (size_t)nh * 4, cudaMemcpyDeviceToHost, s));
@@ -877,7 +883,7 @@ int map_autotune(map_graph *g, uint32_t sched, map_tune_result *out)
     map_opts o;
     memset(&o, 0, sizeof o);
     o.sched = sched;
-    o.flags = MAP_FLAG_PROFILE; // host-stepped run, CUDA events around every phase
+    o.flags = MAP_FLAG_PROFILE | MAP_FLAG_DENSE_START; // host-stepped run, CUDA events around every phase
     map_result r;
     // the dense-round shape first (with the fix-point shape as it is), then the fix-point shape
     const uint32_t cands[] = {1, 2, 3, 4, 6, 8};
@@ -911,6 +917,28 @@ int map_autotune(map_graph *g, uint32_t sched, map_tune_result *out)
     out->rounds_blocks_per_sm = best_r;
     out->dense_ms = t_d;
     out->rounds_ms = t_r;
+    // the start of every outer iteration, with those shapes: whole runs as one graph launch each,
+    // the better of two per start
+    g->tuned_fstart = false;
+    if (!g->comp && g->nacc0) {
+        double t[2] = {1e30, 1e30};
+        for (int f = 0; f < 2; ++f) {
+            map_opts q;
+            memset(&q, 0, sizeof q);
+            q.sched = sched;
+            q.flags = f ? MAP_FLAG_FRONTIER_START : MAP_FLAG_DENSE_START;
+            for (int rep = 0; rep < 2; ++rep) {
+                const int rc = run_impl(g, &q, &r, nullptr);
+                if (rc != MAP_OK) return rc;
+                out->trials++;
+                t[f] = std::min(t[f], r.device_ms);
+            }
+        }
+        g->tuned_fstart = t[1] < t[0];
+        out->frontier_start = g->tuned_fstart ? 1u : 0u;
+        out->dense_start_ms = t[0];
+        out->frontier_start_ms = t[1];
+    }
     return MAP_OK;
 }
 

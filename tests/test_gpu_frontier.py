@@ -126,3 +126,33 @@ def test_refused_for_batches_and_static_runs(pkg):
     rc = lib.map_run_static(g.n, g.rowptr.ctypes.data, g.colidx.ctypes.data, pkg.pack_bits(g.acc).ctypes.data,
                             ctypes.byref(opts), ctypes.byref(res), None, None)
     assert rc == pkg.MAP_ERR_ARG
+
+
+@pytest.mark.parametrize("sched", [0, 1])
+def test_autotune_chooses_a_start(pkg, sched):
+    """map_autotune also times both starts and keeps the faster; every later run (the chosen
+    start, each start forced) still equals the oracle, and both start flags together are refused."""
+    for g in (mapgen.layered_graph(1 << 20, 62, seed=3), mapgen.random_graph(3001, 2, 6, 1.0, seed=77,
+                                                                              variant="plain")):
+        want = oracle.run_graph(g)
+        h = pkg.map_create(g.n, g.rowptr, g.colidx, pkg.pack_bits(g.acc))
+        try:
+            tune = pkg.map_autotune(h, sched)
+            assert tune["dense_start_ms"] > 0 and tune["frontier_start_ms"] > 0
+            assert tune["frontier_start"] == (tune["frontier_start_ms"] < tune["dense_start_ms"])
+            for flags in (0, pkg.MAP_FLAG_DENSE_START, _fs(pkg)):
+                out = np.empty(g.n, np.uint32)
+                r = pkg.map_run(h, sched=sched, flags=flags, map_out=out)
+                assert (r.verdict, r.witness, r.outer) == (want.verdict, want.witness, want.outer), flags
+                assert np.array_equal(out, want.map), flags
+                if sched == 0:
+                    assert (r.rounds, r.relaxations) == (want.rounds, want.relaxations), flags
+            p = pkg.map_run(h, sched=sched, flags=pkg.MAP_FLAG_PROFILE)
+            assert (p.dense_launches == 0) == tune["frontier_start"]
+            p = pkg.map_run(h, sched=sched, flags=pkg.MAP_FLAG_PROFILE | pkg.MAP_FLAG_DENSE_START)
+            assert p.dense_launches == p.outer
+            with pytest.raises(pkg.MapError) as e:
+                pkg.map_run(h, flags=_fs(pkg) | pkg.MAP_FLAG_DENSE_START)
+            assert e.value.code == pkg.MAP_ERR_ARG
+        finally:
+            pkg.map_destroy(h)
