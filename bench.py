@@ -71,21 +71,35 @@ def _peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling (SM clock, throttle reasons) during the timed region."""
+    """nvidia-smi sampling (SM clock, throttle reasons) every 50 ms.  The sampler starts before the
+    warm-up (it needs a moment to start); mark_start() / mark_end() bracket the timed region, and
+    summary() keeps the samples stamped inside it (the nearest one if the region is shorter than
+    the sampling interval)."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
+        self.t_start = self.t_end = None
+
+    def mark_start(self):
+        import datetime
+
+        self.t_start = datetime.datetime.now()
+
+    def mark_end(self):
+        import datetime
+
+        self.t_end = datetime.datetime.now()
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
         return self
@@ -102,22 +116,37 @@ class Clocks:
             self.lines = [line for line in out.splitlines() if line.strip()]
 
     def summary(self):
-        sm, smax, reasons = [], None, set()
+        import datetime
+
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []  # (time, sm MHz, max MHz, reasons)
         for line in getattr(self, "lines", []):
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
             try:
-                sm.append(float(f[1]))
-                smax = float(f[2])
+                t = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f")
+            except ValueError:
+                t = None  # an unexpected time format: no filtering by time
+            try:
+                rows.append((t, float(f[1]), float(f[2]), {nm for nm, val in zip(names, f[5:9])
+                                                          if val.lower().startswith("active")}))
             except ValueError:
                 continue
-            for nm, val in zip(names, f[5:9]):
-                if val.lower().startswith("active"):
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        window = "timed region"
+        sel = rows
+        if any(r[0] is None for r in rows):
+            window = "whole sampling (no time stamps)"
+        elif self.t_start is not None and self.t_end is not None and rows:
+            sel = [r for r in rows if self.t_start <= r[0] <= self.t_end]
+            if not sel:  # a region shorter than the interval: the sample nearest to it
+                mid = self.t_start + (self.t_end - self.t_start) / 2
+                sel = [min(rows, key=lambda r: abs((r[0] - mid).total_seconds()))]
+                window = "nearest sample"
+        reasons = set().union(*[r[3] for r in sel]) if sel else set()
+        return {"sm_mhz": statistics.median([r[1] for r in sel]) if sel else None,
+                "sm_max_mhz": sel[-1][2] if sel else None, "reasons": sorted(reasons), "samples": len(sel),
+                "window": window}
 
 
 def replica_value(ms, edges, device="cuda"):
@@ -388,20 +417,26 @@ def main():
     def step(flags=0):
         return pkg.map_run(h, sched=args.sched, flags=flags | start_flags, map_out=out)
 
-    for _ in range(max(args.warmup, 3)):
-        r0 = step()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
     results = []
     with Clocks(local) as clk:
+        # warm-up: at least W steps, and at least 0.4 s so that the clock sampler is running
+        t_w = time.perf_counter()
+        for _ in range(max(args.warmup, 3)):
+            r0 = step()
+        while time.perf_counter() - t_w < 0.4:
+            step()
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clk.mark_start()
         e0.record(stream)
         for _ in range(args.steps):
             results.append(step())
         e1.record(stream)
         torch.cuda.synchronize()
+        clk.mark_end()
     if ws > 1:
         dist.barrier()
     ms = e0.elapsed_time(e1)
@@ -499,24 +534,28 @@ def main():
         finally:
             pkg.map_destroy(h2)
 
-    if args.e2e_steps:
-        e2e_step()  # warm-up: the device memory pool grows to hold a second copy of the graph
     # each step timed on its own (host clock, device synchronised on both sides); the value is
     # taken at the median step, so that one step stalled on the host does not decide it, and
     # every step's time is reported with it
     e2e_ms, e2e_edges = [], 0
-    for _ in range(args.e2e_steps):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        e2e_edges = e2e_step().edges_total
-        torch.cuda.synchronize()
-        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    with Clocks(local) as e2e_clk:
+        if args.e2e_steps:
+            e2e_step()  # warm-up: the device memory pool grows to hold a second copy of the graph
+        e2e_clk.mark_start()
+        for _ in range(args.e2e_steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2e_edges = e2e_step().edges_total
+            torch.cuda.synchronize()
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        e2e_clk.mark_end()
     e2e = None
     if args.e2e_steps:
         med = float(np.median(e2e_ms))
         e2e = {"value": e2e_edges / (med / 1e3) / 1e9 * ws, "unit": "GTEPS",
                "h2d_bytes_per_step": 4 * (g.n + 1) + 4 * g.m + 4 * words, "d2h_bytes_per_step": 4 * g.n,
                "ms_per_step_median": med, "ms_per_step": e2e_ms, "value_from": "median step",
+               "clocks": e2e_clk.summary(),
                "includes": "map_create (H2D, validation, transpose) + map_run + map D2H + map_destroy"}
 
     line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
