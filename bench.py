@@ -257,7 +257,9 @@ def configs_leg(pkg, np, torch, stream, steps=10):
 def batched_leg(pkg, np, torch, stream, count=256, steps=2, sched=0):
     """256 graphs (sizes log-uniform in [1e3, 2e6], 40 % with a planted accepting cycle, layered
     recipe) in one batched run, against the same 256 graphs run one after another with map_run.
-    Inputs resident in HBM in both legs; device time by CUDA events; jobs/s = graphs / time."""
+    map_autotune picks the batch's launch shapes and its start (dense round or frontier start);
+    the one-by-one runs use the same start.  Inputs resident in HBM in both legs; device time
+    by CUDA events; jobs/s = graphs / time."""
     import mapgen
 
     sizes, planted, seeds = mapgen.batch_plan(count=count, lo=1000, hi=2_000_000, frac_cycle=0.4, seed=4)
@@ -272,8 +274,9 @@ def batched_leg(pkg, np, torch, stream, count=256, steps=2, sched=0):
         tune = pkg.map_autotune(hb, sched)  # launch shapes for this batch, by measurement
         t_tune = time.perf_counter() - t_tune
         res = pkg.map_batch_run(hb, count, sched=sched)  # warm-up (builds the graph)
+        sflags = pkg.MAP_FLAG_FRONTIER_START if tune["frontier_start"] else 0
         for h in singles:
-            pkg.map_run(h, sched=sched)
+            pkg.map_run(h, sched=sched, flags=sflags)
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(steps):
@@ -284,7 +287,7 @@ def batched_leg(pkg, np, torch, stream, count=256, steps=2, sched=0):
         e0.record(stream)
         seq = None
         for _ in range(steps):
-            seq = [pkg.map_run(h, sched=sched) for h in singles]
+            seq = [pkg.map_run(h, sched=sched, flags=sflags) for h in singles]
         e1.record(stream)
         torch.cuda.synchronize()
         seq_ms = e0.elapsed_time(e1) / steps
@@ -301,6 +304,7 @@ def batched_leg(pkg, np, torch, stream, count=256, steps=2, sched=0):
             "batch_ms": batch_ms, "sequential_ms": seq_ms,
             "jobs_per_s_batched": count / (batch_ms / 1e3), "jobs_per_s_sequential": count / (seq_ms / 1e3),
             "speedup": seq_ms / batch_ms, "gteps_batched": edges / (batch_ms / 1e3) / 1e9,
+            "start": "frontier" if tune["frontier_start"] else "dense",
             "results_identical": bool(same), "autotune": dict(tune, seconds=t_tune)}
 
 

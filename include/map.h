@@ -89,8 +89,8 @@ enum { MAP_SCHED_SYNC = 0, MAP_SCHED_ASYNC = 1 };
                                   and relaxation counts are the same as without it (relaxations stay the
                                   canonical counts of the pull schedule); under MAP_SCHED_ASYNC relaxations
                                   count the pushes actually made.  It pays when the accepting set is small
-                                  against the edges.  Single graphs only (refused by map_batch_run and
-                                  map_run_static). */
+                                  against the edges.  In a batch, a graph that has finished keeps its
+                                  last map vector as with the dense round.  Refused by map_run_static. */
 
 #define MAP_FLAG_DENSE_START 8u /* the dense round, even on a handle that map_autotune set to the frontier
                                    start (without either flag a handle starts the way map_autotune chose,
@@ -245,7 +245,7 @@ MAP_API int map_server_destroy(map_server *sv);
  * measurement.  The dense-round kernel and the fix-point kernel are timed with
  * CUDA events on full runs of this very graph, at several numbers of resident
  * blocks per SM (up to each kernel's occupancy limit).  The fastest shape of
- * each is kept for later runs of the handle.  For a single graph it then times
+ * each is kept for later runs of the handle.  It then times
  * whole runs with the dense start and with the frontier start
  * (MAP_FLAG_FRONTIER_START) and keeps the faster one as the handle's start
  * (MAP_FLAG_DENSE_START / MAP_FLAG_FRONTIER_START still force either).  It
@@ -259,9 +259,9 @@ typedef struct {
     double dense_ms;               /* its dense-round time per run at that shape */
     double rounds_ms;              /* its fix-point time per run at that shape */
     uint32_t trials;               /* runs made */
-    uint32_t frontier_start;       /* 1: the handle now starts with the frontier start (single graphs) */
-    double dense_start_ms;         /* run time with the dense start (0 for a batch) */
-    double frontier_start_ms;      /* run time with the frontier start (0 for a batch) */
+    uint32_t frontier_start;       /* 1: the handle now starts with the frontier start */
+    double dense_start_ms;         /* run time with the dense start */
+    double frontier_start_ms;      /* run time with the frontier start */
 } map_tune_result;
 MAP_API int map_autotune(map_graph *g, uint32_t sched, map_tune_result *out);
 

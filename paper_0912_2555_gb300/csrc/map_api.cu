@@ -694,14 +694,12 @@ static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint
     const bool stepped = opts.trace != nullptr || profile || force_stepped;
     if ((opts.flags & MAP_FLAG_FRONTIER_START) && (opts.flags & MAP_FLAG_DENSE_START))
         return fail(MAP_ERR_ARG, "map_run: MAP_FLAG_FRONTIER_START and MAP_FLAG_DENSE_START together");
-    if ((opts.flags & MAP_FLAG_FRONTIER_START) && g->comp)
-        return fail(MAP_ERR_ARG, "map_batch_run: MAP_FLAG_FRONTIER_START is for single graphs");
     // frontier start (round 1 pushed from the accepting vertices): asked for, or chosen by
     // map_autotune and not overridden; with none accepting no iteration runs and the
     // dense-round graph does as well
     const bool fstart = ((opts.flags & MAP_FLAG_FRONTIER_START) ||
                          (g->tuned_fstart && !(opts.flags & MAP_FLAG_DENSE_START))) &&
-                        g->nacc0 > 0 && !g->comp;
+                        g->nacc0 > 0;
     struct FstartOff { // the flag only holds for the launches of this run
         map_graph *g;
         ~FstartOff() { g->fstart_on = false; }
@@ -920,7 +918,7 @@ int map_autotune(map_graph *g, uint32_t sched, map_tune_result *out)
     // the start of every outer iteration, with those shapes: whole runs as one graph launch each,
     // the better of two per start
     g->tuned_fstart = false;
-    if (!g->comp && g->nacc0) {
+    if (g->nacc0) {
         double t[2] = {1e30, 1e30};
         for (int f = 0; f < 2; ++f) {
             map_opts q;

@@ -492,6 +492,7 @@ __device__ void epilogue_batch(const Dev &d, Handles hd)
             v->outer = v->outer + 1;
             v->lcnt[0].v = v->lcnt[1].v = v->lcnt[2].v = 0;
             v->fcnt[0].v = v->fcnt[1].v = v->fcnt[2].v = 0;
+            v->tprev = v->tcnt.v;
             v->tcnt.v = 0;
             v->elim.v = 0;
             v->k = 0;
@@ -999,8 +1000,11 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
         default_stop(ctl, hd.outer);
         const uint32_t tp = vc->tprev;
         const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
-        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tp; i += nthreads)
-            d.mval[__ldg(d.touched + i)] = 0;
+        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tp; i += nthreads) {
+            const uint32_t v = __ldg(d.touched + i);
+            // (batched: a graph that has finished keeps its last map vector)
+            if (!d.comp || *(volatile uint32_t *)&d.cs[__ldg(d.comp + v)].active) d.mval[v] = 0;
+        }
         if (!grid_barrier(ctl)) status = ST_TIMEOUT; // every reset is visible before any push
         nl = d.na;
         r = 0;
@@ -1089,7 +1093,10 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
                     const bool acc_u = acc_bit(d.acc, u);
                     o[k] = acc_u ? max(mu, u + 1) : mu;
                     b[k] = __ldg(d.rrowptr + u);
-                    len[k] = (first && !loc && !acc_u) ? 0u : __ldg(d.rrowptr + u + 1) - b[k]; // eliminated: nothing new
+                    // round 1: an eliminated vertex offers nothing new, nor does one of a finished graph
+                    const bool idle = first && !loc &&
+                                      (!acc_u || (d.comp && !*(volatile uint32_t *)&d.cs[__ldg(d.comp + u)].active));
+                    len[k] = idle ? 0u : __ldg(d.rrowptr + u + 1) - b[k];
                     if (SYNC && listed) *rec_snap(d.rec + u, p_in) = 0;
                     if (listed && !first) atomicAnd(rec_flags(d.rec + u), ~CB(p_in));
                 }

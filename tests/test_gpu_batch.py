@@ -1,6 +1,7 @@
 """Batched runs (many graphs in one launch): every graph must get exactly what it gets alone --
 verdict, witness (in its own ids), outer count, rounds of every outer iteration, relaxation
-count and final map vector -- checked against separate map_run calls and against the oracle."""
+count and final map vector -- checked against separate map_run calls and against the oracle,
+with the dense start and with the frontier start (MAP_FLAG_FRONTIER_START)."""
 import numpy as np
 import pytest
 
@@ -40,9 +41,11 @@ def _mixed_graphs():
     return gs
 
 
+@pytest.mark.parametrize("start", ["dense", "frontier"])
 @pytest.mark.parametrize("sched", [0, 1])
 @pytest.mark.parametrize("on_device", [False, True])
-def test_batch_equals_separate_runs_and_oracle(pkg, sched, on_device):
+def test_batch_equals_separate_runs_and_oracle(pkg, sched, on_device, start):
+    flags = pkg.MAP_FLAG_FRONTIER_START if start == "frontier" else 0
     gs = _mixed_graphs()
     dev = (lambda a: torch.from_numpy(a.view(np.int32)).cuda()) if on_device else (lambda a: a)
     items = [(g.n, dev(g.rowptr), dev(g.colidx if g.m else np.zeros(1, np.uint32)), dev(pkg.pack_bits(g.acc)))
@@ -51,8 +54,8 @@ def test_batch_equals_separate_runs_and_oracle(pkg, sched, on_device):
     h = pkg.map_batch_create(items)
     try:
         out = np.empty(total, np.uint32)
-        res = pkg.map_batch_run(h, len(gs), sched=sched, map_out=out)
-        res2 = pkg.map_batch_run(h, len(gs), sched=sched)  # runs repeat exactly
+        res = pkg.map_batch_run(h, len(gs), sched=sched, map_out=out, flags=flags)
+        res2 = pkg.map_batch_run(h, len(gs), sched=sched, flags=flags)  # runs repeat exactly
     finally:
         pkg.map_destroy(h)
     off = 0
@@ -79,12 +82,14 @@ def test_batch_of_layered_graphs_with_planted_cycles(pkg):
     h = pkg.map_batch_create([(g.n, g.rowptr, g.colidx, pkg.pack_bits(g.acc)) for g in gs])
     try:
         res = pkg.map_batch_run(h, len(gs))
+        resf = pkg.map_batch_run(h, len(gs), flags=pkg.MAP_FLAG_FRONTIER_START)
     finally:
         pkg.map_destroy(h)
-    for g, p, r in zip(gs, planted, res):
+    for g, p, r, rf in zip(gs, planted, res, resf):
         want = oracle.run_graph(g)
-        assert (r.verdict, r.witness, r.outer, r.rounds, r.relaxations) == (
-            want.verdict, want.witness, want.outer, want.rounds, want.relaxations)
+        for x in (r, rf):
+            assert (x.verdict, x.witness, x.outer, x.rounds, x.relaxations) == (
+                want.verdict, want.witness, want.outer, want.rounds, want.relaxations)
         assert r.verdict == int(p)
 
 

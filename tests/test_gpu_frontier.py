@@ -6,7 +6,8 @@ accepting vertex it holds and no other row gets anything.  The flag computes exa
 values from the accepting set, so everything the oracle fixes must match bit for bit: the map
 vector of every outer iteration, the verdict, the witness, the outer count and, on the
 synchronous schedule, the round and relaxation counts (relaxations stay the canonical counts
-of the pull schedule).  The full-size layered graph is checked in test_gpu_parity.py.
+of the pull schedule).  The full-size layered graph is checked in test_gpu_parity.py, batches
+in test_gpu_batch.py.
 """
 import numpy as np
 import pytest
@@ -109,15 +110,8 @@ def test_alternating_starts_on_one_handle(pkg):
             pkg.map_destroy(h)
 
 
-def test_refused_for_batches_and_static_runs(pkg):
+def test_refused_for_static_runs(pkg):
     g = mapgen.from_lists([[1], [0]], [1, 0])
-    h = pkg.map_batch_create([(g.n, g.rowptr, g.colidx, pkg.pack_bits(g.acc))] * 2)
-    try:
-        with pytest.raises(pkg.MapError) as e:
-            pkg.map_batch_run(h, 2, flags=_fs(pkg))
-        assert e.value.code == pkg.MAP_ERR_ARG
-    finally:
-        pkg.map_destroy(h)
     lib = pkg.load()
     import ctypes
     opts = pkg.MapOpts()
