@@ -39,8 +39,8 @@ METRIC = "MAP edge relaxations/s (GTEPS)"
 # DRAM traffic of one k_dense launch from the ncu capture summarised in
 # profiles/k_dense_layered-2p24.md (dram__bytes_read.sum + dram__bytes_write.sum of one sparse-write
 # launch on the 2^24-vertex case, whose algorithmic bytes are 339,748,616); valid only for the kernel source it was taken on
-# (a hash of the kernel file up to the end of the dense-round section).
-DENSE_TRAFFIC = {"kernel_file_sha256_16": "132397fe39ad87c2", "bytes": 350_473_728,
+# (a hash of the dense-round section of the kernel file, which holds k_dense and its helpers).
+DENSE_TRAFFIC = {"dense_section_sha256_16": "548c2d1b991c1821", "bytes": 350_473_728,
                  "algorithmic_bytes": 339_748_616, "case": "layered 2^24 vertices, m = 67,111,361, outer iteration 4"}
 
 
@@ -52,11 +52,11 @@ def _dense_traffic(dense_bytes):
         text = open(path, "rb").read()
     except OSError:
         return None, "kernel source not found"
-    # the kernel's source: the shared definitions and the dense-round section, i.e. the file up to
-    # the push-round section (later sections do not enter k_dense)
-    cut = text.find(b"// ------------------------------------------------------------ push rounds --")
-    sha = hashlib.sha256(text[:cut] if cut > 0 else text).hexdigest()[:16]
-    if sha != DENSE_TRAFFIC["kernel_file_sha256_16"]:
+    # the kernel's source: the dense-round section of the file (k_dense and its helpers)
+    a = text.find(b"// ------------------------------------------------------------ dense round --")
+    b = text.find(b"// ------------------------------------------------------------ push rounds --")
+    sha = hashlib.sha256(text[a:b] if 0 <= a < b else text).hexdigest()[:16]
+    if sha != DENSE_TRAFFIC["dense_section_sha256_16"]:
         return None, "kernel changed since the ncu capture"
     scale = dense_bytes / DENSE_TRAFFIC["algorithmic_bytes"]
     return DENSE_TRAFFIC["bytes"] * scale, (f"ncu capture on {DENSE_TRAFFIC['case']}, scaled by the ratio of "

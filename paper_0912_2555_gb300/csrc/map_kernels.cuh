@@ -739,68 +739,6 @@ __global__ void __launch_bounds__(DT_THREADS, MAPGPU_DENSE_MIN_BLOCKS) k_dense(c
     if (last_block(ctl)) epilogue_dense(ctl);
 }
 
-// ------------------------------------------------- self-map test, elimination --
-//
-// Over the touched vertices (exactly the vertices with a defined map value),
-// Section 2: witness = smallest v with map(v) = v; every map value u is removed
-// from the accepting set (exact count of removals).  The map vector is left
-// intact (the next dense round overwrites it).  Every thread of the grid calls
-// it (it ends with a last-block epilogue).  When the loop runs as a CUDA graph
-// it is the tail of the fix-point kernel; stepped from the host it is k_check.
-__device__ __forceinline__ void check_phase(const Dev &d, Handles hd, bool work = true)
-{
-    Ctl *ctl = d.ctl;
-    const uint32_t nt = work ? *(volatile uint32_t *)&ctl->tcnt.v : 0u; // without work: only the ticket
-    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
-    unsigned elim = 0;
-    uint32_t wit = NONE;
-    // warp-uniform loop (batched runs aggregate per graph within the warp)
-    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < nt; base += nthreads) {
-        const uint64_t i = base + lane_id();
-        uint32_t c = 0xFFFFFFFFu, removed = 0;
-        if (i < nt) {
-            const uint32_t v = __ldg(d.touched + i);
-            const uint32_t x = __ldg(d.mval + v);
-            const uint32_t u = x - 1; // x != 0 for a touched vertex (checked all the same below)
-            if (d.comp) c = __ldg(d.comp + v);
-            if (x != 0 && u == v) {
-                wit = min(wit, u);
-                if (d.comp) atomicMin(&d.cs[c].witness, u);
-            }
-            const uint32_t bit = 1u << (u & 31u);
-            if (x != 0 && (*(volatile uint32_t *)(d.acc + (u >> 5)) & bit)) {
-                const uint32_t old = atomicAnd(d.acc + (u >> 5), ~bit);
-                if (old & bit) { // this thread removed u
-                    elim++;
-                    removed = 1;
-                    if (!d.alist) { // the dense round reads the flag in the matrix entries: clear it, log u
-                        d.elog[atomicAdd(&ctl->ecnt.v, 1u)] = u;
-                        const uint32_t b = __ldg(d.rrowptr + u), e = __ldg(d.rrowptr + u + 1);
-                        for (uint32_t j = b; j < e; ++j) d.colidx_w[__ldg(d.rpos + j)] = u;
-                    }
-                }
-            }
-        }
-        if (d.comp) { // per graph: touched vertices and removals, one atomic per graph in the warp
-            const unsigned same = __match_any_sync(0xFFFFFFFFu, c);
-            const unsigned nt_c = __popc(same);
-            const unsigned ne_c = __reduce_add_sync(same, removed);
-            if (c != 0xFFFFFFFFu && lane_id() == (unsigned)(__ffs(same) - 1)) {
-                atomicAdd(&d.cs[c].touched, nt_c);
-                if (ne_c) atomicAdd(&d.cs[c].elim, ne_c);
-            }
-        }
-    }
-    block_add_min_u32(elim, wit, &ctl->elim.v, &ctl->witness.v);
-    if (!d.comp) {
-        if (last_block(ctl)) epilogue_check(ctl, hd);
-    } else if (last_block_all(ctl)) {
-        epilogue_batch(d, hd);
-    }
-}
-
-__global__ void __launch_bounds__(256) k_check(const Dev d, Handles hd) { check_phase(d, hd); }
-
 // ------------------------------------------------------------ push rounds --
 //
 // Round k + 1 >= 2.  In the synchronous schedule a row's new value is
@@ -970,6 +908,68 @@ constexpr uint32_t LC_CAP = 1024; // entries recorded per block and round (the r
 #ifndef MAPGPU_ROUNDS_MIN_BLOCKS
 #define MAPGPU_ROUNDS_MIN_BLOCKS 6 // resident blocks per SM the register budget is sized for (measured best)
 #endif
+
+// ------------------------------------------------- self-map test, elimination --
+//
+// Over the touched vertices (exactly the vertices with a defined map value),
+// Section 2: witness = smallest v with map(v) = v; every map value u is removed
+// from the accepting set (exact count of removals).  The map vector is left
+// intact (the next dense round overwrites it).  Every thread of the grid calls
+// it (it ends with a last-block epilogue).  When the loop runs as a CUDA graph
+// it is the tail of the fix-point kernel; stepped from the host it is k_check.
+__device__ __forceinline__ void check_phase(const Dev &d, Handles hd, bool work = true)
+{
+    Ctl *ctl = d.ctl;
+    const uint32_t nt = work ? *(volatile uint32_t *)&ctl->tcnt.v : 0u; // without work: only the ticket
+    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+    unsigned elim = 0;
+    uint32_t wit = NONE;
+    // warp-uniform loop (batched runs aggregate per graph within the warp)
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < nt; base += nthreads) {
+        const uint64_t i = base + lane_id();
+        uint32_t c = 0xFFFFFFFFu, removed = 0;
+        if (i < nt) {
+            const uint32_t v = __ldg(d.touched + i);
+            const uint32_t x = __ldg(d.mval + v);
+            const uint32_t u = x - 1; // x != 0 for a touched vertex (checked all the same below)
+            if (d.comp) c = __ldg(d.comp + v);
+            if (x != 0 && u == v) {
+                wit = min(wit, u);
+                if (d.comp) atomicMin(&d.cs[c].witness, u);
+            }
+            const uint32_t bit = 1u << (u & 31u);
+            if (x != 0 && (*(volatile uint32_t *)(d.acc + (u >> 5)) & bit)) {
+                const uint32_t old = atomicAnd(d.acc + (u >> 5), ~bit);
+                if (old & bit) { // this thread removed u
+                    elim++;
+                    removed = 1;
+                    if (!d.alist) { // the dense round reads the flag in the matrix entries: clear it, log u
+                        d.elog[atomicAdd(&ctl->ecnt.v, 1u)] = u;
+                        const uint32_t b = __ldg(d.rrowptr + u), e = __ldg(d.rrowptr + u + 1);
+                        for (uint32_t j = b; j < e; ++j) d.colidx_w[__ldg(d.rpos + j)] = u;
+                    }
+                }
+            }
+        }
+        if (d.comp) { // per graph: touched vertices and removals, one atomic per graph in the warp
+            const unsigned same = __match_any_sync(0xFFFFFFFFu, c);
+            const unsigned nt_c = __popc(same);
+            const unsigned ne_c = __reduce_add_sync(same, removed);
+            if (c != 0xFFFFFFFFu && lane_id() == (unsigned)(__ffs(same) - 1)) {
+                atomicAdd(&d.cs[c].touched, nt_c);
+                if (ne_c) atomicAdd(&d.cs[c].elim, ne_c);
+            }
+        }
+    }
+    block_add_min_u32(elim, wit, &ctl->elim.v, &ctl->witness.v);
+    if (!d.comp) {
+        if (last_block(ctl)) epilogue_check(ctl, hd);
+    } else if (last_block_all(ctl)) {
+        epilogue_batch(d, hd);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_check(const Dev d, Handles hd) { check_phase(d, hd); }
 
 template <bool SYNC>
 __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const Dev d, Handles hd)
