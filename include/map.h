@@ -162,12 +162,15 @@ MAP_API int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colid
 /*
  * map_run -- run MAP to its verdict (Section 2: propagate to the fix-point,
  * self-map test, eliminate, restart).
- *   opts     NULL for defaults (SYNC, no limits, no trace).
+ *   opts     NULL for defaults (SYNC, no limits, no trace, the dense start
+ *            unless map_autotune chose the frontier start for this handle).
  *   res      filled on MAP_OK and on MAP_ERR_LIMIT (with what was computed).
  *   map_out  optional, n entries, host or device memory: the map vector of the
  *            last outer iteration (all MAP_NONE when no vertex is accepting).
  * The graph is not changed: the accepting set is restored at every call, so
  * runs repeat exactly.  Blocks the calling thread until the result is known.
+ * Without a trace or MAP_FLAG_PROFILE the whole run is one CUDA-graph launch
+ * (its graph is built on the handle's first run with that schedule and start).
  */
 MAP_API int map_run(map_graph *g, const map_opts *opts, map_result *res, uint32_t *map_out);
 
@@ -180,8 +183,8 @@ MAP_API int map_destroy(map_graph *g);
  * are offset, which keeps its own order of accepting vertices), and one
  * CUDA-graph launch runs MAP on all of them at once: every outer iteration is
  * one outer iteration of each graph still running; a graph that has reached
- * its verdict is frozen (the dense round skips its rows).  Every graph gets
- * exactly the result it gets alone.
+ * its verdict is frozen (the dense round skips its rows, the frontier start
+ * leaves its values alone).  Every graph gets exactly the result it gets alone.
  *
  * map_batch_create -- count >= 1 graphs; graph c has ns[c] vertices, rowptrs[c]
  *   (ns[c] + 1 entries), colidxs[c] (its own ids, < ns[c]), acc_bits[c] (as for
