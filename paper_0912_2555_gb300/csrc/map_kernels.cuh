@@ -23,15 +23,20 @@
 //                            (synchronous rounds), and flags: CB(p) = "in list[p]",
 //                            FB(p) = "in flist[p]";
 //   touched[n]               vertices that got a value in this outer iteration;
+//   alist[|A0|]              the initially accepting vertices (frontier start only);
 //   Ctl                      the control block below (one per graph).
 //
 // One outer iteration: the dense round (every row, k_dense), then push rounds
 // until a round changes nothing (k_rounds, one persistent cooperative launch
 // with a grid barrier between rounds), then the self-map test and the
-// elimination over the touched vertices (k_check).  Every kernel that ends a
-// step of the loop finishes with a last-block epilogue (the last block to
-// retire, found with an atomic ticket) that updates the control block and, when
-// the loop runs as a CUDA graph, sets the graph's conditional WHILE handles.
+// elimination over the touched vertices (check_phase: the tail of k_rounds when
+// the loop runs as a CUDA graph, the kernel k_check when it is stepped from the
+// host).  With the frontier start there is no dense round: k_rounds resets the
+// previous iteration's values and pushes round 1 from the accepting vertices.
+// Every kernel that ends a step of the loop finishes with a last-block epilogue
+// (the last block to retire, found with an atomic ticket) that updates the
+// control block and, when the loop runs as a CUDA graph, sets the graph's
+// conditional WHILE handles.
 #pragma once
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
