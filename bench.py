@@ -195,7 +195,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GTEPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic", "config": dict(WORKLOAD, l2="inputs larger than L2 (1.34 GB CSR)"),
+            "data": "synthetic",
+            "config": dict(WORKLOAD, n=g.n, m=g.m, sched="sync", start="dense", parallelism="host, 1 thread",
+                           l2="inputs larger than L2 (1.34 GB CSR)"),
             "cpu_baseline": {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",
                              "sample": f"first {sample_outer} outer iterations of the same graph per step"},
             "e2e": {"value": v, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
