@@ -33,7 +33,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tmp = LIB + f".tmp{os.getpid()}"
     extra = os.environ.get("MAPGPU_NVCC_FLAGS", "").split()  # e.g. launch-shape experiments
     cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC,-fvisibility=hidden", *extra,
-           "-cudart", "static", "-Xlinker", "--exclude-libs,ALL", "-I", os.path.join(ROOT, "include"),
+           "-cudart", "static", "-Xlinker", "--exclude-libs,ALL", "-ldl", "-I", os.path.join(ROOT, "include"),
            "-o", tmp] + [os.path.join(CSRC, f) for f in SOURCES]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")

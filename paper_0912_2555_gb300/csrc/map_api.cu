@@ -23,6 +23,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "map.h"
 #include "map_kernels.cuh"
 
@@ -116,6 +118,15 @@ PinnedSlots &ctl_slots()
     static PinnedSlots *pool = new PinnedSlots; // process lifetime (page-locked chunks are kept to exit)
     return *pool;
 }
+
+// An NVTX range for profilers, popped when the scope ends (a no-op unless a tool is attached):
+// map_create, every map_run and served job, and each outer iteration of a host-stepped run.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 int pick_group(uint32_t n, uint64_t m)
 {
@@ -491,6 +502,7 @@ void keep_pool_memory()
 template <class Upload>
 int create_graph(uint32_t n, uint64_t m, cudaStream_t s, const char *who, Upload upload, map_graph **out)
 {
+    NvtxRange range(who);
     keep_pool_memory();
     map_graph *g = new (std::nothrow) map_graph;
     if (!g) return fail(MAP_ERR_OOM, "%s: host allocation failed", who);
@@ -697,6 +709,7 @@ static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint
     // frontier start (round 1 pushed from the accepting vertices): asked for, or chosen by
     // map_autotune and not overridden; with none accepting no iteration runs and the
     // dense-round graph does as well
+    NvtxRange range(stepped ? "map_run (stepped)" : "map_run");
     const bool fstart = ((opts.flags & MAP_FLAG_FRONTIER_START) ||
                          (g->tuned_fstart && !(opts.flags & MAP_FLAG_DENSE_START))) &&
                         g->nacc0 > 0;
@@ -761,6 +774,9 @@ static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint
         CK(cudaGetLastError());
         if ((rc = read_ctl(g))) return rc;
         while (g->h_ctl->outer_go) {
+            char label[32];
+            snprintf(label, sizeof label, "outer %u", g->h_ctl->outer);
+            NvtxRange outer_range(label);
             if (!fstart) {
                 if (profile) CK(cudaEventRecord(g->ev[2], s));
                 if ((rc = launch_dense(g, s, none))) return rc;
@@ -1815,6 +1831,7 @@ void server_worker(map_server *sv, cudaStream_t stream)
             memcpy(p, ab, job->acc.size() * 4);
             ab = p;
         }
+        NvtxRange job_range("served job");
         map_graph *g = nullptr;
         int rc = map_create(job->n, rp, ci, ab, stream, &g);
         if (rc == MAP_OK && sv->slots > 1) {
