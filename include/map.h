@@ -362,8 +362,9 @@ MAP_API int map_graph_info(const map_graph *g, uint32_t *n, uint64_t *m);
  *   larger graphs are rejected with MAP_ERR_ARG and a message naming the limit.
  *   rowptr, colidx, acc_bits, map_out: as for map_create / map_run, host or
  *   device memory; the inputs are copied into the array on every call.
- *   opts: as for map_run, except that traces and MAP_FLAG_PROFILE are refused
- *   (MAP_ERR_ARG); res: as for map_run (device_ms stays 0).
+ *   opts: as for map_run, except that traces, MAP_FLAG_PROFILE and
+ *   MAP_FLAG_FRONTIER_START are refused (MAP_ERR_ARG); res: as for map_run
+ *   (device_ms stays 0).
  *   cuda_stream: the stream all work is issued on; the call returns when the
  *   result is known.
  * The first call on a device looks the array's device address up
