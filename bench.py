@@ -36,10 +36,11 @@ WORKLOAD = dict(workload="layered-2^26v-4000L", n=1 << 26, layers=4000, seed=3, 
 METRIC = "MAP edge relaxations/s (GTEPS)"
 
 
-# DRAM traffic of one k_dense launch from the ncu capture summarised in
-# profiles/k_dense_layered-2p24.md (dram__bytes_read.sum + dram__bytes_write.sum of one sparse-write
-# launch on the 2^24-vertex case, whose algorithmic bytes are 339,748,616); valid only for the kernel source it was taken on
-# (a hash of the dense-round section of the kernel file, which holds k_dense and its helpers).
+# DRAM traffic of one k_dense launch, from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of a sparse-write launch (outer iteration 4) on the layered graph of
+# 2^24 vertices (1,000 layers, m = 67,111,361), whose algorithmic bytes are 339,748,616: 350.5 MB
+# of traffic, 1.03 x the algorithmic bytes.  Valid only for the kernel source it was taken on (a
+# hash of the dense-round section of the kernel file, which holds k_dense and its helpers).
 DENSE_TRAFFIC = {"dense_section_sha256_16": "548c2d1b991c1821", "bytes": 350_473_728,
                  "algorithmic_bytes": 339_748_616, "case": "layered 2^24 vertices, m = 67,111,361, outer iteration 4"}
 
@@ -172,6 +173,12 @@ def dist_init():
     return ws, rank, local
 
 
+def workload_config(g, layers=None):
+    """The workload both arms time: the graph recipe and its size (nothing measured)."""
+    return dict(WORKLOAD, n=g.n, m=g.m, layers=layers or WORKLOAD["layers"],
+                l2="inputs larger than L2 (CSR 1.34 GB vs 129 MB L2); no flush")
+
+
 def run_reference(args):
     """The oracle as it stands, on the host cores, each step a bounded sample of the workload."""
     ws, rank, _ = dist_init()
@@ -196,9 +203,9 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
-            "config": dict(WORKLOAD, n=g.n, m=g.m, sched="sync", start="dense", parallelism="host, 1 thread",
-                           l2="inputs larger than L2 (1.34 GB CSR)"),
-            "cpu_baseline": {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "config": workload_config(g),
+            "run": {"impl": "CPU oracle (synchronous rounds)", "placement": "host, 1 thread"},
+            "cpu_baseline": {"value": v, "unit": "GTEPS", "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"first {sample_outer} outer iterations of the same graph per step"},
             "e2e": {"value": v, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -212,15 +219,18 @@ def cpu_baseline(g, outer):
     t0 = time.perf_counter()
     r = oracle.run_graph(g, max_outer=outer)
     dt = time.perf_counter() - t0
-    return {"value": g.m * r.outer / dt / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+    return {"value": g.m * r.outer / dt / 1e9, "unit": "GTEPS", "cores": 1, "host_cores": os.cpu_count(),
+            "kind": "oracle",
             "sample": f"first {r.outer} outer iterations of the same graph ({dt:.1f} s, single thread, "
                       f"including the oracle's own set-up)"}
 
 
-def configs_leg(pkg, np, torch, stream, steps=10):
+def configs_leg(pkg, np, torch, stream, peak, steps=10):
     """The two other single-graph workloads, resident in HBM, both schedules: the 16,384-vertex
     random graph (both variants; latency-bound, reported in microseconds per run) and the
-    8 x 7 lock-step process product (2 x 7^8 vertices; GTEPS)."""
+    8 x 7 lock-step process product (2 x 7^8 vertices; GTEPS, and the run against the HBM roofline:
+    one minimal pass over the matrix per outer iteration -- rowptr 4(n + 1), colidx 4m and one
+    4-byte gather per edge -- over the run time)."""
     import mapgen
 
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -240,9 +250,13 @@ def configs_leg(pkg, np, torch, stream, steps=10):
                 e1.record(stream)
                 torch.cuda.synchronize()
                 ms = e0.elapsed_time(e1) / steps
+                alg = (4 * (g.n + 1) + 8 * g.m) * r.outer
                 out[name] = {"us_per_run": ms * 1e3, "gteps": g.m * r.outer / (ms / 1e3) / 1e9,
                              "verdict": r.verdict, "witness": r.witness, "outer": r.outer,
-                             "rounds": sum(r.rounds)}
+                             "rounds": sum(r.rounds), "relaxations": r.relaxations,
+                             "phases_ms": {"dense": r.dense_ms, "rounds": r.round_ms, "check": r.check_ms},
+                             "roofline": {"bytes_per_run": alg, "achieved_gbs": alg / (ms / 1e3) / 1e9,
+                                          "peak_gbs": peak, "frac": alg / (ms / 1e3) / 1e9 / peak}}
         finally:
             pkg.map_destroy(h)
         return out
@@ -471,8 +485,8 @@ def main():
 
     # round 1 pushed from the accepting vertices (MAP_FLAG_FRONTIER_START) instead of the dense
     # round: the same maps, verdict and outer count from far fewer edges when the accepting set is
-    # small.  Reported beside the headline, which streams the whole matrix every outer iteration
-    # as the paper's product does; value = the same m x outer / time, relaxations = pushes made.
+    # small.  Reported beside the headline as time and pushes per run: it does not examine every
+    # edge in every outer iteration, so m x outer / time would not be an edge rate.
     fs = pkg.MAP_FLAG_FRONTIER_START
     for _ in range(3):
         step(fs)
@@ -485,10 +499,12 @@ def main():
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
-    fvalue, fms, _ = replica_value(e0.elapsed_time(e1), sum(r.edges_total for r in fres), device="cuda")
+    fms = e0.elapsed_time(e1) / args.steps
     frontier_line = {"flag": "MAP_FLAG_FRONTIER_START", "sched": "sync" if args.sched == 0 else "async",
-                     "value": fvalue, "unit": "GTEPS", "ms_per_step": fms / args.steps,
-                     "relaxations_per_run": fres[0].relaxations, "rounds_per_run": sum(fres[0].rounds),
+                     "ms_per_run": fms, "headline_ms_per_run": ms / args.steps,
+                     "relaxations_per_run": fres[0].relaxations,
+                     "relaxations_are": "pushes made" if args.sched == 1 else "canonical count of the synchronous schedule",
+                     "sweeps_per_run": sum(fres[0].rounds),
                      "same_result": (fres[0].verdict, fres[0].witness, fres[0].outer) == (r0.verdict, r0.witness,
                                                                                           r0.outer)}
 
@@ -525,20 +541,41 @@ def main():
                     "achieved": run_dense_bytes / (run_ms / 1e3) / 1e9 if run_ms else None, "peak": peak,
                     "unit": "GB/s", "frac": run_dense_bytes / (run_ms / 1e3) / 1e9 / peak if run_ms else None,
                     "counted": "dense-round bytes only"}
-    phases = {"dense_ms_per_run": dense_ms / len(prof), "rounds_ms_per_run": sum(r.round_ms for r in prof) / len(prof),
-              "check_ms_per_run": sum(r.check_ms for r in prof) / len(prof),
-              "frontier_rows_per_run": prof[0].frontier_rows, "stepped_run_ms": prof[0].device_ms}
+    # the timed runs' own phases: the kernels stamp %globaltimer at the end of every dense round,
+    # fix-point loop and elimination (each phase runs from the end of the one before it)
+    k = len(results)
+    phases = {"dense_ms_per_run": sum(r.dense_ms for r in results) / k,
+              "rounds_ms_per_run": sum(r.round_ms for r in results) / k,
+              "check_ms_per_run": sum(r.check_ms for r in results) / k,
+              "frontier_rows_per_run": results[0].frontier_rows,
+              "source": "device %globaltimer stamps inside the timed graph runs",
+              "stepped_events": {"dense_ms_per_run": dense_ms / len(prof),
+                                 "rounds_ms_per_run": sum(r.round_ms for r in prof) / len(prof),
+                                 "check_ms_per_run": sum(r.check_ms for r in prof) / len(prof),
+                                 "run_ms": prof[0].device_ms,
+                                 "source": "CUDA events around each launch of 2 host-stepped runs"}}
 
     # end to end through the C ABI from pinned host buffers
     hp = [torch.from_numpy(x.view(np.int32)).pin_memory() for x in (g.rowptr, g.colidx, pkg.pack_bits(g.acc))]
     hout = torch.empty(g.n, dtype=torch.int32).pin_memory()
 
+    e2e_split = []  # host time of each call of each step (ms): create, run, destroy
+
     def e2e_step():
+        t0 = time.perf_counter()
         h2 = pkg.map_create(g.n, hp[0], hp[1], hp[2], stream)
+        t1 = time.perf_counter()
         try:
-            return pkg.map_run(h2, sched=args.sched, flags=start_flags, map_out=hout)
+            r = pkg.map_run(h2, sched=args.sched, flags=start_flags, map_out=hout)
         finally:
+            t2 = time.perf_counter()
             pkg.map_destroy(h2)
+            torch.cuda.synchronize()
+            t3 = time.perf_counter()
+            e2e_split.append({"map_create": (t1 - t0) * 1e3, "map_run": (t2 - t1) * 1e3, "map_destroy": (t3 - t2) * 1e3,
+                              "run_device_ms": None})
+        e2e_split[-1]["run_device_ms"] = r.device_ms
+        return r
 
     # each step timed on its own (host clock, device synchronised on both sides); the value is
     # taken at the median step, so that one step stalled on the host does not decide it, and
@@ -561,24 +598,24 @@ def main():
         e2e = {"value": e2e_edges / (med / 1e3) / 1e9 * ws, "unit": "GTEPS",
                "h2d_bytes_per_step": 4 * (g.n + 1) + 4 * g.m + 4 * words, "d2h_bytes_per_step": 4 * g.n,
                "ms_per_step_median": med, "ms_per_step": e2e_ms, "value_from": "median step",
+               "calls_ms": e2e_split[-args.e2e_steps:],
                "clocks": e2e_clk.summary(),
                "includes": "map_create (H2D, validation, transpose) + map_run + map D2H + map_destroy"}
 
     line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": dict(WORKLOAD, n=g.n, m=g.m, layers=layers, sched="sync" if args.sched == 0 else "async",
-                           start=args.start, outer_iters=r0.outer, rounds_per_run=sum(r0.rounds),
-                           relaxations_per_run=r0.relaxations, verdict=r0.verdict,
-                           l2="inputs larger than L2 (CSR 1.34 GB vs 129 MB L2); no flush",
-                           parallelism="replicas" if ws > 1 else "single GPU"),
+            "config": workload_config(g, layers),
+            "run": {"sched": "sync" if args.sched == 0 else "async", "start": args.start, "outer_iters": r0.outer,
+                    "rounds_per_run": sum(r0.rounds), "relaxations_per_run": r0.relaxations, "verdict": r0.verdict,
+                    "placement": "replicas, one per GPU" if ws > 1 else "single GPU"},
             "roofline": roofline, "run_roofline": run_roofline, "phases": phases, "e2e": e2e,
             "other_schedule": other_line, "frontier_start": frontier_line,
             "gpu_launches": sum(r.launches for r in results),
             "clocks": clk.summary()}
     pkg.map_destroy(h)
     if not args.no_batch and args.n is None and ws == 1:
-        line["configs"] = configs_leg(pkg, np, torch, stream)
+        line["configs"] = configs_leg(pkg, np, torch, stream, peak)
         line["batched"] = batched_leg(pkg, np, torch, stream, sched=0)  # canonical counts compared too
     if not args.no_serve and args.n is None and ws == 1:
         line["serving"] = serving_leg(pkg, np)

@@ -126,12 +126,15 @@ typedef struct {
                                  iteration plus one per push (batched ASYNC runs: frontier) */
     uint64_t edges_total;     /* m x outer_iters: the edges a fix-point must examine at least once */
     double device_ms;         /* stream time of the whole run (CUDA events) */
-    double dense_ms;          /* with MAP_FLAG_PROFILE: summed time of the dense-round kernel */
-    uint32_t dense_launches;  /* with MAP_FLAG_PROFILE: its launches */
+    double dense_ms;          /* time of the dense rounds summed over the run: CUDA events around each
+                                 launch with MAP_FLAG_PROFILE, else the kernels' own %globaltimer stamps
+                                 (each phase runs from the end of the one before it) */
+    uint32_t dense_launches;  /* dense-round launches */
     uint32_t accepting_left;  /* accepting vertices left at the end */
     uint64_t launches;        /* kernel launches issued by this run */
-    double round_ms;          /* with MAP_FLAG_PROFILE: summed time of the rounds after the first */
-    double check_ms;          /* with MAP_FLAG_PROFILE: summed time of the self-map test + elimination */
+    double round_ms;          /* time of the fix-point rounds after the dense round (with the frontier
+                                 start: all rounds), summed as dense_ms */
+    double check_ms;          /* time of the self-map tests and eliminations, summed as dense_ms */
     uint64_t frontier_rows;   /* frontier rows summed over the rounds after the first (single-
                                  graph ASYNC runs: the vertices that pushed) */
     uint32_t status;          /* map_status of this graph's run (batched runs report one per graph) */
@@ -348,35 +351,37 @@ MAP_API int map_graph_info(const map_graph *g, uint32_t *n, uint64_t *m);
  * map_run_static -- one MAP run on a small graph without allocating anything.
  *
  * (The paper has no counterpart: this entry point exists for callers that
- * cannot allocate device memory while they run -- code issuing work on a stream
- * that is being captured into a CUDA graph, where cudaMalloc is not allowed;
- * plug-ins whose host application owns the whole device budget; real-time
- * loops that must never enter an allocator.)
+ * cannot allocate device memory while they run -- plug-ins whose host
+ * application owns the whole device budget and hands out none of it, and
+ * real-time loops that must never enter an allocator.)
  *
  * Computes exactly what map_create + map_run + map_destroy compute on the same
  * arguments, with the same kernels, but every piece of work space lives in one
- * file-scope device array of MAP_STATIC_SCRATCH_BYTES (about 10 MiB) that each
- * GPU which loads this library holds until the process exits.  No cudaMalloc,
- * cudaFree, cudaMallocHost or other allocating call is made.
+ * file-scope device array of MAP_STATIC_SCRATCH_BYTES (about 10.3 MiB) that
+ * each GPU which loads this library holds until the process exits.  No
+ * cudaMalloc, cudaFree, cudaMallocHost or other allocating call is made.
  *   n <= MAP_STATIC_MAX_N vertices and m = rowptr[n] <= MAP_STATIC_MAX_M edges;
  *   larger graphs are rejected with MAP_ERR_ARG and a message naming the limit.
  *   rowptr, colidx, acc_bits, map_out: as for map_create / map_run, host or
  *   device memory; the inputs are copied into the array on every call.
- *   opts: as for map_run, except that traces, MAP_FLAG_PROFILE and
- *   MAP_FLAG_FRONTIER_START are refused (MAP_ERR_ARG); res: as for map_run
- *   (device_ms stays 0).
- *   cuda_stream: the stream all work is issued on; the call returns when the
- *   result is known.
- * The first call on a device looks the array's device address up
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  Every call on a device shares the one array and
- * overwrites what the previous call left there, so calls that overlap on the
- * GPU (from several host threads, or on several streams) race and must be
- * serialised by the caller.
+ *   opts: as for map_run (schedules, limits, timeout_ms, rounds_out for every
+ *   outer iteration, MAP_FLAG_EARLY_EXIT, MAP_FLAG_DENSE_START), except that
+ *   traces, MAP_FLAG_PROFILE and MAP_FLAG_FRONTIER_START are refused
+ *   (MAP_ERR_ARG); res: as for map_run, status included (device_ms stays 0).
+ *   cuda_stream: the stream all work is issued on.
+ * The call blocks: it waits for cuda_stream several times (it reads rowptr[0]
+ * and rowptr[n], then the control block after every step of the loop, into
+ * host memory), so it must not be issued on a stream that is being captured
+ * into a CUDA graph.  The first call on a device also looks the array's device
+ * address up (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture begins in the process.  Every call on a
+ * device shares the one array and overwrites what the previous call left
+ * there, so calls that overlap on the GPU (from several host threads, or on
+ * several streams) race and must be serialised by the caller.
  */
 #define MAP_STATIC_MAX_N 65536u
 #define MAP_STATIC_MAX_M 524288u
-#define MAP_STATIC_SCRATCH_BYTES 10532096u
+#define MAP_STATIC_SCRATCH_BYTES 10778112u
 MAP_API int map_run_static(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const uint32_t *acc_bits,
                            const map_opts *opts, map_result *res, uint32_t *map_out, void *cuda_stream);
 

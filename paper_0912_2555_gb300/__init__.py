@@ -332,18 +332,20 @@ def map_run(handle, sched: int = MAP_SCHED_SYNC, max_outer: int = 0, max_inner: 
 
 
 def map_run_static(n: int, rowptr, colidx, acc_bits, sched: int = MAP_SCHED_SYNC, max_outer: int = 0,
-                   max_inner: int = 0, map_out=None, stream=None, rounds_cap: int = 4096,
-                   allow_limit: bool = False) -> RunResult:
+                   max_inner: int = 0, flags: int = 0, map_out=None, stream=None, rounds_cap: int = 1 << 16,
+                   allow_limit: bool = False, timeout_ms: int = 0) -> RunResult:
     """One MAP run without any allocation (small graphs only; see include/map.h).
 
     For callers that cannot allocate device memory at run time; the library's work space is
-    one fixed device array shared by every call on a device, so calls must not overlap."""
+    one fixed device array shared by every call on a device, so calls must not overlap.  The
+    call blocks and must not be issued on a stream that is being captured."""
     lib = load()
     rp, k1 = _ptr(rowptr)
     ci, k2 = _ptr(colidx)
     ab, k3 = _ptr(acc_bits)
     opts = MapOpts()
-    opts.sched, opts.max_outer, opts.max_inner = sched, max_outer, max_inner
+    opts.sched, opts.max_outer, opts.max_inner, opts.flags = sched, max_outer, max_inner, flags
+    opts.timeout_ms = timeout_ms
     rounds = np.zeros(max(rounds_cap, 1), dtype=np.uint32)
     opts.rounds_out = rounds.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
     opts.rounds_cap = rounds_cap

@@ -186,11 +186,20 @@ struct map_graph {
     uint32_t na = 0;
     bool fstart_on = false;
     bool tuned_fstart = false; // map_autotune found the frontier start faster on this graph
-    // the whole run as one CUDA graph, per schedule and start (built on first use): index
-    // sched + 2 * frontier start
-    cudaGraph_t graph[4] = {};
-    cudaGraphExec_t exec[4] = {};
-    mapk::Handles handles[4] = {};
+    // worklist fix-point of the asynchronous schedule (single graphs; allocated on first use):
+    // the queue's cells, its counters, the in-queue bitmap; whether the launches being issued
+    // use it, and whether a drain stopped early (the queue must then be reset)
+    uint64_t *qcell = nullptr;
+    uint64_t qcap = 0;
+    mapk::QState *qs = nullptr;
+    uint32_t *inq = nullptr;
+    bool queue_on = false;
+    bool queue_engine = false; // asynchronous runs use the worklist (map_autotune may choose the rounds)
+    // the whole run as one CUDA graph, per schedule, start and engine (built on first use):
+    // index sched + 2 * frontier start + 4 * worklist
+    cudaGraph_t graph[8] = {};
+    cudaGraphExec_t exec[8] = {};
+    mapk::Handles handles[8] = {};
 };
 
 namespace {
@@ -198,13 +207,13 @@ namespace {
 void free_graph(map_graph *g)
 {
     if (!g) return;
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 8; ++i) {
         if (g->exec[i]) cudaGraphExecDestroy(g->exec[i]);
         if (g->graph[i]) cudaGraphDestroy(g->graph[i]);
     }
     void *dev[] = {g->rowptr, g->colidx, g->rrowptr, g->rcol,    g->rpos, g->elog, g->acc0, g->acc,
                    g->mval,   g->list,   g->flist,   g->rec,     g->touched, g->xbuf, g->hist, g->ctl,
-                   g->alist};
+                   g->alist,  g->qcell,  g->qs,      g->inq};
     for (void *p : dev)
         if (p) cudaFreeAsync(p, g->stream); // stream-ordered: no device-wide synchronisation
     if (g->comp) cudaFreeAsync(g->comp, g->stream);
@@ -307,6 +316,10 @@ mapk::Dev dev_of(const map_graph *g)
     d.ctl = g->ctl;
     d.alist = g->fstart_on ? g->alist : nullptr;
     d.na = g->fstart_on ? g->na : 0;
+    d.qcell = g->queue_on ? g->qcell : nullptr;
+    d.qcap = g->queue_on ? g->qcap : 0;
+    d.qs = g->queue_on ? g->qs : nullptr;
+    d.inq = g->queue_on ? g->inq : nullptr;
     d.comp = g->comp;
     d.cs = g->cs;
     d.chist = g->chist;
@@ -336,7 +349,30 @@ int launch_rounds(map_graph *g, cudaStream_t s, bool sync_sched, mapk::Handles h
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (sync_sched) CK(cudaLaunchKernelEx(&cfg, mapk::k_rounds<true>, d, hd));
+    else if (d.qcell) CK(cudaLaunchKernelEx(&cfg, mapk::k_queue, d, hd));
     else CK(cudaLaunchKernelEx(&cfg, mapk::k_rounds<false>, d, hd));
+    return MAP_OK;
+}
+
+// the worklist's queue: allocated on first use (cells for n vertices plus one per thread of the
+// largest fix-point grid, so that a producer never waits for its cell), and reset when new or
+// after a drain that stopped early
+int ensure_queue(map_graph *g, cudaStream_t s, bool reset)
+{
+    if (!g->qcell) {
+        const uint64_t cap = (uint64_t)g->n + (uint64_t)g->sms * 2048 + 64; // 2048: resident threads per SM
+        CK(cudaMallocAsync((void **)&g->qcell, cap * sizeof(uint64_t), s));
+        CK(cudaMallocAsync((void **)&g->qs, sizeof(mapk::QState), s));
+        CK(cudaMallocAsync((void **)&g->inq, ((size_t)g->words + 4) * 4, s));
+        g->qcap = cap;
+        reset = true;
+    }
+    if (reset) {
+        mapk::k_queue_init<<<grid_for(g, g->qcap, 1), 256, 0, s>>>(g->qcell, g->qcap);
+        CK(cudaGetLastError());
+        CK(cudaMemsetAsync(g->qs, 0, sizeof(mapk::QState), s));
+        CK(cudaMemsetAsync(g->inq, 0, ((size_t)g->words + 4) * 4, s));
+    }
     return MAP_OK;
 }
 
@@ -393,7 +429,7 @@ int add_while(cudaStream_t cs, unsigned long long handle, cudaGraph_t *body)
 
 int build_run_graph(map_graph *g, int sched)
 {
-    const int slot = sched + (g->fstart_on ? 2 : 0);
+    const int slot = sched + (g->fstart_on ? 2 : 0) + (g->queue_on ? 4 : 0);
     if (g->exec[slot]) return MAP_OK;
     const bool sync_sched = sched == MAP_SCHED_SYNC;
     cudaStream_t cs;
@@ -521,10 +557,11 @@ int create_graph(uint32_t n, uint64_t m, cudaStream_t s, const char *who, Upload
     if (occ <= 0) occ = 1;
     const uint64_t ntiles = ((uint64_t)n + mapk::WT_ROWS - 1) / mapk::WT_ROWS;
     g->dense_grid = (int)std::min<uint64_t>((ntiles + mapk::WT_WARPS - 1) / mapk::WT_WARPS, (uint64_t)g->sms * occ);
-    int occ_r = 0, occ_a = 0;
+    int occ_r = 0, occ_a = 0, occ_q = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_r, mapk::k_rounds<true>, 256, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, mapk::k_rounds<false>, 256, 0);
-    occ_r = std::max(1, std::min(occ_r, occ_a));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_q, mapk::k_queue, 256, 0);
+    occ_r = std::max(1, std::min(occ_r, std::min(occ_a, occ_q)));
     // launch shape of the fix-point kernel: MAPGPU_ROUNDS_BLOCKS_PER_SM (1 .. the occupancy
     // limit) overrides the default of every resident slot
     if (const char *e = getenv("MAPGPU_ROUNDS_BLOCKS_PER_SM")) {
@@ -713,9 +750,16 @@ static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint
     const bool fstart = ((opts.flags & MAP_FLAG_FRONTIER_START) ||
                          (g->tuned_fstart && !(opts.flags & MAP_FLAG_DENSE_START))) &&
                         g->nacc0 > 0;
-    struct FstartOff { // the flag only holds for the launches of this run
+    // the worklist fix-point for the asynchronous schedule of a single graph (unless map_autotune
+    // chose the rounds for this handle); a limit of one round per outer iteration needs the rounds
+    const bool queue = !sync_sched && !g->comp && g->queue_engine && (opts.max_inner == 0 || opts.max_inner >= 2);
+    struct FstartOff { // the flags only hold for the launches of this run
         map_graph *g;
-        ~FstartOff() { g->fstart_on = false; }
+        ~FstartOff()
+        {
+            g->fstart_on = false;
+            g->queue_on = false;
+        }
     } fstart_off{g};
     memset(res, 0, sizeof *res);
     cudaStream_t s = g->stream;
@@ -752,13 +796,15 @@ static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint
     if (g->dirty) { // the previous run stopped early: clear the round state it may have left
         CK(cudaMemsetAsync(g->rec, 0, (size_t)n * 16, s));
     }
+    if ((queue || (g->dirty && g->qcell)) && (rc = ensure_queue(g, s, g->dirty))) return rc;
+    g->queue_on = queue;
     g->dirty = true; // until this run completes normally
     if (!stepped) {
         if ((rc = build_run_graph(g, opts.sched))) return rc;
         *g->h_ctl = init;
         CK(cudaEventRecord(g->ev[0], s));
         CK(cudaMemcpyAsync(g->ctl, g->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
-        CK(cudaGraphLaunch(g->exec[opts.sched + (fstart ? 2 : 0)], s));
+        CK(cudaGraphLaunch(g->exec[opts.sched + (fstart ? 2 : 0) + (queue ? 4 : 0)], s));
         CK(cudaEventRecord(g->ev[1], s));
         if ((rc = read_ctl(g))) return rc;
         res->launches = 0; // filled below from the counts
@@ -832,6 +878,12 @@ static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint
     res->relaxations = c.relax.v;
     res->edges_total = g->m * (uint64_t)c.outer;
     res->device_ms = total_ms;
+    if (!profile) { // the kernels' own %globaltimer stamps of each phase
+        dense_ms = (float)(c.ph_dense * 1e-6);
+        round_ms = (float)(c.ph_rounds * 1e-6);
+        check_ms = (float)(c.ph_check * 1e-6);
+        res->dense_launches = fstart ? 0u : c.outer;
+    }
     res->dense_ms = dense_ms;
     res->round_ms = round_ms;
     res->frontier_rows = c.frontier_rows.v;
@@ -875,7 +927,7 @@ static void set_shapes(map_graph *g, uint32_t dense_bps, uint32_t rounds_bps)
         1, std::min<uint64_t>((ntiles + mapk::WT_WARPS - 1) / mapk::WT_WARPS, (uint64_t)g->sms * dense_bps));
     g->rounds_grid = (int)std::max<uint64_t>(
         1, std::min<uint64_t>(((uint64_t)g->n + 255) / 256, (uint64_t)g->sms * rounds_bps));
-    for (int i = 0; i < 4; ++i) { // the captured graphs hold the old shapes
+    for (int i = 0; i < 8; ++i) { // the captured graphs hold the old shapes
         if (g->exec[i]) cudaGraphExecDestroy(g->exec[i]);
         if (g->graph[i]) cudaGraphDestroy(g->graph[i]);
         g->exec[i] = nullptr;
@@ -890,9 +942,11 @@ int map_autotune(map_graph *g, uint32_t sched, map_tune_result *out)
     if (sched > MAP_SCHED_ASYNC) return fail(MAP_ERR_ARG, "map_autotune: unknown schedule %u", sched);
     int occ_d = 0, occ_r = 0, occ_a = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_d, mapk::k_dense, mapk::DT_THREADS, mapk::DT_SMEM));
+    int occ_q = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_r, mapk::k_rounds<true>, 256, 0));
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, mapk::k_rounds<false>, 256, 0));
-    occ_r = std::min(occ_r, occ_a);
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_q, mapk::k_queue, 256, 0));
+    occ_r = std::min(occ_r, std::min(occ_a, occ_q));
     memset(out, 0, sizeof *out);
     map_opts o;
     memset(&o, 0, sizeof o);
@@ -1416,15 +1470,17 @@ int map_batch_run(map_graph *g, const map_opts *opts, map_result *results, uint3
 // ============================================================================
 // map_run_static: a whole MAP run that allocates nothing.
 //
-// Some callers cannot allocate device memory at run time: code that runs while
-// its stream is being captured into a CUDA graph (cudaMalloc is not allowed
-// during capture), host applications that hand a fixed device budget to their
-// plug-ins and own every allocation themselves, and real-time loops that must
-// not call into the allocator.  For graphs up to MAP_STATIC_MAX_N vertices and
-// MAP_STATIC_MAX_M edges, map_run_static keeps all of its work space in the
-// file-scope device array below, which every GPU that loads this library holds
-// until the process exits, and it calls no cudaMalloc, cudaFree or allocating
-// routine.  It runs the same kernels as map_run, stepped from the host.
+// Some callers cannot allocate device memory at run time: plug-ins whose host
+// application hands them a fixed device budget and owns every allocation,
+// real-time loops that must never enter an allocator, and code running where
+// the allocator is off limits for other reasons.  For graphs up to
+// MAP_STATIC_MAX_N vertices and MAP_STATIC_MAX_M edges, map_run_static keeps
+// all of its work space in the file-scope device array below, which every GPU
+// that loads this library holds until the process exits, and it calls no
+// cudaMalloc, cudaFree or allocating routine.  It runs the same kernels as
+// map_run, stepped from the host: it waits for its stream several times per
+// call (to read the CSR's end offsets and the control block between steps), so
+// it blocks, and it cannot be issued on a stream that is being captured.
 // ============================================================================
 
 namespace {
@@ -1432,7 +1488,7 @@ namespace {
 constexpr uint64_t ST_MAX_N = MAP_STATIC_MAX_N;
 constexpr uint64_t ST_MAX_M = MAP_STATIC_MAX_M;
 constexpr uint64_t ST_MAX_W = (ST_MAX_N + 31) / 32;
-constexpr uint64_t ST_HIST = 4096;
+constexpr uint64_t ST_HIST = ST_MAX_N; // rounds per outer iteration: a run has at most n outer iterations
 constexpr uint64_t st_pad(uint64_t words) { return (words + 63) & ~uint64_t(63); } // 256-byte pieces
 // word offsets of the pieces of the scratch array
 constexpr uint64_t ST_CTL = 0;
@@ -1508,10 +1564,9 @@ int static_read_ctl(Ctl *h, const Ctl *d, cudaStream_t s)
 
 } // namespace
 
-extern "C" int map_run_static(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const uint32_t *acc_bits,
-                              const map_opts *opts_in, map_result *res, uint32_t *map_out, void *cuda_stream)
+static int run_static_impl(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const uint32_t *acc_bits,
+                           const map_opts *opts_in, map_result *res, uint32_t *map_out, void *cuda_stream)
 {
-    g_err.clear();
     if (!res) return fail(MAP_ERR_ARG, "map_run_static: result is NULL");
     if (n == 0 || n > ST_MAX_N)
         return fail(MAP_ERR_ARG, "map_run_static: n = %u is outside [1, %llu] (MAP_STATIC_MAX_N); use map_create/map_run",
@@ -1624,6 +1679,7 @@ extern "C" int map_run_static(uint32_t n, const uint32_t *rowptr, const uint32_t
     h.rounds_hist = g.hist;
     h.out = out_dev ? map_out : g.xbuf;
     h.use_graph = 0;
+    h.early_exit = (opts.flags & MAP_FLAG_EARLY_EXIT) ? 1 : 0;
     h.timeout_ns = (uint64_t)(opts.timeout_ms ? opts.timeout_ms : 120000u) * 1000000ull;
     h.witness.v = mapk::NONE;
     CK(cudaMemcpyAsync(ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, s));
@@ -1646,7 +1702,7 @@ extern "C" int map_run_static(uint32_t n, const uint32_t *rowptr, const uint32_t
     res->verdict = h.verdict ? MAP_CYCLE : MAP_NO_CYCLE;
     res->witness = h.verdict ? h.witness.v : MAP_NONE;
     res->outer_iters = h.outer;
-    res->inner_canonical = sync_sched ? 1 : 0;
+    res->inner_canonical = (sync_sched && !h.early_hit) ? 1 : 0;
     res->inner_iters = h.inner_total;
     res->relaxations = h.relax.v;
     res->edges_total = m * (uint64_t)h.outer;
@@ -1661,6 +1717,15 @@ extern "C" int map_run_static(uint32_t n, const uint32_t *rowptr, const uint32_t
     if (h.status == mapk::ST_LIMIT) return fail(MAP_ERR_LIMIT, "map_run_static: max_outer or max_inner reached");
     if (h.status == mapk::ST_TIMEOUT) return fail(MAP_ERR_TIMEOUT, "map_run_static: stopped after the timeout");
     return MAP_OK;
+}
+
+extern "C" int map_run_static(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const uint32_t *acc_bits,
+                              const map_opts *opts, map_result *res, uint32_t *map_out, void *cuda_stream)
+{
+    g_err.clear();
+    const int rc = run_static_impl(n, rowptr, colidx, acc_bits, opts, res, map_out, cuda_stream);
+    if (res) res->status = (uint32_t)rc; // as map_run: the run's status beside what was computed
+    return rc;
 }
 
 // ============================================================================
@@ -1752,7 +1817,10 @@ size_t graph_footprint(uint64_t n, uint64_t m)
     const uint64_t W = (n + 31) / 32;
     const uint64_t words = 2 * (n + 5) + 3 * (m + 4) + 3 * (W + 4) + (n + 4) + 2 * 3 * (n + 4) + 4 * (n + 4) +
                            3 * (n + 4) + (1u << 16);
-    return (size_t)words * 4 + sizeof(Ctl) + (1u << 20);
+    // the worklist queue of asynchronous runs: 8 bytes per vertex and per resident thread, the
+    // in-queue bitmap
+    const uint64_t queue = 8 * (n + 152ull * 2048 + 64) + 4 * (W + 4) + sizeof(mapk::QState);
+    return (size_t)words * 4 + sizeof(Ctl) + (size_t)queue + (1u << 20);
 }
 
 } // namespace

@@ -99,6 +99,10 @@ struct Ctl {
     uint32_t early_hit;    // it did (the run's round state is then left dirty)
     uint32_t tprev;        // |touched| of the previous outer iteration (frontier start resets their values)
     uint32_t pad[2];
+    // %globaltimer stamps of the phases (ns), summed over the run: the end of the last phase
+    // (t_mark), the dense rounds, the fix-point rounds, the self-map tests and eliminations.  Each
+    // phase runs from the end of the one before it, so gaps between launches count to the next.
+    uint64_t t_mark, ph_dense, ph_rounds, ph_check;
 };
 
 struct Handles {
@@ -129,6 +133,21 @@ struct CompState {
     uint64_t pad1;
 };
 
+// Work queue of the asynchronous worklist fix-point (k_queue), one per single-graph handle.
+// Positions grow without bound over the handle's life (64-bit counters); position p lives in
+// cell p % qcap.  A cell is one 64-bit word: the high half is a sequence number (the low 32
+// bits of p while the cell is free for position p, of p + 1 once the item of position p is
+// published), the low half the queued vertex.  A consumer that has read position p frees the
+// cell for position p + qcap.  With at most one queued item per vertex (the in-queue bitmap)
+// and qcap >= n + the threads of the grid, a producer never finds its cell still taken.
+struct QState {
+    Cnt64 tail; // next position to write (reserved by producers)
+    Cnt64 head; // next position to read (reserved by consumers; may run ahead of tail)
+    Cnt64 done; // positions whose item has been processed (equal to tail when the queue is drained)
+    Cnt32 stop; // Q_STOP_* once the drain must end early
+};
+constexpr uint32_t Q_STOP_TIMEOUT = 1, Q_STOP_EARLY = 2, Q_STOP_FAULT = 3;
+
 struct Dev {
     uint32_t n, words;
     // batched runs only (comp == NULL for a single graph)
@@ -149,6 +168,11 @@ struct Dev {
     // those still accepting instead of the dense round (NULL: the dense round runs)
     const uint32_t *alist;
     uint32_t na;
+    // worklist fix-point (single graphs, asynchronous schedule; NULL: the round kernel runs)
+    uint64_t *qcell;
+    uint64_t qcap;
+    QState *qs;
+    uint32_t *inq; // bit v: v is queued (set when queued, cleared when a consumer takes it)
 };
 
 __device__ __forceinline__ uint32_t CB(uint32_t p) { return 1u << p; } // in list[p]
@@ -364,9 +388,18 @@ __device__ __forceinline__ bool timed_out(volatile Ctl *v)
 
 // After round 1 (the dense round) of an outer iteration: list[1] holds the
 // vertices that got a value, which are also the touched vertices so far.
+// the time since the last phase ended goes to *acc; this phase ends now
+__device__ __forceinline__ void phase_end(volatile Ctl *v, volatile uint64_t *acc)
+{
+    const uint64_t now = global_ns();
+    *acc = *acc + (now - v->t_mark);
+    v->t_mark = now;
+}
+
 __device__ void epilogue_dense(Ctl *c)
 {
     volatile Ctl *v = c;
+    phase_end(v, &v->ph_dense);
     v->tcnt.v = v->lcnt[1].v;
     v->k = 1;
     v->relax.v = v->relax.v + v->m;
@@ -377,6 +410,7 @@ __device__ void epilogue_dense(Ctl *c)
 __device__ void epilogue_check(Ctl *c, Handles hd)
 {
     volatile Ctl *v = c;
+    phase_end(v, &v->ph_check);
     const uint32_t outer = v->outer, k = v->k;
     if (outer - 1 < v->hist_cap) c->rounds_hist[outer - 1] = k;
     v->inner_total = v->inner_total + k;
@@ -445,6 +479,7 @@ __device__ void epilogue_batch(const Dev &d, Handles hd)
     __shared__ uint32_t s_any, s_gst;
     volatile Ctl *v = d.ctl;
     if (threadIdx.x == 0) {
+        phase_end(v, &v->ph_check);
         uint32_t gst = v->status; // a limit or timeout inside the fix-point loop
         if (gst == ST_OK && timed_out(v)) gst = ST_TIMEOUT;
         s_gst = gst;
@@ -533,6 +568,8 @@ __global__ void k_run_begin(Ctl *c, Handles hd)
     v->relax.v = 0;
     v->inner_total = 0;
     v->t0 = global_ns();
+    v->t_mark = v->t0;
+    v->ph_dense = v->ph_rounds = v->ph_check = 0;
     const uint32_t go = v->nacc0 ? 1u : 0u;
     v->outer = go;
     v->outer_go = go;
@@ -863,10 +900,17 @@ __device__ __forceinline__ uint32_t block_inclusive_scan(uint32_t x, uint32_t *s
 }
 
 // Bounded grid-wide barrier of a cooperative launch (every block resident).
-// Returns false if the wait gave up (the caller then stops).
+// Returns false if the wait gave up (the caller then stops).  Only thread 0 of
+// each block touches the barrier words; with `p` < 3 it also reads the counters
+// the next round needs (|list[p]|, |flist[p]|, self_seen, stop_req) into `s_vals`
+// before the block is released, so that they cost one L2 read per block instead
+// of one per warp.
 constexpr uint32_t BAR_SPIN_LIMIT = 1u << 24;
+#ifndef MAPGPU_BAR_SLEEP_NS
+#define MAPGPU_BAR_SLEEP_NS 32 // back-off between polls of the barrier generation
+#endif
 
-__device__ __forceinline__ bool grid_barrier(Ctl *ctl)
+__device__ __forceinline__ bool grid_barrier(Ctl *ctl, uint32_t p = 3, uint32_t *s_vals = nullptr)
 {
     __shared__ uint32_t s_ok;
     __syncthreads();
@@ -884,11 +928,18 @@ __device__ __forceinline__ bool grid_barrier(Ctl *ctl)
                     ok = 0;
                     break;
                 }
-                if (it > 16) __nanosleep(32);
+                if (it > 16) __nanosleep(MAPGPU_BAR_SLEEP_NS);
             }
         }
         __threadfence();
         s_ok = ok;
+        if (p < 3) {
+            volatile Ctl *v = ctl;
+            s_vals[0] = v->lcnt[p].v;
+            s_vals[1] = v->fcnt[p].v;
+            s_vals[2] = v->self_seen.v;
+            s_vals[3] = v->stop_req.v;
+        }
     }
     __syncthreads();
     return s_ok != 0;
@@ -985,6 +1036,7 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
     __shared__ uint32_t s_loc[LC_CAP], s_ln; // vertices this block listed in this round
     __shared__ uint32_t *s_dst[3][2];
     __shared__ unsigned int *s_ctr[3];
+    __shared__ uint32_t s_vals[4]; // after each barrier: |list|, |flist| of the round, self_seen, stop_req
     Ctl *ctl = d.ctl;
     volatile Ctl *vc = ctl;
     const unsigned lane = lane_id();
@@ -993,6 +1045,7 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
     unsigned long long relax = 0, frows = 0;
     uint32_t status = ST_OK;
     uint32_t nl = vc->lcnt[1].v; // vertices that got a value in the dense round
+    uint32_t nf = vc->fcnt[1].v; // frontier rows of the last round (cleared at the start of the next)
     uint32_t r = 1;              // rounds completed
     const bool early = vc->early_exit && !d.comp;
     // Frontier start: no dense round ran.  Round 1 gives every row the largest accepting id in
@@ -1050,7 +1103,7 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
         st.buf = s_stage[threadIdx.x >> 5];
         st.cnt[0] = st.cnt[1] = st.cnt[2] = 0;
         // the previous round's frontier: clear its flags, count its relaxations
-        if (track && !first) relax += clear_frontier(pick3(p_in, d.flist), vc->fcnt[p_in].v, p_in, d.rec, d.rowptr, d);
+        if (track && !first) relax += clear_frontier(pick3(p_in, d.flist), nf, p_in, d.rec, d.rowptr, d);
         // round 1 of a frontier start keeps no frontier: its relaxations are the canonical m
         const bool trk = track && !first;
 
@@ -1184,32 +1237,288 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
         }
         stage_flush_block<3>(st, s_cnt, s_base, dst, ctr);
         if (lead && timed_out(vc)) vc->stop_req.v = 1;
-        if (!grid_barrier(ctl)) {
+        if (!grid_barrier(ctl, p_out, s_vals)) {
             status = ST_TIMEOUT;
             break;
         }
         r = rr;
-        if (!first) frows += track ? vc->fcnt[p_out].v : nl; // frontier rows, or the vertices that pushed
-        nl = vc->lcnt[p_out].v;                  // changed in this round
-        if (early && nl && vc->self_seen.v != NONE) { // stop here: the recorded vertex is the witness
+        nf = s_vals[1];
+        if (!first) frows += track ? nf : nl; // frontier rows, or the vertices that pushed
+        nl = s_vals[0];                       // changed in this round
+        if (early && nl && s_vals[2] != NONE) { // stop here: the recorded vertex is the witness
             nl = 0;
             if (lead) vc->early_hit = 1;
         }
-        if (vc->stop_req.v) status = ST_TIMEOUT;
+        if (s_vals[3]) status = ST_TIMEOUT;
         else if (nl && r + 1 > max_inner) status = ST_LIMIT;
     }
     // the last round's frontier: clear its flags, count its relaxations
-    if (r > 1 && track) relax += clear_frontier(pick3(r % 3, d.flist), vc->fcnt[r % 3].v, r % 3, d.rec, d.rowptr, d);
+    if (r > 1 && track) relax += clear_frontier(pick3(r % 3, d.flist), nf, r % 3, d.rec, d.rowptr, d);
     block_add_u64(relax, (unsigned long long *)&ctl->relax.v);
     if (threadIdx.x == 0 && status != ST_OK) vc->status = status; // any block that stopped early
     if (lead) {
         vc->k = r;
         vc->frontier_rows.v = vc->frontier_rows.v + frows;
+        phase_end(vc, &vc->ph_rounds); // every block has passed the last barrier
         __threadfence();
     }
     // In a CUDA graph the self-map test and the elimination follow in this launch (one kernel
     // boundary less per outer iteration); every block's appends were flushed before the last
     // barrier.  A block whose barrier gave up skips the work but still takes its ticket.
+    if (vc->use_graph) check_phase(d, hd, status == ST_OK);
+}
+
+// ------------------------------------------------- worklist fix-point --
+//
+// The asynchronous schedule of a single graph without rounds (k_queue): after round 1 (the
+// dense round, or for the frontier start the accepting vertices themselves) every vertex that
+// got a value is queued; a consumer takes a queued vertex u, reads its live value, offers
+// max(u + 1 if u accepting, map(u)) to its readers with atomicMax, and queues each reader it
+// raises that is not queued already.  Values only grow and each is a real accepting successor,
+// so the loop ends at the unique least fix-point, the one the synchronous rounds reach
+// (Section 2: propagation to the fix-point); there is no grid-wide step between propagation
+// steps, so no thread waits for the slowest one of a round.
+//
+// Lost updates are excluded per vertex: a producer raises map(w), then tests-and-sets w's
+// in-queue bit; a consumer clears the bit, then reads map(u).  A full fence sits between the
+// two accesses on both sides, so either the consumer reads the raised value or the producer
+// sees the bit cleared and queues w again.
+//
+// The loop ends when every reserved position has been processed (done == tail, read in that
+// order): only processing creates items, so nothing can be queued afterwards.  Consumers
+// reserve positions ahead of the producers (each warp keeps one reservation per lane) and wait
+// for them with a growing back-off; every wait ends by the run's time limit.
+constexpr uint32_t Q_SPIN_LIMIT = 1u << 22; // a producer's wait for its cell (never long: see QState)
+constexpr uint32_t Q_BACKOFF_MAX_NS = 2048;
+
+__device__ __forceinline__ uint64_t q_load(const uint64_t *c)
+{
+    return *(const volatile uint64_t *)c;
+}
+__device__ __forceinline__ void q_store(uint64_t *c, uint64_t x) { *(volatile uint64_t *)c = x; }
+
+// queue w where flag holds (every lane of the warp calls it): one reservation per warp; false
+// in every lane if a cell stayed taken past the spin limit (the drain then stops)
+__device__ __forceinline__ bool q_push(const Dev &d, bool flag, uint32_t w)
+{
+    const unsigned mask = __ballot_sync(0xFFFFFFFFu, flag);
+    if (!mask) return true;
+    const unsigned lane = lane_id(), leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd((unsigned long long *)&d.qs->tail.v, (unsigned long long)__popc(mask));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    bool ok = true;
+    if (flag) {
+        const uint64_t p = base + __popc(mask & ((1u << lane) - 1u));
+        uint64_t *cell = d.qcell + p % d.qcap;
+        for (uint32_t spin = 0; (uint32_t)(q_load(cell) >> 32) != (uint32_t)p; ++spin) {
+            if (spin > Q_SPIN_LIMIT) {
+                ok = false;
+                break;
+            }
+            __nanosleep(64);
+        }
+        if (ok) q_store(cell, ((uint64_t)(uint32_t)(p + 1) << 32) | w);
+    }
+    return __all_sync(0xFFFFFFFFu, ok);
+}
+
+// free the cells of the queue: cell i waits for position i (once per handle and after a drain
+// that stopped early)
+__global__ void k_queue_init(uint64_t *qcell, uint64_t qcap)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < qcap; i += stride)
+        qcell[i] = (uint64_t)(uint32_t)i << 32;
+}
+
+__global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_queue(const Dev d, Handles hd)
+{
+    Ctl *ctl = d.ctl;
+    volatile Ctl *vc = ctl;
+    QState *qs = d.qs;
+    const unsigned lane = lane_id();
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    const bool fstart = d.alist != nullptr;
+    const bool early = vc->early_exit != 0;
+    const uint64_t t0 = vc->t0, tmo = vc->timeout_ns;
+    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t status = ST_OK;
+    // the queue is drained at this point: tail == done, head may have run ahead of them
+    const uint64_t T0 = *(volatile uint64_t *)&qs->tail.v;
+
+    // ---- round 1 and the first items
+    uint32_t nseed = 0;
+    const uint32_t *seed = nullptr;
+    if (fstart) {
+        // round 1 from the accepting vertices: reset the previous iteration's values first
+        default_stop(ctl, hd.outer);
+        const uint32_t tp = vc->tprev;
+        for (uint64_t i = gtid; i < tp; i += nthreads) d.mval[__ldg(d.touched + i)] = 0;
+        nseed = d.na;
+        seed = d.alist;
+    } else if (!(early && vc->self_seen.v != NONE)) { // (the dense round may have found a self-mapped vertex)
+        nseed = vc->lcnt[1].v; // vertices that got a value in the dense round
+        seed = d.list[1];
+    }
+    bool ok = true;
+    for (uint64_t base = gtid & ~31ull; base < nseed; base += nthreads) { // warp-uniform
+        const uint64_t i = base + lane;
+        uint32_t u = 0;
+        bool f = false;
+        if (i < nseed) {
+            u = __ldg(seed + i);
+            f = !fstart || acc_bit(d.acc, u); // (frontier start: eliminated vertices offer nothing)
+            if (f) atomicOr(d.inq + (u >> 5), 1u << (u & 31u));
+        }
+        ok &= q_push(d, f, u);
+    }
+    if (!ok) atomicExch(&qs->stop.v, Q_STOP_FAULT);
+    if (lead) *(volatile unsigned long long *)&qs->head.v = T0; // consumers start at the first item
+    if (!grid_barrier(ctl)) status = ST_TIMEOUT;
+
+    // ---- the drain: one reservation per lane; ready lanes' items are processed by the whole warp
+    unsigned long long relax = 0, items = 0;
+    bool has = false;
+    uint64_t mypos = 0;
+    uint32_t backoff = 0, iter = 0;
+    while (status == ST_OK) {
+        const unsigned need = __ballot_sync(0xFFFFFFFFu, !has);
+        if (need) {
+            unsigned long long b = 0;
+            if (lane == 0) b = atomicAdd((unsigned long long *)&qs->head.v, (unsigned long long)__popc(need));
+            b = __shfl_sync(0xFFFFFFFFu, b, 0);
+            if (!has) {
+                mypos = b + __popc(need & ((1u << lane) - 1u));
+                has = true;
+            }
+        }
+        uint64_t *cell = d.qcell + mypos % d.qcap;
+        const uint64_t cv = q_load(cell);
+        const bool ready = (uint32_t)(cv >> 32) == (uint32_t)(mypos + 1);
+        const uint32_t u = (uint32_t)cv;
+        if (ready) {
+            q_store(cell, (uint64_t)(uint32_t)(mypos + d.qcap) << 32); // free for the next lap
+            has = false;
+        }
+        const unsigned rmask = __ballot_sync(0xFFFFFFFFu, ready);
+        ++iter;
+        if (!rmask) { // nothing here yet: the end of the drain, a stop, or wait
+            uint32_t fin = 0;
+            if (lane == 0) {
+                const uint64_t D = *(volatile unsigned long long *)&qs->done.v;
+                const uint64_t T = *(volatile unsigned long long *)&qs->tail.v;
+                fin = D == T ? 4u : 0u;
+                uint32_t stp = *(volatile uint32_t *)&qs->stop.v;
+                if (!fin && !stp && (iter & 15u) == 0 && global_ns() - t0 > tmo) {
+                    atomicExch(&qs->stop.v, Q_STOP_TIMEOUT);
+                    stp = Q_STOP_TIMEOUT;
+                }
+                fin |= stp;
+            }
+            if (__shfl_sync(0xFFFFFFFFu, fin, 0)) break;
+            backoff = backoff ? min(backoff * 2, Q_BACKOFF_MAX_NS) : 64;
+            __nanosleep(backoff);
+            continue;
+        }
+        backoff = 0;
+        if ((iter & 15u) == 0) { // a stop is rare: look (and at the clock) every 16 busy iterations
+            uint32_t stp = 0;
+            if (lane == 0) {
+                stp = *(volatile uint32_t *)&qs->stop.v;
+                if (!stp && global_ns() - t0 > tmo) {
+                    atomicExch(&qs->stop.v, Q_STOP_TIMEOUT);
+                    stp = Q_STOP_TIMEOUT;
+                }
+            }
+            if (__shfl_sync(0xFFFFFFFFu, stp, 0)) break;
+        }
+        // take the items: clear their in-queue bits, then (after a full fence) read their values
+        if (ready) atomicAnd(d.inq + (u >> 5), ~(1u << (u & 31u)));
+        __threadfence();
+        uint32_t o = 0, rb = 0, len = 0;
+        if (ready) {
+            const uint32_t x = *(volatile uint32_t *)(d.mval + u);
+            o = acc_bit(d.acc, u) ? max(x, u + 1) : x;
+            rb = __ldg(d.rrowptr + u);
+            len = o ? __ldg(d.rrowptr + u + 1) - rb : 0u;
+        }
+        const uint32_t incl = warp_inclusive_scan(len);
+        const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        const uint32_t excl = incl - len;
+        if (lane == 0) {
+            relax += total; // pushes
+            items += __popc(rmask);
+        }
+        bool okp = true;
+        for (uint32_t p0 = 0; p0 < total; p0 += 32) {
+            const uint32_t p = p0 + lane;
+            // the owner of pair p: the first lane whose inclusive sum exceeds p
+            uint32_t j = 0;
+#pragma unroll
+            for (uint32_t st = 16; st >= 1; st >>= 1)
+                if (__shfl_sync(0xFFFFFFFFu, incl, j + st - 1) <= p) j += st;
+            const uint32_t ob = __shfl_sync(0xFFFFFFFFu, o, j & 31u);
+            const uint32_t jj = __shfl_sync(0xFFFFFFFFu, rb, j & 31u) + (p - __shfl_sync(0xFFFFFFFFu, excl, j & 31u));
+            const bool act = p < total;
+            uint32_t w = 0, old = 0xFFFFFFFFu;
+            if (act) {
+                w = __ldg(d.rcol + jj);
+                old = atomicMax(d.mval + w, ob);
+            }
+            const bool raised = act && ob > old;
+            const bool fresh = raised && old == 0; // w got its first value of this outer iteration
+            {
+                const unsigned fm = __ballot_sync(0xFFFFFFFFu, fresh);
+                if (fm) {
+                    const unsigned leader = __ffs(fm) - 1;
+                    unsigned at = 0;
+                    if (lane == leader) at = atomicAdd(&ctl->tcnt.v, (unsigned)__popc(fm));
+                    at = __shfl_sync(0xFFFFFFFFu, at, leader);
+                    if (fresh) {
+                        d.touched[at + __popc(fm & ((1u << lane) - 1u))] = w;
+                        if (d.stale) atomicOr(d.stale + (w >> 5), 1u << (w & 31u)); // the next dense round resets it
+                    }
+                }
+            }
+            if (raised && ob == w + 1) { // w reaches itself: an accepting cycle
+                atomicMin(&ctl->self_seen.v, w);
+                if (early) atomicExch(&qs->stop.v, Q_STOP_EARLY);
+            }
+            const unsigned rm = __ballot_sync(0xFFFFFFFFu, raised);
+            if (rm) __threadfence(); // the raise is visible before the in-queue bit is tested
+            const bool enq = raised && test_and_set(d.inq, w);
+            okp &= q_push(d, enq, w);
+        }
+        if (!okp && lane == 0) atomicExch(&qs->stop.v, Q_STOP_FAULT);
+        // the items are processed (their readers queued): count them
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence();
+            atomicAdd((unsigned long long *)&qs->done.v, (unsigned long long)__popc(rmask));
+        }
+    }
+    // a drain that stopped early leaves appends in flight in other blocks: wait for every block
+    // before the touched vertices are examined
+    __shared__ uint32_t s_stop;
+    __syncthreads();
+    if (threadIdx.x == 0) s_stop = *(volatile uint32_t *)&qs->stop.v;
+    __syncthreads();
+    const uint32_t stp = s_stop;
+    if (stp && !grid_barrier(ctl)) status = ST_TIMEOUT;
+    if (stp == Q_STOP_TIMEOUT || stp == Q_STOP_FAULT) status = ST_TIMEOUT;
+    block_add_u64(relax, (unsigned long long *)&ctl->relax.v);
+    if (lane == 0 && items) atomicAdd((unsigned long long *)&ctl->frontier_rows.v, items);
+    if (threadIdx.x == 0 && status != ST_OK) vc->status = status;
+    if (lead) {
+        // one pass over the queue counts as one round after round 1 (fewer than the synchronous
+        // rounds, which need at least one more round whenever round 1 changed something)
+        vc->k = (nseed == 0 && !fstart) ? 1u : (vc->tcnt.v ? 2u : 1u);
+        if (stp == Q_STOP_EARLY) vc->early_hit = 1;
+        phase_end(vc, &vc->ph_rounds);
+        __threadfence();
+    }
     if (vc->use_graph) check_phase(d, hd, status == ST_OK);
 }
 
