@@ -96,6 +96,16 @@ enum { MAP_SCHED_SYNC = 0, MAP_SCHED_ASYNC = 1 };
                                    start (without either flag a handle starts the way map_autotune chose,
                                    by default with the dense round).  Both start flags together: MAP_ERR_ARG. */
 
+#define MAP_FLAG_PUSH 64u  /* every round after round 1 pushes from the vertices changed in the round before
+                              to their readers (the reverse CSR) */
+#define MAP_FLAG_PULL 128u /* every round after round 1 pulls: each row takes the largest offer of the
+                              vertices in it that changed in the round before (one pass over the whole
+                              matrix, like the dense round).  Without either flag a round pulls when its
+                              list holds at least a share of the vertices that map_autotune measures per
+                              handle (by default none pulls).  Push and pull give the same values in every round,
+                              and under MAP_SCHED_SYNC the same canonical round and relaxation counts.
+                              Both flags together: MAP_ERR_ARG.  map_run_static always pushes. */
+
 /* Called after the fix-point of every outer iteration, before the cycle test
  * and the elimination: map[v] is map(v) of that iteration (MAP_NONE if none),
  * host memory valid during the call only; rounds is that iteration's round
@@ -139,6 +149,9 @@ typedef struct {
                                  graph ASYNC runs: the vertices that pushed) */
     uint32_t status;          /* map_status of this graph's run (batched runs report one per graph) */
     uint32_t reserved;
+    double queue_ms;          /* served jobs (map_poll): from map_submit until a worker took the job */
+    double setup_ms;          /* served jobs: map_create (copy to the device, validation, readers) */
+    double run_ms;            /* served jobs: the run until the map is back in host memory (host clock) */
 } map_result;
 
 typedef struct map_graph map_graph; /* opaque: the device-resident graph and its work space */
@@ -237,7 +250,14 @@ MAP_API int map_batch_run(map_graph *g, const map_opts *opts, map_result *result
  *   it once).
  * map_server_destroy -- finishes the jobs already admitted and queued, then
  *   frees everything; unpolled results are discarded.
- * The server's calls may come from any host threads.
+ * The server's calls may come from any host threads.  A job that fails (for
+ * example MAP_ERR_OOM when its device memory cannot be had) reports its status
+ * at map_poll and releases what it held; the other jobs are not affected.
+ *
+ * Fault injection for tests (host side, off by default): when the environment
+ * variable MAPGPU_INJECT_OOM holds "job:k[,job:k...]" at map_server_create,
+ * the k-th device allocation of map_create for the job with that id (ids count
+ * from 1 in submission order) fails as if the device were out of memory.
  */
 typedef struct map_server map_server; /* opaque */
 MAP_API int map_server_create(size_t hbm_budget_bytes, uint32_t max_slots, map_server **out);
@@ -247,16 +267,19 @@ MAP_API int map_poll(map_server *sv, uint64_t job_id, map_result *res, uint32_t 
 MAP_API int map_server_destroy(map_server *sv);
 
 /*
- * map_autotune -- pick the launch shapes of a handle (single graph or batch) by
- * measurement.  The dense-round kernel and the fix-point kernel are timed with
- * CUDA events on full runs of this very graph, at several numbers of resident
- * blocks per SM (up to each kernel's occupancy limit).  The fastest shape of
- * each is kept for later runs of the handle.  It then times
- * whole runs with the dense start and with the frontier start
- * (MAP_FLAG_FRONTIER_START) and keeps the faster one as the handle's start
- * (MAP_FLAG_DENSE_START / MAP_FLAG_FRONTIER_START still force either).  It
- * takes about sixteen runs; results are unaffected (launch shapes and the start
- * do not change any map vector, verdict, witness or outer count, nor the
+ * map_autotune -- pick how a handle (single graph or batch) runs, by measurement
+ * on full runs of this very graph under schedule `sched`, timed with CUDA
+ * events; every choice is kept for later runs of the handle and reported:
+ *  1. from which list size a round pulls over the whole matrix instead of
+ *     pushing through the readers: never, or from 1/256, 1/64, 1/32, 1/16, 1/8
+ *     or 1/4 of the vertices (MAP_FLAG_PUSH / MAP_FLAG_PULL still force
+ *     either);
+ *  2. the launch shapes: resident blocks per SM of the dense-round kernel and
+ *     of the fix-point kernel (up to each kernel's occupancy limit);
+ *  3. the start of every outer iteration: the dense round or the frontier
+ *     start (MAP_FLAG_DENSE_START / MAP_FLAG_FRONTIER_START still force either).
+ * It takes about thirty runs; results are unaffected (none of these
+ * choices changes any map vector, verdict, witness or outer count, nor the
  * counts of the synchronous schedule).
  */
 typedef struct {
@@ -268,6 +291,9 @@ typedef struct {
     uint32_t frontier_start;       /* 1: the handle now starts with the frontier start */
     double dense_start_ms;         /* run time with the dense start */
     double frontier_start_ms;      /* run time with the frontier start */
+    double pull_share;             /* rounds over lists of at least this share of the vertices pull (0: never) */
+    double pull_ms;                /* run time with that share (0: not timed) */
+    double push_only_ms;           /* run time when no round pulls (0: not timed) */
 } map_tune_result;
 MAP_API int map_autotune(map_graph *g, uint32_t sched, map_tune_result *out);
 

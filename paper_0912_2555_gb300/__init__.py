@@ -29,6 +29,8 @@ MAP_FLAG_PROFILE = 1
 MAP_FLAG_EARLY_EXIT = 2
 MAP_FLAG_FRONTIER_START = 4
 MAP_FLAG_DENSE_START = 8
+MAP_FLAG_PUSH = 64
+MAP_FLAG_PULL = 128
 STATUS_NAMES = ["MAP_OK", "MAP_ERR_ARG", "MAP_ERR_CSR", "MAP_ERR_OOM", "MAP_ERR_CUDA", "MAP_ERR_TIMEOUT",
                 "MAP_ERR_LIMIT", "MAP_ERR_NOT_READY", "MAP_ERR_BUSY"]
 
@@ -78,6 +80,9 @@ class MapResult(ctypes.Structure):
         ("frontier_rows", ctypes.c_uint64),
         ("status", ctypes.c_uint32),
         ("reserved", ctypes.c_uint32),
+        ("queue_ms", ctypes.c_double),
+        ("setup_ms", ctypes.c_double),
+        ("run_ms", ctypes.c_double),
     ]
 
 
@@ -91,6 +96,9 @@ class TuneResult(ctypes.Structure):
         ("frontier_start", ctypes.c_uint32),
         ("dense_start_ms", ctypes.c_double),
         ("frontier_start_ms", ctypes.c_double),
+        ("pull_share", ctypes.c_double),
+        ("pull_ms", ctypes.c_double),
+        ("push_only_ms", ctypes.c_double),
     ]
 
 
@@ -104,7 +112,8 @@ def map_autotune(handle, sched: int = MAP_SCHED_SYNC) -> dict:
     return {"dense_blocks_per_sm": t.dense_blocks_per_sm, "rounds_blocks_per_sm": t.rounds_blocks_per_sm,
             "dense_ms": t.dense_ms, "rounds_ms": t.rounds_ms, "trials": t.trials,
             "frontier_start": bool(t.frontier_start), "dense_start_ms": t.dense_start_ms,
-            "frontier_start_ms": t.frontier_start_ms}
+            "frontier_start_ms": t.frontier_start_ms, "pull_share": t.pull_share, "pull_ms": t.pull_ms,
+            "push_only_ms": t.push_only_ms}
 
 
 def map_lasso(handle, witness: int, init: int = MAP_NONE, cap: int = 1 << 20):
@@ -293,6 +302,9 @@ class RunResult:
     check_ms: float
     frontier_rows: int
     trace: list
+    queue_ms: float = 0.0  # served jobs: waiting for a worker
+    setup_ms: float = 0.0  # served jobs: map_create
+    run_ms: float = 0.0  # served jobs: run and map back to host memory
 
 
 def map_run(handle, sched: int = MAP_SCHED_SYNC, max_outer: int = 0, max_inner: int = 0, flags: int = 0,
@@ -416,7 +428,8 @@ def map_batch_run(handle, count: int, sched: int = MAP_SCHED_SYNC, max_outer: in
 def _result(r, trace=()):
     return RunResult(r.status, r.verdict, r.witness, r.outer_iters, [], r.inner_iters, bool(r.inner_canonical),
                      r.relaxations, r.edges_total, r.device_ms, r.dense_ms, r.dense_launches, r.accepting_left,
-                     r.launches, r.round_ms, r.check_ms, r.frontier_rows, list(trace))
+                     r.launches, r.round_ms, r.check_ms, r.frontier_rows, list(trace), r.queue_ms, r.setup_ms,
+                     r.run_ms)
 
 
 class Server:

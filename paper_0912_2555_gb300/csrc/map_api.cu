@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -33,6 +34,9 @@ using mapk::Ctl;
 namespace {
 
 thread_local std::string g_err;
+// fault injection for tests (served jobs, MAPGPU_INJECT_OOM): when positive, the device
+// allocation of create_graph that brings it to zero fails with MAP_ERR_OOM
+thread_local int t_inject_alloc = 0;
 
 int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
 int fail(int code, const char *fmt, ...)
@@ -128,6 +132,40 @@ struct NvtxRange {
     NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
+// Rounds over lists of at least this share of the vertices pull instead of pushing (0 = never,
+// the default; map_autotune measures the share per handle; MAPGPU_PULL_FRAC sets the default).
+double default_pull_frac()
+{
+    if (const char *e = getenv("MAPGPU_PULL_FRAC")) return atof(e);
+    return 0.0;
+}
+
+uint32_t pull_min_for(uint32_t n, double frac)
+{
+    if (!(frac > 0)) return 0;
+    const double v = std::ceil(frac * n);
+    return (uint32_t)std::max(1.0, std::min(v, 4294967295.0));
+}
+
+// resident 256-thread blocks per SM that every variant of the fix-point kernel supports (its
+// launch is cooperative, so the grid may not exceed it)
+int rounds_occupancy()
+{
+    int occ = 1 << 30, o = 0;
+    auto take = [&](const void *k) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, 256, 0) != cudaSuccess) {
+            cudaGetLastError();
+            o = 1;
+        }
+        occ = std::min(occ, o);
+    };
+    take((const void *)mapk::k_rounds<true, false>);
+    take((const void *)mapk::k_rounds<true, true>);
+    take((const void *)mapk::k_rounds<false, false>);
+    take((const void *)mapk::k_rounds<false, true>);
+    return std::max(1, occ);
+}
+
 int pick_group(uint32_t n, uint64_t m)
 {
     const double avg = n ? (double)m / n : 0.0;
@@ -161,6 +199,8 @@ struct map_graph {
     uint4 *rec = nullptr;      // n: per-vertex round state (snapshots, list and frontier flags)
     uint32_t *touched = nullptr, *xbuf = nullptr;
     uint32_t *stale = nullptr; // words: vertices whose mval the next dense round must reset
+    uint32_t *cbit = nullptr;  // 3 bitmaps of `words` (+ slack): the list a pull round reads, by round mod 3
+    uint32_t pull_min = 0;     // rounds over lists of at least this many vertices pull (0: never)
     uint32_t *ids = nullptr; // reduced graphs: the original id of each vertex (else NULL: identity)
     uint32_t rows = 0;       // rows expanded so far (growing graphs); the rest are empty
     bool dirty = false; // a run stopped early: per-round state may be stale
@@ -186,17 +226,9 @@ struct map_graph {
     uint32_t na = 0;
     bool fstart_on = false;
     bool tuned_fstart = false; // map_autotune found the frontier start faster on this graph
-    // worklist fix-point of the asynchronous schedule (single graphs; allocated on first use):
-    // the queue's cells, its counters, the in-queue bitmap; whether the launches being issued
-    // use it, and whether a drain stopped early (the queue must then be reset)
-    uint64_t *qcell = nullptr;
-    uint64_t qcap = 0;
-    mapk::QState *qs = nullptr;
-    uint32_t *inq = nullptr;
-    bool queue_on = false;
-    bool queue_engine = false; // asynchronous runs use the worklist (map_autotune may choose the rounds)
-    // the whole run as one CUDA graph, per schedule, start and engine (built on first use):
-    // index sched + 2 * frontier start + 4 * worklist
+    bool pull_on = false;     // the launches being issued may pull (the fix-point kernel's pull variant)
+    // the whole run as one CUDA graph, per schedule, start and kernel variant (built on first
+    // use): index sched + 2 * frontier start + 4 * pull variant
     cudaGraph_t graph[8] = {};
     cudaGraphExec_t exec[8] = {};
     mapk::Handles handles[8] = {};
@@ -213,12 +245,13 @@ void free_graph(map_graph *g)
     }
     void *dev[] = {g->rowptr, g->colidx, g->rrowptr, g->rcol,    g->rpos, g->elog, g->acc0, g->acc,
                    g->mval,   g->list,   g->flist,   g->rec,     g->touched, g->xbuf, g->hist, g->ctl,
-                   g->alist,  g->qcell,  g->qs,      g->inq};
+                   g->alist};
     for (void *p : dev)
         if (p) cudaFreeAsync(p, g->stream); // stream-ordered: no device-wide synchronisation
     if (g->comp) cudaFreeAsync(g->comp, g->stream);
     if (g->ids) cudaFreeAsync(g->ids, g->stream);
     if (g->stale) cudaFreeAsync(g->stale, g->stream);
+    if (g->cbit) cudaFreeAsync(g->cbit, g->stream);
     if (g->cs) cudaFreeAsync(g->cs, g->stream);
     if (g->chist) cudaFreeAsync(g->chist, g->stream);
     free(g->h_cs);
@@ -311,15 +344,12 @@ mapk::Dev dev_of(const map_graph *g)
         d.flist[p] = g->flist + p * n;
     }
     d.rec = g->rec;
+    for (int p = 0; p < 3; ++p) d.cbit[p] = g->cbit ? g->cbit + p * ((size_t)g->words + 4) : nullptr;
     d.touched = g->touched;
     d.stale = g->comp ? nullptr : g->stale;
     d.ctl = g->ctl;
     d.alist = g->fstart_on ? g->alist : nullptr;
     d.na = g->fstart_on ? g->na : 0;
-    d.qcell = g->queue_on ? g->qcell : nullptr;
-    d.qcap = g->queue_on ? g->qcap : 0;
-    d.qs = g->queue_on ? g->qs : nullptr;
-    d.inq = g->queue_on ? g->inq : nullptr;
     d.comp = g->comp;
     d.cs = g->cs;
     d.chist = g->chist;
@@ -348,31 +378,10 @@ int launch_rounds(map_graph *g, cudaStream_t s, bool sync_sched, mapk::Handles h
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (sync_sched) CK(cudaLaunchKernelEx(&cfg, mapk::k_rounds<true>, d, hd));
-    else if (d.qcell) CK(cudaLaunchKernelEx(&cfg, mapk::k_queue, d, hd));
-    else CK(cudaLaunchKernelEx(&cfg, mapk::k_rounds<false>, d, hd));
-    return MAP_OK;
-}
-
-// the worklist's queue: allocated on first use (cells for n vertices plus one per thread of the
-// largest fix-point grid, so that a producer never waits for its cell), and reset when new or
-// after a drain that stopped early
-int ensure_queue(map_graph *g, cudaStream_t s, bool reset)
-{
-    if (!g->qcell) {
-        const uint64_t cap = (uint64_t)g->n + (uint64_t)g->sms * 2048 + 64; // 2048: resident threads per SM
-        CK(cudaMallocAsync((void **)&g->qcell, cap * sizeof(uint64_t), s));
-        CK(cudaMallocAsync((void **)&g->qs, sizeof(mapk::QState), s));
-        CK(cudaMallocAsync((void **)&g->inq, ((size_t)g->words + 4) * 4, s));
-        g->qcap = cap;
-        reset = true;
-    }
-    if (reset) {
-        mapk::k_queue_init<<<grid_for(g, g->qcap, 1), 256, 0, s>>>(g->qcell, g->qcap);
-        CK(cudaGetLastError());
-        CK(cudaMemsetAsync(g->qs, 0, sizeof(mapk::QState), s));
-        CK(cudaMemsetAsync(g->inq, 0, ((size_t)g->words + 4) * 4, s));
-    }
+    if (sync_sched && g->pull_on) CK(cudaLaunchKernelEx(&cfg, mapk::k_rounds<true, true>, d, hd));
+    else if (sync_sched) CK(cudaLaunchKernelEx(&cfg, mapk::k_rounds<true, false>, d, hd));
+    else if (g->pull_on) CK(cudaLaunchKernelEx(&cfg, mapk::k_rounds<false, true>, d, hd));
+    else CK(cudaLaunchKernelEx(&cfg, mapk::k_rounds<false, false>, d, hd));
     return MAP_OK;
 }
 
@@ -429,7 +438,7 @@ int add_while(cudaStream_t cs, unsigned long long handle, cudaGraph_t *body)
 
 int build_run_graph(map_graph *g, int sched)
 {
-    const int slot = sched + (g->fstart_on ? 2 : 0) + (g->queue_on ? 4 : 0);
+    const int slot = sched + (g->fstart_on ? 2 : 0) + (g->pull_on ? 4 : 0);
     if (g->exec[slot]) return MAP_OK;
     const bool sync_sched = sched == MAP_SCHED_SYNC;
     cudaStream_t cs;
@@ -557,11 +566,7 @@ int create_graph(uint32_t n, uint64_t m, cudaStream_t s, const char *who, Upload
     if (occ <= 0) occ = 1;
     const uint64_t ntiles = ((uint64_t)n + mapk::WT_ROWS - 1) / mapk::WT_ROWS;
     g->dense_grid = (int)std::min<uint64_t>((ntiles + mapk::WT_WARPS - 1) / mapk::WT_WARPS, (uint64_t)g->sms * occ);
-    int occ_r = 0, occ_a = 0, occ_q = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_r, mapk::k_rounds<true>, 256, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, mapk::k_rounds<false>, 256, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_q, mapk::k_queue, 256, 0);
-    occ_r = std::max(1, std::min(occ_r, std::min(occ_a, occ_q)));
+    int occ_r = rounds_occupancy();
     // launch shape of the fix-point kernel: MAPGPU_ROUNDS_BLOCKS_PER_SM (1 .. the occupancy
     // limit) overrides the default of every resident slot
     if (const char *e = getenv("MAPGPU_ROUNDS_BLOCKS_PER_SM")) {
@@ -573,8 +578,11 @@ int create_graph(uint32_t n, uint64_t m, cudaStream_t s, const char *who, Upload
     g->occ_rounds = occ_r;
     g->check_grid = (int)std::min<uint64_t>(((uint64_t)n + 255) / 256, (uint64_t)g->sms * 4);
     g->hist_cap = 1u << 16;
+    g->pull_min = pull_min_for(n, default_pull_frac());
 
     auto alloc = [&](uint32_t **p, uint64_t words) -> int {
+        if (t_inject_alloc > 0 && --t_inject_alloc == 0)
+            return fail(MAP_ERR_OOM, "%s: injected device allocation failure (MAPGPU_INJECT_OOM)", who);
         // stream-ordered allocation (does not synchronise the device; graphs on other
         // streams keep running); 16 bytes of slack at the end
         CK(cudaMallocAsync((void **)p, (words + 4) * sizeof(uint32_t), s));
@@ -588,7 +596,7 @@ int create_graph(uint32_t n, uint64_t m, cudaStream_t s, const char *who, Upload
         (rc = alloc(&g->acc, W)) || (rc = alloc(&g->mval, n)) || (rc = alloc(&g->list, 3 * (uint64_t)n)) ||
         (rc = alloc(&g->flist, 3 * (uint64_t)n)) || (rc = alloc((uint32_t **)&g->rec, 4 * (uint64_t)n)) ||
         (rc = alloc(&g->touched, n)) || (rc = alloc(&g->xbuf, n)) || (rc = alloc(&g->stale, W)) ||
-        (rc = alloc(&g->hist, g->hist_cap))) {
+        (rc = alloc(&g->cbit, 3 * (W + 4))) || (rc = alloc(&g->hist, g->hist_cap))) {
         free_graph(g);
         return rc;
     }
@@ -632,7 +640,8 @@ int create_graph(uint32_t n, uint64_t m, cudaStream_t s, const char *who, Upload
     if ((rc = ck(cudaMemsetAsync(g->colidx + m, 0, 16, s), "pad")) ||
         (rc = ck(cudaMemsetAsync(g->mval, 0, ((size_t)n + 4) * 4, s), "memset mval")) ||
         (rc = ck(cudaMemsetAsync(g->rec, 0, (size_t)n * 16, s), "memset rec")) ||
-        (rc = ck(cudaMemsetAsync(g->stale, 0, ((size_t)W + 4) * 4, s), "memset stale"))) {
+        (rc = ck(cudaMemsetAsync(g->stale, 0, ((size_t)W + 4) * 4, s), "memset stale")) ||
+        (rc = ck(cudaMemsetAsync(g->cbit, 0, 3 * ((size_t)W + 4) * 4, s), "memset cbit"))) {
         free_graph(g);
         return rc;
     }
@@ -752,13 +761,14 @@ static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint
                         g->nacc0 > 0;
     // the worklist fix-point for the asynchronous schedule of a single graph (unless map_autotune
     // chose the rounds for this handle); a limit of one round per outer iteration needs the rounds
-    const bool queue = !sync_sched && !g->comp && g->queue_engine && (opts.max_inner == 0 || opts.max_inner >= 2);
+    if ((opts.flags & MAP_FLAG_PUSH) && (opts.flags & MAP_FLAG_PULL))
+        return fail(MAP_ERR_ARG, "map_run: MAP_FLAG_PUSH and MAP_FLAG_PULL together");
     struct FstartOff { // the flags only hold for the launches of this run
         map_graph *g;
         ~FstartOff()
         {
             g->fstart_on = false;
-            g->queue_on = false;
+            g->pull_on = false;
         }
     } fstart_off{g};
     memset(res, 0, sizeof *res);
@@ -780,6 +790,8 @@ static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint
     init.early_exit = (opts.flags & MAP_FLAG_EARLY_EXIT) ? 1 : 0;
     init.timeout_ns = (uint64_t)(opts.timeout_ms ? opts.timeout_ms : 120000u) * 1000000ull;
     init.witness.v = mapk::NONE;
+    init.pull_min = (opts.flags & MAP_FLAG_PULL) ? 1u : (opts.flags & MAP_FLAG_PUSH) ? 0u : g->pull_min;
+    g->pull_on = init.pull_min != 0;
 
     int rc = MAP_OK;
     float dense_ms = 0.f, round_ms = 0.f, check_ms = 0.f;
@@ -795,16 +807,15 @@ static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint
     g->fstart_on = fstart;
     if (g->dirty) { // the previous run stopped early: clear the round state it may have left
         CK(cudaMemsetAsync(g->rec, 0, (size_t)n * 16, s));
+        CK(cudaMemsetAsync(g->cbit, 0, 3 * ((size_t)g->words + 4) * 4, s));
     }
-    if ((queue || (g->dirty && g->qcell)) && (rc = ensure_queue(g, s, g->dirty))) return rc;
-    g->queue_on = queue;
     g->dirty = true; // until this run completes normally
     if (!stepped) {
         if ((rc = build_run_graph(g, opts.sched))) return rc;
         *g->h_ctl = init;
         CK(cudaEventRecord(g->ev[0], s));
         CK(cudaMemcpyAsync(g->ctl, g->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
-        CK(cudaGraphLaunch(g->exec[opts.sched + (fstart ? 2 : 0) + (queue ? 4 : 0)], s));
+        CK(cudaGraphLaunch(g->exec[opts.sched + (fstart ? 2 : 0) + (g->pull_on ? 4 : 0)], s));
         CK(cudaEventRecord(g->ev[1], s));
         if ((rc = read_ctl(g))) return rc;
         res->launches = 0; // filled below from the counts
@@ -940,19 +951,52 @@ int map_autotune(map_graph *g, uint32_t sched, map_tune_result *out)
     g_err.clear();
     if (!g || !out) return fail(MAP_ERR_ARG, "map_autotune: NULL handle or result");
     if (sched > MAP_SCHED_ASYNC) return fail(MAP_ERR_ARG, "map_autotune: unknown schedule %u", sched);
-    int occ_d = 0, occ_r = 0, occ_a = 0;
+    int occ_d = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_d, mapk::k_dense, mapk::DT_THREADS, mapk::DT_SMEM));
-    int occ_q = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_r, mapk::k_rounds<true>, 256, 0));
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, mapk::k_rounds<false>, 256, 0));
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_q, mapk::k_queue, 256, 0));
-    occ_r = std::min(occ_r, std::min(occ_a, occ_q));
+    const int occ_r = rounds_occupancy();
     memset(out, 0, sizeof *out);
+    map_result r;
+    // whole runs (one graph launch each) with `flags`, the better of two
+    auto whole_run = [&](uint32_t flags, double *best_ms) -> int {
+        map_opts q;
+        memset(&q, 0, sizeof q);
+        q.sched = sched;
+        q.flags = flags;
+        *best_ms = 1e30;
+        for (int rep = 0; rep < 2; ++rep) {
+            const int rc = run_impl(g, &q, &r, nullptr);
+            if (rc != MAP_OK) return rc;
+            out->trials++;
+            *best_ms = std::min(*best_ms, r.device_ms);
+        }
+        return MAP_OK;
+    };
+    int rc = MAP_OK;
+    // 1. when a round pulls instead of pushing (rounds over lists of at least a share of the
+    // vertices; 0 = never)
+    out->pull_share = 0;
+    if (g->nacc0) {
+        const double shares[] = {0.0, 1.0 / 256, 1.0 / 64, 1.0 / 32, 1.0 / 16, 1.0 / 8, 1.0 / 4};
+        double best = 1e30;
+        uint32_t best_min = 0;
+        for (double sh : shares) {
+            g->pull_min = pull_min_for(g->n, sh);
+            double t = 0;
+            if ((rc = whole_run(MAP_FLAG_DENSE_START, &t))) return rc;
+            if (sh == 0.0) out->push_only_ms = t;
+            if (t < best) {
+                best = t;
+                best_min = g->pull_min;
+                out->pull_share = sh;
+            }
+        }
+        g->pull_min = best_min;
+        out->pull_ms = best;
+    }
     map_opts o;
     memset(&o, 0, sizeof o);
     o.sched = sched;
     o.flags = MAP_FLAG_PROFILE | MAP_FLAG_DENSE_START; // host-stepped run, CUDA events around every phase
-    map_result r;
     // the dense-round shape first (with the fix-point shape as it is), then the fix-point shape
     const uint32_t cands[] = {1, 2, 3, 4, 6, 8};
     uint32_t best_d = 0, best_r = 0;
@@ -961,8 +1005,7 @@ int map_autotune(map_graph *g, uint32_t sched, map_tune_result *out)
     for (uint32_t bps : cands) {
         if ((int)bps > occ_d) continue;
         set_shapes(g, bps, cur_r);
-        const int rc = run_impl(g, &o, &r, nullptr);
-        if (rc != MAP_OK) return rc;
+        if ((rc = run_impl(g, &o, &r, nullptr)) != MAP_OK) return rc;
         out->trials++;
         if (r.dense_ms < t_d) {
             t_d = r.dense_ms;
@@ -972,8 +1015,7 @@ int map_autotune(map_graph *g, uint32_t sched, map_tune_result *out)
     for (uint32_t bps : cands) {
         if ((int)bps > occ_r) continue;
         set_shapes(g, best_d, bps);
-        const int rc = run_impl(g, &o, &r, nullptr);
-        if (rc != MAP_OK) return rc;
+        if ((rc = run_impl(g, &o, &r, nullptr)) != MAP_OK) return rc;
         out->trials++;
         if (r.round_ms < t_r) {
             t_r = r.round_ms;
@@ -990,18 +1032,8 @@ int map_autotune(map_graph *g, uint32_t sched, map_tune_result *out)
     g->tuned_fstart = false;
     if (g->nacc0) {
         double t[2] = {1e30, 1e30};
-        for (int f = 0; f < 2; ++f) {
-            map_opts q;
-            memset(&q, 0, sizeof q);
-            q.sched = sched;
-            q.flags = f ? MAP_FLAG_FRONTIER_START : MAP_FLAG_DENSE_START;
-            for (int rep = 0; rep < 2; ++rep) {
-                const int rc = run_impl(g, &q, &r, nullptr);
-                if (rc != MAP_OK) return rc;
-                out->trials++;
-                t[f] = std::min(t[f], r.device_ms);
-            }
-        }
+        for (int f = 0; f < 2; ++f)
+            if ((rc = whole_run(f ? MAP_FLAG_FRONTIER_START : MAP_FLAG_DENSE_START, &t[f]))) return rc;
         g->tuned_fstart = t[1] < t[0];
         out->frontier_start = g->tuned_fstart ? 1u : 0u;
         out->dense_start_ms = t[0];
@@ -1608,12 +1640,10 @@ static int run_static_impl(uint32_t n, const uint32_t *rowptr, const uint32_t *c
     int dev = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&g.sms, cudaDevAttrMultiProcessorCount, dev));
-    int occ = 0, occ_r = 0, occ_a = 0;
+    int occ = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mapk::k_dense, mapk::DT_THREADS, mapk::DT_SMEM));
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_r, mapk::k_rounds<true>, 256, 0));
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, mapk::k_rounds<false>, 256, 0));
     occ = std::max(occ, 1);
-    occ_r = std::max(1, std::min(occ_r, occ_a));
+    const int occ_r = rounds_occupancy();
     const uint64_t ntiles = ((uint64_t)n + mapk::WT_ROWS - 1) / mapk::WT_ROWS;
     g.dense_grid = (int)std::min<uint64_t>((ntiles + mapk::WT_WARPS - 1) / mapk::WT_WARPS, (uint64_t)g.sms * occ);
     g.rounds_grid = (int)std::min<uint64_t>(((uint64_t)n + 255) / 256, (uint64_t)g.sms * occ_r);
@@ -1809,6 +1839,8 @@ struct ServerJob {
     map_result res{};
     std::vector<uint32_t> map;
     std::string err;
+    std::chrono::steady_clock::time_point t_submit;
+    int inject_alloc = 0; // test hook: the k-th device allocation of its map_create fails
 };
 
 // device bytes of a graph: the allocations of create_graph
@@ -1817,15 +1849,14 @@ size_t graph_footprint(uint64_t n, uint64_t m)
     const uint64_t W = (n + 31) / 32;
     const uint64_t words = 2 * (n + 5) + 3 * (m + 4) + 3 * (W + 4) + (n + 4) + 2 * 3 * (n + 4) + 4 * (n + 4) +
                            3 * (n + 4) + (1u << 16);
-    // the worklist queue of asynchronous runs: 8 bytes per vertex and per resident thread, the
-    // in-queue bitmap
-    const uint64_t queue = 8 * (n + 152ull * 2048 + 64) + 4 * (W + 4) + sizeof(mapk::QState);
-    return (size_t)words * 4 + sizeof(Ctl) + (size_t)queue + (1u << 20);
+    // the changed-vertex bitmaps of pull rounds
+    return (size_t)(words + 3 * (W + 4)) * 4 + sizeof(Ctl) + (1u << 20);
 }
 
 } // namespace
 
 struct map_server {
+    std::map<uint64_t, int> inject; // MAPGPU_INJECT_OOM: job id -> allocation that fails
     size_t budget = 0;
     size_t used = 0;
     int device = 0;
@@ -1900,8 +1931,12 @@ void server_worker(map_server *sv, cudaStream_t stream)
             ab = p;
         }
         NvtxRange job_range("served job");
+        const auto t_take = std::chrono::steady_clock::now();
         map_graph *g = nullptr;
+        t_inject_alloc = job->inject_alloc;
         int rc = map_create(job->n, rp, ci, ab, stream, &g);
+        t_inject_alloc = 0;
+        const auto t_created = std::chrono::steady_clock::now();
         if (rc == MAP_OK && sv->slots > 1) {
             // the fix-point kernel is a cooperative launch: with every resident slot of the device
             // (the single-graph shape) a job's rounds cannot run beside another job's.  Each worker's
@@ -1923,6 +1958,14 @@ void server_worker(map_server *sv, cudaStream_t stream)
             map_destroy(g);
         }
         if (rc != MAP_OK) job->err = g_err;
+        {
+            using ms = std::chrono::duration<double, std::milli>;
+            const auto t_end = std::chrono::steady_clock::now();
+            job->res.queue_ms = ms(t_take - job->t_submit).count();
+            job->res.setup_ms = ms(t_created - t_take).count();
+            job->res.run_ms = ms(t_end - t_created).count();
+            job->res.status = (uint32_t)rc;
+        }
         // the job's inputs are not needed any more
         std::vector<uint32_t>().swap(job->rowptr);
         std::vector<uint32_t>().swap(job->colidx);
@@ -1957,6 +2000,20 @@ int map_server_create(size_t hbm_budget_bytes, uint32_t max_slots, map_server **
     }
     sv->budget = hbm_budget_bytes;
     sv->slots = max_slots;
+    if (const char *e = getenv("MAPGPU_INJECT_OOM")) { // "job:k,job:k" (test hook)
+        const char *q = e;
+        while (*q) {
+            char *end = nullptr;
+            const unsigned long long job = strtoull(q, &end, 10);
+            if (end == q || *end != ':') break;
+            q = end + 1;
+            const long k = strtol(q, &end, 10);
+            if (end == q) break;
+            if (k > 0) sv->inject[job] = (int)k;
+            q = end;
+            if (*q == ',') ++q;
+        }
+    }
     ctl_slots().reserve(2 * (size_t)max_slots); // control-block mirrors for the workers' graphs, allocated now
     // pinned staging for queued and finished jobs: a quarter of the device budget, at most 2 GiB
     sv->arena.init(std::min<size_t>(hbm_budget_bytes / 4, (size_t)2 << 30));
@@ -2014,9 +2071,12 @@ int map_submit(map_server *sv, uint32_t n, const uint32_t *rowptr, const uint32_
     job->opts.rounds_out = nullptr;
     job->opts.rounds_cap = 0;
     job->footprint = graph_footprint(n, m);
+    job->t_submit = std::chrono::steady_clock::now();
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         job->id = sv->next_id++;
+        const auto inj = sv->inject.find(job->id);
+        if (inj != sv->inject.end()) job->inject_alloc = inj->second;
         sv->jobs[job->id] = job;
         sv->queue.push_back(job);
         *job_id = job->id;

@@ -42,6 +42,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace mapk {
 
 namespace cg = cooperative_groups;
@@ -98,7 +100,8 @@ struct Ctl {
     uint32_t early_exit;   // stop the fix-point loop at the first self-mapped vertex
     uint32_t early_hit;    // it did (the run's round state is then left dirty)
     uint32_t tprev;        // |touched| of the previous outer iteration (frontier start resets their values)
-    uint32_t pad[2];
+    uint32_t pull_min;     // a round whose list holds at least this many vertices pulls (0: never)
+    uint32_t pad[1];
     // %globaltimer stamps of the phases (ns), summed over the run: the end of the last phase
     // (t_mark), the dense rounds, the fix-point rounds, the self-map tests and eliminations.  Each
     // phase runs from the end of the one before it, so gaps between launches count to the next.
@@ -133,21 +136,6 @@ struct CompState {
     uint64_t pad1;
 };
 
-// Work queue of the asynchronous worklist fix-point (k_queue), one per single-graph handle.
-// Positions grow without bound over the handle's life (64-bit counters); position p lives in
-// cell p % qcap.  A cell is one 64-bit word: the high half is a sequence number (the low 32
-// bits of p while the cell is free for position p, of p + 1 once the item of position p is
-// published), the low half the queued vertex.  A consumer that has read position p frees the
-// cell for position p + qcap.  With at most one queued item per vertex (the in-queue bitmap)
-// and qcap >= n + the threads of the grid, a producer never finds its cell still taken.
-struct QState {
-    Cnt64 tail; // next position to write (reserved by producers)
-    Cnt64 head; // next position to read (reserved by consumers; may run ahead of tail)
-    Cnt64 done; // positions whose item has been processed (equal to tail when the queue is drained)
-    Cnt32 stop; // Q_STOP_* once the drain must end early
-};
-constexpr uint32_t Q_STOP_TIMEOUT = 1, Q_STOP_EARLY = 2, Q_STOP_FAULT = 3;
-
 struct Dev {
     uint32_t n, words;
     // batched runs only (comp == NULL for a single graph)
@@ -161,6 +149,7 @@ struct Dev {
     uint32_t *elog;
     uint32_t *list[3], *flist[3];
     uint4 *rec; // .x / .y / .z: snap[0..2]; .w: flags
+    uint32_t *cbit[3]; // pull rounds: bit u of cbit[p] = u is in list[p] (set for a pull round, cleared in the next)
     uint32_t *touched;
     uint32_t *stale; // single graphs: bit v = mval[v] holds a value of an earlier outer iteration (NULL: batched)
     Ctl *ctl;
@@ -168,11 +157,6 @@ struct Dev {
     // those still accepting instead of the dense round (NULL: the dense round runs)
     const uint32_t *alist;
     uint32_t na;
-    // worklist fix-point (single graphs, asynchronous schedule; NULL: the round kernel runs)
-    uint64_t *qcell;
-    uint64_t qcap;
-    QState *qs;
-    uint32_t *inq; // bit v: v is queued (set when queued, cleared when a consumer takes it)
 };
 
 __device__ __forceinline__ uint32_t CB(uint32_t p) { return 1u << p; } // in list[p]
@@ -236,10 +220,12 @@ __device__ __forceinline__ unsigned long long warp_sum64(unsigned long long x)
 }
 
 // Block-wide sum (or min) of per-thread values, applied to a global counter with
-// one atomic per block.  Every thread of the block calls these (__syncthreads).
+// one atomic per block.  Every thread of the block calls these (__syncthreads); the barrier on
+// entry keeps a call from overwriting the partial sums a previous call is still reading.
 __device__ __forceinline__ void block_add_u64(unsigned long long x, unsigned long long *dst)
 {
     __shared__ unsigned long long part[32];
+    __syncthreads();
     x = warp_sum64(x);
     if (lane_id() == 0) part[threadIdx.x >> 5] = x;
     __syncthreads();
@@ -253,6 +239,7 @@ __device__ __forceinline__ void block_add_u64(unsigned long long x, unsigned lon
 __device__ __forceinline__ void block_add_min_u32(uint32_t add, uint32_t mn, uint32_t *dst_add, uint32_t *dst_min)
 {
     __shared__ uint32_t part_add[32], part_min[32];
+    __syncthreads();
     add = __reduce_add_sync(0xFFFFFFFFu, add);
     mn = __reduce_min_sync(0xFFFFFFFFu, mn);
     if (lane_id() == 0) {
@@ -945,9 +932,15 @@ __device__ __forceinline__ bool grid_barrier(Ctl *ctl, uint32_t p = 3, uint32_t 
     return s_ok != 0;
 }
 
-constexpr int RC_E = 1;                 // listed vertices per thread and chunk
-constexpr int RC_ENTRIES = 256 * RC_E;  // per block and chunk
-constexpr int RC_P = 1;                 // push pairs per thread and step
+#ifndef MAPGPU_RC_E
+#define MAPGPU_RC_E 1 // listed vertices per thread and chunk
+#endif
+#ifndef MAPGPU_RC_P
+#define MAPGPU_RC_P 1 // push pairs per thread and step (loads and atomics in flight together)
+#endif
+constexpr int RC_E = MAPGPU_RC_E;
+constexpr int RC_ENTRIES = 256 * RC_E; // per block and chunk
+constexpr int RC_P = MAPGPU_RC_P;
 #ifndef MAPGPU_LC_PASSES
 #define MAPGPU_LC_PASSES 1 // asynchronous schedule: block-local passes over a block's own raised vertices per round
                            // (measured on the 2^26 layered graph, ms per run for 0 / 1 / 2 / 4 / 8 passes:
@@ -964,6 +957,173 @@ constexpr uint32_t LC_CAP = 1024; // entries recorded per block and round (the r
 #ifndef MAPGPU_ROUNDS_MIN_BLOCKS
 #define MAPGPU_ROUNDS_MIN_BLOCKS 6 // resident blocks per SM the register budget is sized for (measured best)
 #endif
+
+// ------------------------------------------------------------- pull rounds --
+//
+// A round whose list is a large share of the graph pulls instead of pushing: every row w
+// streams its entries (as the dense round does, with the same warp tiles), and an entry u
+// that changed in the round before (bit u of cbit[p_in], set from the list beforehand) offers
+// max(u + 1 if u accepting, m(u)) -- its snapshot of the round before under the synchronous
+// schedule, its live value under the asynchronous one.  Row w takes the largest offer if it
+// is above its value; only row w's own warp writes w, so no atomics on values are needed and
+// the synchronous round is the exact Jacobi step (Section 2: one product over the matrix):
+// every value read is one of the round before.  A row holding a changed entry is a frontier
+// row of the pull formulation, so the canonical relaxation count adds its length.  The
+// snapshots, list flags and bits of the pulled list are cleared in the next round (or after
+// the last one), when nobody reads them any more.
+constexpr int PT_ROWS = 128;
+constexpr int PT_UNROLL = 2;
+constexpr uint32_t PT_Q = 64;
+
+struct NoPullSmem {
+    uint32_t unused;
+};
+struct PullSmem {
+    uint32_t rp[8][PT_ROWS + 8];
+    uint32_t best[8][PT_ROWS];
+    uint32_t qe[8][PT_Q], qu[8][PT_Q], qn[8];
+    uint32_t hit[8][PT_ROWS / 32];
+};
+
+template <bool SYNC>
+__device__ __forceinline__ uint32_t pull_offer(const Dev &d, uint32_t u, uint32_t p_in)
+{
+    const uint32_t x = SYNC ? *(volatile uint32_t *)rec_snap(d.rec + u, p_in) : *(volatile uint32_t *)(d.mval + u);
+    return acc_bit(d.acc, u) ? max(x, u + 1) : x;
+}
+
+// the whole round by pull; appends go to list 1 (changed) and 2 (touched) of `st`.  relax
+// gets the canonical count (SYNC or batched) or the entries pulled (asynchronous single
+// graphs), prow the frontier rows.
+template <bool SYNC>
+__device__ __forceinline__ void pull_round(const Dev &d, uint32_t rr, uint32_t p_in, uint32_t p_out, PullSmem &ps, Stage<3> &st,
+                           uint32_t *(*dst)[2], unsigned int **ctr, unsigned long long &relax,
+                           unsigned long long &prow)
+{
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    const uint32_t n = d.n;
+    const uint32_t *__restrict__ rowptr = d.rowptr;
+    const uint32_t *__restrict__ colidx = d.colidx;
+    const uint32_t *cb = pick3(p_in, d.cbit);
+    const bool track = SYNC || d.comp;
+    uint32_t *rp = ps.rp[warp], *best = ps.best[warp];
+    unsigned long long hits = 0; // changed entries pulled
+    const uint32_t ntiles = (n + PT_ROWS - 1) / PT_ROWS;
+    const uint32_t nw = gridDim.x * (blockDim.x >> 5);
+    if (lane == 0) ps.qn[warp] = 0;
+    if (lane < PT_ROWS / 32) ps.hit[warp][lane] = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) best[lane * 4 + k] = 0;
+    __syncwarp();
+    // entry e of row (found by binary search in the tile's slice) offers the value of u
+    auto apply = [&](uint32_t e, uint32_t u, uint32_t rows) {
+        const uint32_t row = tile_row_of(rp, rows, e);
+        atomicMax(&best[row], pull_offer<SYNC>(d, u, p_in));
+        atomicOr(&ps.hit[warp][row >> 5], 1u << (row & 31u));
+    };
+    for (uint32_t t = blockIdx.x * (blockDim.x >> 5) + warp; t < ntiles; t += nw) {
+        const uint32_t r0 = t * PT_ROWS, rows = min((uint32_t)PT_ROWS, n - r0);
+        if (d.comp) { // a tile inside one finished graph holds no changed vertex
+            const uint32_t c0 = __ldg(d.comp + r0), c1 = __ldg(d.comp + r0 + rows - 1);
+            if (c0 == c1 && !*(volatile uint32_t *)&d.cs[c0].active) continue;
+        }
+        for (uint32_t i = lane; i <= rows; i += 32) rp[i] = __ldg(rowptr + r0 + i);
+        __syncwarp();
+        const uint32_t E0 = rp[0], E1 = rp[rows];
+        for (uint32_t cs = E0 & ~3u; cs < E1; cs += 32 * 4 * PT_UNROLL) {
+            uint4 w[PT_UNROLL];
+#pragma unroll
+            for (int j = 0; j < PT_UNROLL; ++j) {
+                const uint32_t idx = cs + (j * 32 + lane) * 4;
+                w[j] = idx < E1 ? __ldg(reinterpret_cast<const uint4 *>(colidx + idx)) : make_uint4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int j = 0; j < PT_UNROLL; ++j) {
+                const uint32_t ebase = cs + (j * 32 + lane) * 4;
+                const uint32_t c4[4] = {w[j].x, w[j].y, w[j].z, w[j].w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t e = ebase + k, u = c4[k] & 0x7FFFFFFFu;
+                    if (e < E0 || e >= E1) continue;
+                    // (a plain load: the grid barrier before the round's pull is an acquire, so no
+                    // line of an earlier round's bits is left in L1)
+                    if (!((cb[u >> 5] >> (u & 31u)) & 1u)) continue;
+                    ++hits;
+                    const uint32_t q = atomicAdd(&ps.qn[warp], 1u);
+                    if (q < PT_Q) {
+                        ps.qe[warp][q] = e;
+                        ps.qu[warp][q] = u;
+                    } else {
+                        apply(e, u, rows);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        {
+            const uint32_t nq = min(ps.qn[warp], PT_Q);
+            for (uint32_t i = lane; i < nq; i += 32) apply(ps.qe[warp][i], ps.qu[warp][i], rows);
+            __syncwarp();
+            if (lane == 0) ps.qn[warp] = 0;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t row = lane * 4 + k, w = r0 + row;
+            const bool in = row < rows;
+            const bool hit = in && ((ps.hit[warp][row >> 5] >> (row & 31u)) & 1u);
+            const uint32_t b = in ? best[row] : 0u;
+            if (in) best[row] = 0;
+            uint32_t old = 0;
+            bool raised = false;
+            uint64_t len = 0;
+            if (hit) {
+                len = rp[row + 1] - rp[row];
+                prow += 1;
+                if (track) relax += len;
+                old = *(volatile uint32_t *)(d.mval + w);
+                raised = b > old;
+                if (raised) {
+                    d.mval[w] = b;
+                    if (SYNC) *rec_snap(d.rec + w, p_out) = b;
+                    atomicOr(rec_flags(d.rec + w), CB(p_out));
+                    if (b == w + 1) atomicMin(&d.ctl->self_seen.v, w); // w reaches itself
+                    if (old == 0 && d.stale) atomicOr(d.stale + (w >> 5), 1u << (w & 31u));
+                }
+            }
+            if (d.comp) { // batched: per graph, the change and the frontier rows' lengths
+                const uint32_t c = hit ? __ldg(d.comp + w) : 0xFFFFFFFFu;
+                if (raised && *(volatile uint32_t *)&d.cs[c].last_change < rr) atomicMax(&d.cs[c].last_change, rr);
+                const unsigned same = __match_any_sync(0xFFFFFFFFu, c);
+                const unsigned lo = __reduce_add_sync(same, (unsigned)(len & 0xFFFFu));
+                const unsigned hi = __reduce_add_sync(same, (unsigned)(len >> 16));
+                const unsigned long long sum = (unsigned long long)lo + ((unsigned long long)hi << 16);
+                if (c != 0xFFFFFFFFu && lane == (unsigned)(__ffs(same) - 1) && sum)
+                    atomicAdd((unsigned long long *)&d.cs[c].relax, sum);
+            }
+            stage_append<3>(st, 1, raised, w, dst, ctr);
+            stage_append<3>(st, 2, raised && old == 0, w, dst, ctr);
+        }
+        __syncwarp();
+        if (lane < PT_ROWS / 32) ps.hit[warp][lane] = 0;
+        __syncwarp();
+    }
+    if (!track) relax += hits;
+}
+
+// after a pull round: its list's bits, list flags and (SYNC) snapshots back to zero
+template <bool SYNC>
+__device__ __forceinline__ void pull_cleanup(const Dev &d, const uint32_t *__restrict__ list, uint32_t nl, uint32_t q)
+{
+    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+    uint32_t *cb = pick3(q, d.cbit);
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += nthreads) {
+        const uint32_t u = __ldg(list + i);
+        if (SYNC) *rec_snap(d.rec + u, q) = 0;
+        atomicAnd(rec_flags(d.rec + u), ~CB(q));
+        cb[u >> 5] = 0; // every bit set in cbit[q] belongs to this list
+    }
+}
 
 // ------------------------------------------------- self-map test, elimination --
 //
@@ -1027,7 +1187,9 @@ __device__ __forceinline__ void check_phase(const Dev &d, Handles hd, bool work 
 
 __global__ void __launch_bounds__(256) k_check(const Dev d, Handles hd) { check_phase(d, hd); }
 
-template <bool SYNC>
+// PULL: the variant with pull rounds (launched when some round may pull; the push-only
+// variant keeps the register budget of the push path free of the pull path's needs)
+template <bool SYNC, bool PULL>
 __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const Dev d, Handles hd)
 {
     __shared__ uint32_t s_stage[8][3 * SB_ENTRIES];
@@ -1037,6 +1199,7 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
     __shared__ uint32_t *s_dst[3][2];
     __shared__ unsigned int *s_ctr[3];
     __shared__ uint32_t s_vals[4]; // after each barrier: |list|, |flist| of the round, self_seen, stop_req
+    __shared__ typename std::conditional<PULL, PullSmem, NoPullSmem>::type s_pull;
     Ctl *ctl = d.ctl;
     volatile Ctl *vc = ctl;
     const unsigned lane = lane_id();
@@ -1074,6 +1237,9 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
     // synchronous schedule; a single-graph asynchronous run counts its pushes instead
     const bool track = SYNC || d.comp;
     const bool local = !SYNC && !d.comp;
+    const uint32_t pull_min = (PULL && d.cbit[0]) ? vc->pull_min : 0u;
+    uint32_t pulled = 0; // > 0: the last round pulled, over a list of that many vertices
+    unsigned long long prow = 0; // frontier rows of pull rounds
     while (nl && status == ST_OK) {
         const uint32_t rr = r + 1; // this round
         const uint32_t p_in = (rr - 1) % 3, p_out = rr % 3, p_free = (rr + 1) % 3;
@@ -1081,7 +1247,10 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
             vc->lcnt[p_free].v = 0;
             vc->fcnt[p_free].v = 0;
         }
+        // the list the round before pulled over (list[p_free], which nothing reads any more)
+        if (PULL && pulled) pull_cleanup<SYNC>(d, pick3(p_free, d.list), pulled, p_free);
         const bool first = rr == 1; // round 1 from the accepting vertices (frontier start only)
+        const bool pull = PULL && !first && pull_min && nl >= pull_min;
         const uint32_t *__restrict__ list = first ? d.alist : pick3(p_in, d.list);
         uint32_t *const list_out = pick3(p_out, d.list);
         uint32_t *const flist_out = pick3(p_out, d.flist);
@@ -1111,9 +1280,22 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
         // together); their (vertex, reader) pairs are spread evenly over the block's
         // threads, RC_P pairs per thread per step with all their loads and atomics
         // in flight before any result is used
-        // every block takes an even contiguous share of the list
+        // every block takes an even contiguous share of the list (a pull round: none)
         const uint64_t per = (nl + gridDim.x - 1) / gridDim.x;
-        const uint64_t beg = (uint64_t)blockIdx.x * per, end = min((uint64_t)nl, beg + per);
+        const uint64_t beg = (uint64_t)blockIdx.x * per, end = pull ? beg : min((uint64_t)nl, beg + per);
+        if constexpr (PULL) if (pull) { // the list's bits, then (once every block has set its share) the pull itself
+            uint32_t *cb = pick3(p_in, d.cbit);
+            const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+            for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += nthreads) {
+                const uint32_t u = __ldg(list + i);
+                atomicOr(cb + (u >> 5), 1u << (u & 31u));
+            }
+            if (!grid_barrier(ctl)) {
+                status = ST_TIMEOUT;
+                break;
+            }
+            pull_round<SYNC>(d, rr, p_in, p_out, s_pull, st, dst, ctr, relax, prow);
+        }
         // asynchronous single graph: once its share of the list is done, the block pushes again
         // the live values of the vertices it listed itself in this round (recorded in s_loc), up
         // to LC_PASSES passes, so that values travel several edges per round.  These extra pushes
@@ -1242,6 +1424,7 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
             break;
         }
         r = rr;
+        pulled = pull ? nl : 0u;
         nf = s_vals[1];
         if (!first) frows += track ? nf : nl; // frontier rows, or the vertices that pushed
         nl = s_vals[0];                       // changed in this round
@@ -1254,7 +1437,9 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
     }
     // the last round's frontier: clear its flags, count its relaxations
     if (r > 1 && track) relax += clear_frontier(pick3(r % 3, d.flist), nf, r % 3, d.rec, d.rowptr, d);
+    if (PULL && pulled) pull_cleanup<SYNC>(d, pick3((r + 2) % 3, d.list), pulled, (r + 2) % 3); // list[p_in] of round r
     block_add_u64(relax, (unsigned long long *)&ctl->relax.v);
+    block_add_u64(track ? prow : 0ull, (unsigned long long *)&ctl->frontier_rows.v);
     if (threadIdx.x == 0 && status != ST_OK) vc->status = status; // any block that stopped early
     if (lead) {
         vc->k = r;
@@ -1265,260 +1450,6 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
     // In a CUDA graph the self-map test and the elimination follow in this launch (one kernel
     // boundary less per outer iteration); every block's appends were flushed before the last
     // barrier.  A block whose barrier gave up skips the work but still takes its ticket.
-    if (vc->use_graph) check_phase(d, hd, status == ST_OK);
-}
-
-// ------------------------------------------------- worklist fix-point --
-//
-// The asynchronous schedule of a single graph without rounds (k_queue): after round 1 (the
-// dense round, or for the frontier start the accepting vertices themselves) every vertex that
-// got a value is queued; a consumer takes a queued vertex u, reads its live value, offers
-// max(u + 1 if u accepting, map(u)) to its readers with atomicMax, and queues each reader it
-// raises that is not queued already.  Values only grow and each is a real accepting successor,
-// so the loop ends at the unique least fix-point, the one the synchronous rounds reach
-// (Section 2: propagation to the fix-point); there is no grid-wide step between propagation
-// steps, so no thread waits for the slowest one of a round.
-//
-// Lost updates are excluded per vertex: a producer raises map(w), then tests-and-sets w's
-// in-queue bit; a consumer clears the bit, then reads map(u).  A full fence sits between the
-// two accesses on both sides, so either the consumer reads the raised value or the producer
-// sees the bit cleared and queues w again.
-//
-// The loop ends when every reserved position has been processed (done == tail, read in that
-// order): only processing creates items, so nothing can be queued afterwards.  Consumers
-// reserve positions ahead of the producers (each warp keeps one reservation per lane) and wait
-// for them with a growing back-off; every wait ends by the run's time limit.
-constexpr uint32_t Q_SPIN_LIMIT = 1u << 22; // a producer's wait for its cell (never long: see QState)
-constexpr uint32_t Q_BACKOFF_MAX_NS = 2048;
-
-__device__ __forceinline__ uint64_t q_load(const uint64_t *c)
-{
-    return *(const volatile uint64_t *)c;
-}
-__device__ __forceinline__ void q_store(uint64_t *c, uint64_t x) { *(volatile uint64_t *)c = x; }
-
-// queue w where flag holds (every lane of the warp calls it): one reservation per warp; false
-// in every lane if a cell stayed taken past the spin limit (the drain then stops)
-__device__ __forceinline__ bool q_push(const Dev &d, bool flag, uint32_t w)
-{
-    const unsigned mask = __ballot_sync(0xFFFFFFFFu, flag);
-    if (!mask) return true;
-    const unsigned lane = lane_id(), leader = __ffs(mask) - 1;
-    unsigned long long base = 0;
-    if (lane == leader) base = atomicAdd((unsigned long long *)&d.qs->tail.v, (unsigned long long)__popc(mask));
-    base = __shfl_sync(0xFFFFFFFFu, base, leader);
-    bool ok = true;
-    if (flag) {
-        const uint64_t p = base + __popc(mask & ((1u << lane) - 1u));
-        uint64_t *cell = d.qcell + p % d.qcap;
-        for (uint32_t spin = 0; (uint32_t)(q_load(cell) >> 32) != (uint32_t)p; ++spin) {
-            if (spin > Q_SPIN_LIMIT) {
-                ok = false;
-                break;
-            }
-            __nanosleep(64);
-        }
-        if (ok) q_store(cell, ((uint64_t)(uint32_t)(p + 1) << 32) | w);
-    }
-    return __all_sync(0xFFFFFFFFu, ok);
-}
-
-// free the cells of the queue: cell i waits for position i (once per handle and after a drain
-// that stopped early)
-__global__ void k_queue_init(uint64_t *qcell, uint64_t qcap)
-{
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < qcap; i += stride)
-        qcell[i] = (uint64_t)(uint32_t)i << 32;
-}
-
-__global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_queue(const Dev d, Handles hd)
-{
-    Ctl *ctl = d.ctl;
-    volatile Ctl *vc = ctl;
-    QState *qs = d.qs;
-    const unsigned lane = lane_id();
-    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
-    const bool fstart = d.alist != nullptr;
-    const bool early = vc->early_exit != 0;
-    const uint64_t t0 = vc->t0, tmo = vc->timeout_ns;
-    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
-    const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t status = ST_OK;
-    // the queue is drained at this point: tail == done, head may have run ahead of them
-    const uint64_t T0 = *(volatile uint64_t *)&qs->tail.v;
-
-    // ---- round 1 and the first items
-    uint32_t nseed = 0;
-    const uint32_t *seed = nullptr;
-    if (fstart) {
-        // round 1 from the accepting vertices: reset the previous iteration's values first
-        default_stop(ctl, hd.outer);
-        const uint32_t tp = vc->tprev;
-        for (uint64_t i = gtid; i < tp; i += nthreads) d.mval[__ldg(d.touched + i)] = 0;
-        nseed = d.na;
-        seed = d.alist;
-    } else if (!(early && vc->self_seen.v != NONE)) { // (the dense round may have found a self-mapped vertex)
-        nseed = vc->lcnt[1].v; // vertices that got a value in the dense round
-        seed = d.list[1];
-    }
-    bool ok = true;
-    for (uint64_t base = gtid & ~31ull; base < nseed; base += nthreads) { // warp-uniform
-        const uint64_t i = base + lane;
-        uint32_t u = 0;
-        bool f = false;
-        if (i < nseed) {
-            u = __ldg(seed + i);
-            f = !fstart || acc_bit(d.acc, u); // (frontier start: eliminated vertices offer nothing)
-            if (f) atomicOr(d.inq + (u >> 5), 1u << (u & 31u));
-        }
-        ok &= q_push(d, f, u);
-    }
-    if (!ok) atomicExch(&qs->stop.v, Q_STOP_FAULT);
-    if (lead) *(volatile unsigned long long *)&qs->head.v = T0; // consumers start at the first item
-    if (!grid_barrier(ctl)) status = ST_TIMEOUT;
-
-    // ---- the drain: one reservation per lane; ready lanes' items are processed by the whole warp
-    unsigned long long relax = 0, items = 0;
-    bool has = false;
-    uint64_t mypos = 0;
-    uint32_t backoff = 0, iter = 0;
-    while (status == ST_OK) {
-        const unsigned need = __ballot_sync(0xFFFFFFFFu, !has);
-        if (need) {
-            unsigned long long b = 0;
-            if (lane == 0) b = atomicAdd((unsigned long long *)&qs->head.v, (unsigned long long)__popc(need));
-            b = __shfl_sync(0xFFFFFFFFu, b, 0);
-            if (!has) {
-                mypos = b + __popc(need & ((1u << lane) - 1u));
-                has = true;
-            }
-        }
-        uint64_t *cell = d.qcell + mypos % d.qcap;
-        const uint64_t cv = q_load(cell);
-        const bool ready = (uint32_t)(cv >> 32) == (uint32_t)(mypos + 1);
-        const uint32_t u = (uint32_t)cv;
-        if (ready) {
-            q_store(cell, (uint64_t)(uint32_t)(mypos + d.qcap) << 32); // free for the next lap
-            has = false;
-        }
-        const unsigned rmask = __ballot_sync(0xFFFFFFFFu, ready);
-        ++iter;
-        if (!rmask) { // nothing here yet: the end of the drain, a stop, or wait
-            uint32_t fin = 0;
-            if (lane == 0) {
-                const uint64_t D = *(volatile unsigned long long *)&qs->done.v;
-                const uint64_t T = *(volatile unsigned long long *)&qs->tail.v;
-                fin = D == T ? 4u : 0u;
-                uint32_t stp = *(volatile uint32_t *)&qs->stop.v;
-                if (!fin && !stp && (iter & 15u) == 0 && global_ns() - t0 > tmo) {
-                    atomicExch(&qs->stop.v, Q_STOP_TIMEOUT);
-                    stp = Q_STOP_TIMEOUT;
-                }
-                fin |= stp;
-            }
-            if (__shfl_sync(0xFFFFFFFFu, fin, 0)) break;
-            backoff = backoff ? min(backoff * 2, Q_BACKOFF_MAX_NS) : 64;
-            __nanosleep(backoff);
-            continue;
-        }
-        backoff = 0;
-        if ((iter & 15u) == 0) { // a stop is rare: look (and at the clock) every 16 busy iterations
-            uint32_t stp = 0;
-            if (lane == 0) {
-                stp = *(volatile uint32_t *)&qs->stop.v;
-                if (!stp && global_ns() - t0 > tmo) {
-                    atomicExch(&qs->stop.v, Q_STOP_TIMEOUT);
-                    stp = Q_STOP_TIMEOUT;
-                }
-            }
-            if (__shfl_sync(0xFFFFFFFFu, stp, 0)) break;
-        }
-        // take the items: clear their in-queue bits, then (after a full fence) read their values
-        if (ready) atomicAnd(d.inq + (u >> 5), ~(1u << (u & 31u)));
-        __threadfence();
-        uint32_t o = 0, rb = 0, len = 0;
-        if (ready) {
-            const uint32_t x = *(volatile uint32_t *)(d.mval + u);
-            o = acc_bit(d.acc, u) ? max(x, u + 1) : x;
-            rb = __ldg(d.rrowptr + u);
-            len = o ? __ldg(d.rrowptr + u + 1) - rb : 0u;
-        }
-        const uint32_t incl = warp_inclusive_scan(len);
-        const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        const uint32_t excl = incl - len;
-        if (lane == 0) {
-            relax += total; // pushes
-            items += __popc(rmask);
-        }
-        bool okp = true;
-        for (uint32_t p0 = 0; p0 < total; p0 += 32) {
-            const uint32_t p = p0 + lane;
-            // the owner of pair p: the first lane whose inclusive sum exceeds p
-            uint32_t j = 0;
-#pragma unroll
-            for (uint32_t st = 16; st >= 1; st >>= 1)
-                if (__shfl_sync(0xFFFFFFFFu, incl, j + st - 1) <= p) j += st;
-            const uint32_t ob = __shfl_sync(0xFFFFFFFFu, o, j & 31u);
-            const uint32_t jj = __shfl_sync(0xFFFFFFFFu, rb, j & 31u) + (p - __shfl_sync(0xFFFFFFFFu, excl, j & 31u));
-            const bool act = p < total;
-            uint32_t w = 0, old = 0xFFFFFFFFu;
-            if (act) {
-                w = __ldg(d.rcol + jj);
-                old = atomicMax(d.mval + w, ob);
-            }
-            const bool raised = act && ob > old;
-            const bool fresh = raised && old == 0; // w got its first value of this outer iteration
-            {
-                const unsigned fm = __ballot_sync(0xFFFFFFFFu, fresh);
-                if (fm) {
-                    const unsigned leader = __ffs(fm) - 1;
-                    unsigned at = 0;
-                    if (lane == leader) at = atomicAdd(&ctl->tcnt.v, (unsigned)__popc(fm));
-                    at = __shfl_sync(0xFFFFFFFFu, at, leader);
-                    if (fresh) {
-                        d.touched[at + __popc(fm & ((1u << lane) - 1u))] = w;
-                        if (d.stale) atomicOr(d.stale + (w >> 5), 1u << (w & 31u)); // the next dense round resets it
-                    }
-                }
-            }
-            if (raised && ob == w + 1) { // w reaches itself: an accepting cycle
-                atomicMin(&ctl->self_seen.v, w);
-                if (early) atomicExch(&qs->stop.v, Q_STOP_EARLY);
-            }
-            const unsigned rm = __ballot_sync(0xFFFFFFFFu, raised);
-            if (rm) __threadfence(); // the raise is visible before the in-queue bit is tested
-            const bool enq = raised && test_and_set(d.inq, w);
-            okp &= q_push(d, enq, w);
-        }
-        if (!okp && lane == 0) atomicExch(&qs->stop.v, Q_STOP_FAULT);
-        // the items are processed (their readers queued): count them
-        __syncwarp();
-        if (lane == 0) {
-            __threadfence();
-            atomicAdd((unsigned long long *)&qs->done.v, (unsigned long long)__popc(rmask));
-        }
-    }
-    // a drain that stopped early leaves appends in flight in other blocks: wait for every block
-    // before the touched vertices are examined
-    __shared__ uint32_t s_stop;
-    __syncthreads();
-    if (threadIdx.x == 0) s_stop = *(volatile uint32_t *)&qs->stop.v;
-    __syncthreads();
-    const uint32_t stp = s_stop;
-    if (stp && !grid_barrier(ctl)) status = ST_TIMEOUT;
-    if (stp == Q_STOP_TIMEOUT || stp == Q_STOP_FAULT) status = ST_TIMEOUT;
-    block_add_u64(relax, (unsigned long long *)&ctl->relax.v);
-    if (lane == 0 && items) atomicAdd((unsigned long long *)&ctl->frontier_rows.v, items);
-    if (threadIdx.x == 0 && status != ST_OK) vc->status = status;
-    if (lead) {
-        // one pass over the queue counts as one round after round 1 (fewer than the synchronous
-        // rounds, which need at least one more round whenever round 1 changed something)
-        vc->k = (nseed == 0 && !fstart) ? 1u : (vc->tcnt.v ? 2u : 1u);
-        if (stp == Q_STOP_EARLY) vc->early_hit = 1;
-        phase_end(vc, &vc->ph_rounds);
-        __threadfence();
-    }
     if (vc->use_graph) check_phase(d, hd, status == ST_OK);
 }
 

@@ -95,3 +95,49 @@ def test_submit_refuses_device_inputs(pkg):
         rc = lib.map_submit(sv.handle, g.n, d.data_ptr(), g.colidx.ctypes.data, pkg.pack_bits(g.acc).ctypes.data,
                             None, ctypes.byref(jid))
         assert rc == pkg.MAP_ERR_ARG
+
+
+def test_injected_allocation_failure_fails_only_that_job(pkg, monkeypatch):
+    """Host-side fault injection (MAPGPU_INJECT_OOM): the 3rd device allocation of job 4's set-up
+    fails.  That job reports MAP_ERR_OOM at map_poll; the jobs before, beside and after it still get
+    the oracle's results, and the server keeps serving (its memory accounting is intact)."""
+    monkeypatch.setenv("MAPGPU_INJECT_OOM", "4:3,9:1")
+    gs = _jobs()[18:]  # two tiny graphs, both 16k workloads, the layered graphs, the product
+    want = [oracle.run_graph(g) for g in gs]
+    with pkg.Server(slots=3) as sv:
+        ids = [sv.submit(g.n, g.rowptr, g.colidx if g.m else None, pkg.pack_bits(g.acc), sched=s)
+               for s in (0, 1) for g in gs]
+        assert ids == list(range(1, len(ids) + 1))
+        done = {}
+        deadline = time.time() + 120
+        while len(done) < len(ids) and time.time() < deadline:
+            for k, jid in enumerate(ids):
+                if jid in done:
+                    continue
+                try:
+                    got = sv.poll(jid)
+                except pkg.MapError as e:
+                    done[jid] = e
+                    continue
+                if got is not None:
+                    done[jid] = got
+            time.sleep(0.001)
+        assert len(done) == len(ids)
+        for k, jid in enumerate(ids):
+            g, w = gs[k % len(gs)], want[k % len(gs)]
+            if jid in (4, 9):
+                assert isinstance(done[jid], pkg.MapError) and done[jid].code == pkg.MAP_ERR_OOM
+                assert "injected" in str(done[jid])
+                continue
+            r, mp = done[jid]
+            assert (r.verdict, r.witness, r.outer) == (w.verdict, w.witness, w.outer), g.name
+            assert np.array_equal(mp, w.map), g.name
+            assert r.queue_ms >= 0 and r.setup_ms > 0 and r.run_ms > 0
+        # still serving after the failures
+        g = gs[2]
+        jid = sv.submit(g.n, g.rowptr, g.colidx, pkg.pack_bits(g.acc))
+        got = None
+        while got is None:
+            got = sv.poll(jid)
+            time.sleep(0.001)
+        assert np.array_equal(got[1], want[2].map)
