@@ -241,6 +241,8 @@ def configs_leg(pkg, np, torch, stream, peak, steps=10):
         out = {}
         try:
             for sched, name in ((1, "async"), (0, "sync")):
+                # this graph's run choices for this schedule, by measurement (the start included)
+                out[f"autotune_{name}"] = pkg.map_autotune(h, sched)
                 for _ in range(3):
                     r = pkg.map_run(h, sched=sched)
                 torch.cuda.synchronize()
@@ -412,6 +414,7 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="override vertex count (smaller runs, not the bench line)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched leg (256 graphs)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg (Poisson arrivals)")
+    ap.add_argument("--no-tune", action="store_true", help="skip map_autotune on the bench graph (library defaults)")
     ap.add_argument("--start", default="dense", choices=["dense", "frontier"],
                     help="round 1 of every outer iteration: the dense round over the whole matrix (default, the "
                          "headline) or MAP_FLAG_FRONTIER_START on every step (profiling that path; no dense roofline)")
@@ -449,8 +452,14 @@ def main():
     ab = torch.from_numpy(pkg.pack_bits(g.acc).view(np.int32)).cuda()
     out = torch.empty(g.n, dtype=torch.int32, device="cuda")
     h = pkg.map_create(g.n, rp, ci, ab, stream)
+    # the handle's run choices by measurement on this graph (pull threshold, block-local passes,
+    # one-block rounds, launch shapes, dense-round loads in flight); the start stays the one asked
+    # for (the headline streams the whole matrix in every outer iteration)
+    t_tune = time.perf_counter()
+    tune = pkg.map_autotune(h, args.sched) if not args.no_tune else None
+    t_tune = time.perf_counter() - t_tune
 
-    start_flags = pkg.MAP_FLAG_FRONTIER_START if args.start == "frontier" else 0
+    start_flags = pkg.MAP_FLAG_FRONTIER_START if args.start == "frontier" else pkg.MAP_FLAG_DENSE_START
 
     def step(flags=0):
         return pkg.map_run(h, sched=args.sched, flags=flags | start_flags, map_out=out)
@@ -506,13 +515,17 @@ def main():
     # small.  Reported beside the headline as time and pushes per run: it does not examine every
     # edge in every outer iteration, so m x outer / time would not be an edge rate.
     fs = pkg.MAP_FLAG_FRONTIER_START
+
+    def fstep():
+        return pkg.map_run(h, sched=args.sched, flags=fs, map_out=out)
+
     for _ in range(3):
-        step(fs)
+        fstep()
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
     e0.record(stream)
-    fres = [step(fs) for _ in range(args.steps)]
+    fres = [fstep() for _ in range(args.steps)]
     e1.record(stream)
     torch.cuda.synchronize()
     if ws > 1:
@@ -629,6 +642,7 @@ def main():
                     "placement": "replicas, one per GPU" if ws > 1 else "single GPU"},
             "roofline": roofline, "run_roofline": run_roofline, "phases": phases, "e2e": e2e,
             "other_schedule": other_line, "frontier_start": frontier_line,
+            "autotune": dict(tune, seconds=t_tune) if tune else None,
             "gpu_launches": sum(r.launches for r in results),
             "clocks": clk.summary()}
     pkg.map_destroy(h)

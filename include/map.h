@@ -274,9 +274,16 @@ MAP_API int map_server_destroy(map_server *sv);
  *     pushing through the readers: never, or from 1/256, 1/64, 1/32, 1/16, 1/8
  *     or 1/4 of the vertices (MAP_FLAG_PUSH / MAP_FLAG_PULL still force
  *     either);
- *  2. the launch shapes: resident blocks per SM of the dense-round kernel and
- *     of the fix-point kernel (up to each kernel's occupancy limit);
- *  3. the start of every outer iteration: the dense round or the frontier
+ *  2. (MAP_SCHED_ASYNC, single graphs) how many times a block pushes again, in
+ *     the same round, the vertices it raised itself (0, 1, 2, 4 or 8; by
+ *     default 1), so that values travel several edges per round;
+ *  3. up to which list size one block runs a round alone, with block barriers
+ *     instead of the grid-wide one (never, 64, 256 or 1024 listed vertices;
+ *     by default 256);
+ *  4. the launch shapes: resident blocks per SM of the dense-round kernel and
+ *     of the fix-point kernel (up to each kernel's occupancy limit), and the
+ *     dense round's 16-byte loads in flight per lane (2, 4 or 8);
+ *  5. the start of every outer iteration: the dense round or the frontier
  *     start (MAP_FLAG_DENSE_START / MAP_FLAG_FRONTIER_START still force either).
  * It takes about thirty runs; results are unaffected (none of these
  * choices changes any map vector, verdict, witness or outer count, nor the
@@ -294,6 +301,11 @@ typedef struct {
     double pull_share;             /* rounds over lists of at least this share of the vertices pull (0: never) */
     double pull_ms;                /* run time with that share (0: not timed) */
     double push_only_ms;           /* run time when no round pulls (0: not timed) */
+    uint32_t solo_max;             /* rounds over at most this many listed vertices run in one block (0: never) */
+    uint32_t dense_unroll;         /* the dense round's 16-byte loads in flight per lane */
+    double solo_ms;                /* run time with that size (0: not timed) */
+    uint32_t local_passes;         /* block-local passes per round of asynchronous runs */
+    uint32_t reserved;
 } map_tune_result;
 MAP_API int map_autotune(map_graph *g, uint32_t sched, map_tune_result *out);
 
@@ -407,7 +419,7 @@ MAP_API int map_graph_info(const map_graph *g, uint32_t *n, uint64_t *m);
  */
 #define MAP_STATIC_MAX_N 65536u
 #define MAP_STATIC_MAX_M 524288u
-#define MAP_STATIC_SCRATCH_BYTES 10778112u
+#define MAP_STATIC_SCRATCH_BYTES 10778368u
 MAP_API int map_run_static(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const uint32_t *acc_bits,
                            const map_opts *opts, map_result *res, uint32_t *map_out, void *cuda_stream);
 

@@ -99,6 +99,11 @@ class TuneResult(ctypes.Structure):
         ("pull_share", ctypes.c_double),
         ("pull_ms", ctypes.c_double),
         ("push_only_ms", ctypes.c_double),
+        ("solo_max", ctypes.c_uint32),
+        ("dense_unroll", ctypes.c_uint32),
+        ("solo_ms", ctypes.c_double),
+        ("local_passes", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
     ]
 
 
@@ -113,7 +118,8 @@ def map_autotune(handle, sched: int = MAP_SCHED_SYNC) -> dict:
             "dense_ms": t.dense_ms, "rounds_ms": t.rounds_ms, "trials": t.trials,
             "frontier_start": bool(t.frontier_start), "dense_start_ms": t.dense_start_ms,
             "frontier_start_ms": t.frontier_start_ms, "pull_share": t.pull_share, "pull_ms": t.pull_ms,
-            "push_only_ms": t.push_only_ms}
+            "push_only_ms": t.push_only_ms, "solo_max": t.solo_max, "solo_ms": t.solo_ms,
+            "dense_unroll": t.dense_unroll, "local_passes": t.local_passes}
 
 
 def map_lasso(handle, witness: int, init: int = MAP_NONE, cap: int = 1 << 20):

@@ -149,6 +149,19 @@ uint32_t pull_min_for(uint32_t n, double frac)
 
 // resident 256-thread blocks per SM that every variant of the fix-point kernel supports (its
 // launch is cooperative, so the grid may not exceed it)
+int dense_occupancy()
+{
+    int occ = 1 << 30, o = 0;
+    for (const void *k : {(const void *)mapk::k_dense<2>, (const void *)mapk::k_dense<4>, (const void *)mapk::k_dense<8>}) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, mapk::DT_THREADS, mapk::DT_SMEM) != cudaSuccess) {
+            cudaGetLastError();
+            o = 1;
+        }
+        occ = std::min(occ, o);
+    }
+    return std::max(1, occ);
+}
+
 int rounds_occupancy()
 {
     int occ = 1 << 30, o = 0;
@@ -201,6 +214,9 @@ struct map_graph {
     uint32_t *stale = nullptr; // words: vertices whose mval the next dense round must reset
     uint32_t *cbit = nullptr;  // 3 bitmaps of `words` (+ slack): the list a pull round reads, by round mod 3
     uint32_t pull_min = 0;     // rounds over lists of at least this many vertices pull (0: never)
+    uint32_t solo_max = 256;   // rounds over at most this many listed vertices run in one block (0: never)
+    int dense_unroll = 4;      // 128-bit loads per lane in flight in the dense round (2, 4 or 8)
+    uint32_t lc_passes = 1;    // asynchronous single graphs: block-local passes per round
     uint32_t *ids = nullptr; // reduced graphs: the original id of each vertex (else NULL: identity)
     uint32_t rows = 0;       // rows expanded so far (growing graphs); the rest are empty
     bool dirty = false; // a run stopped early: per-round state may be stale
@@ -359,7 +375,10 @@ mapk::Dev dev_of(const map_graph *g)
 
 int launch_dense(map_graph *g, cudaStream_t s, mapk::Handles hd)
 {
-    mapk::k_dense<<<g->dense_grid, mapk::DT_THREADS, mapk::DT_SMEM, s>>>(dev_of(g), hd);
+    const mapk::Dev d = dev_of(g);
+    if (g->dense_unroll == 2) mapk::k_dense<2><<<g->dense_grid, mapk::DT_THREADS, mapk::DT_SMEM, s>>>(d, hd);
+    else if (g->dense_unroll == 8) mapk::k_dense<8><<<g->dense_grid, mapk::DT_THREADS, mapk::DT_SMEM, s>>>(d, hd);
+    else mapk::k_dense<4><<<g->dense_grid, mapk::DT_THREADS, mapk::DT_SMEM, s>>>(d, hd);
     CK(cudaGetLastError());
     return MAP_OK;
 }
@@ -561,9 +580,7 @@ int create_graph(uint32_t n, uint64_t m, cudaStream_t s, const char *who, Upload
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev);
     if (g->sms <= 0) g->sms = 1;
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mapk::k_dense, mapk::DT_THREADS, mapk::DT_SMEM);
-    if (occ <= 0) occ = 1;
+    const int occ = dense_occupancy();
     const uint64_t ntiles = ((uint64_t)n + mapk::WT_ROWS - 1) / mapk::WT_ROWS;
     g->dense_grid = (int)std::min<uint64_t>((ntiles + mapk::WT_WARPS - 1) / mapk::WT_WARPS, (uint64_t)g->sms * occ);
     int occ_r = rounds_occupancy();
@@ -579,6 +596,8 @@ int create_graph(uint32_t n, uint64_t m, cudaStream_t s, const char *who, Upload
     g->check_grid = (int)std::min<uint64_t>(((uint64_t)n + 255) / 256, (uint64_t)g->sms * 4);
     g->hist_cap = 1u << 16;
     g->pull_min = pull_min_for(n, default_pull_frac());
+    if (const char *e = getenv("MAPGPU_SOLO_MAX")) g->solo_max = (uint32_t)strtoul(e, nullptr, 10); // (default 256)
+    if (const char *e = getenv("MAPGPU_LC_PASSES")) g->lc_passes = (uint32_t)strtoul(e, nullptr, 10); // (default 1)
 
     auto alloc = [&](uint32_t **p, uint64_t words) -> int {
         if (t_inject_alloc > 0 && --t_inject_alloc == 0)
@@ -792,6 +811,9 @@ static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint
     init.witness.v = mapk::NONE;
     init.pull_min = (opts.flags & MAP_FLAG_PULL) ? 1u : (opts.flags & MAP_FLAG_PUSH) ? 0u : g->pull_min;
     g->pull_on = init.pull_min != 0;
+    init.solo_max = g->solo_max;
+    init.lc_passes = g->lc_passes;
+    init.solo_fmax = 8 * g->solo_max; // (and at most this many frontier rows to clear)
 
     int rc = MAP_OK;
     float dense_ms = 0.f, round_ms = 0.f, check_ms = 0.f;
@@ -951,8 +973,7 @@ int map_autotune(map_graph *g, uint32_t sched, map_tune_result *out)
     g_err.clear();
     if (!g || !out) return fail(MAP_ERR_ARG, "map_autotune: NULL handle or result");
     if (sched > MAP_SCHED_ASYNC) return fail(MAP_ERR_ARG, "map_autotune: unknown schedule %u", sched);
-    int occ_d = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_d, mapk::k_dense, mapk::DT_THREADS, mapk::DT_SMEM));
+    const int occ_d = dense_occupancy();
     const int occ_r = rounds_occupancy();
     memset(out, 0, sizeof *out);
     map_result r;
@@ -993,6 +1014,43 @@ int map_autotune(map_graph *g, uint32_t sched, map_tune_result *out)
         g->pull_min = best_min;
         out->pull_ms = best;
     }
+    // 2. (asynchronous single graphs) block-local passes per round
+    if (g->nacc0 && sched == MAP_SCHED_ASYNC && !g->comp) {
+        const uint32_t passes[] = {0, 1, 2, 4, 8};
+        double best = 1e30;
+        uint32_t best_p = g->lc_passes;
+        for (uint32_t pz : passes) {
+            g->lc_passes = pz;
+            double t = 0;
+            if ((rc = whole_run(MAP_FLAG_DENSE_START, &t))) return rc;
+            if (t < best) {
+                best = t;
+                best_p = pz;
+            }
+        }
+        g->lc_passes = best_p;
+        out->local_passes = best_p;
+    } else {
+        out->local_passes = g->lc_passes;
+    }
+    // 3. up to which list size block 0 runs a round alone (0 = never)
+    if (g->nacc0) {
+        const uint32_t sizes[] = {0, 64, 256, 1024};
+        double best = 1e30;
+        uint32_t best_s = g->solo_max;
+        for (uint32_t sz : sizes) {
+            g->solo_max = sz;
+            double t = 0;
+            if ((rc = whole_run(MAP_FLAG_DENSE_START, &t))) return rc;
+            if (t < best) {
+                best = t;
+                best_s = sz;
+            }
+        }
+        g->solo_max = best_s;
+        out->solo_max = best_s;
+        out->solo_ms = best;
+    }
     map_opts o;
     memset(&o, 0, sizeof o);
     o.sched = sched;
@@ -1011,6 +1069,24 @@ int map_autotune(map_graph *g, uint32_t sched, map_tune_result *out)
             t_d = r.dense_ms;
             best_d = bps;
         }
+    }
+    // the dense round's loads in flight per lane, at that shape
+    {
+        double t_u = 1e30;
+        int best_u = g->dense_unroll;
+        set_shapes(g, best_d, cur_r);
+        for (int u : {2, 4, 8}) {
+            g->dense_unroll = u;
+            if ((rc = run_impl(g, &o, &r, nullptr)) != MAP_OK) return rc;
+            out->trials++;
+            if (r.dense_ms < t_u) {
+                t_u = r.dense_ms;
+                best_u = u;
+            }
+        }
+        g->dense_unroll = best_u;
+        out->dense_unroll = (uint32_t)best_u;
+        t_d = std::min(t_d, t_u);
     }
     for (uint32_t bps : cands) {
         if ((int)bps > occ_r) continue;
@@ -1640,9 +1716,7 @@ static int run_static_impl(uint32_t n, const uint32_t *rowptr, const uint32_t *c
     int dev = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&g.sms, cudaDevAttrMultiProcessorCount, dev));
-    int occ = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mapk::k_dense, mapk::DT_THREADS, mapk::DT_SMEM));
-    occ = std::max(occ, 1);
+    const int occ = dense_occupancy();
     const int occ_r = rounds_occupancy();
     const uint64_t ntiles = ((uint64_t)n + mapk::WT_ROWS - 1) / mapk::WT_ROWS;
     g.dense_grid = (int)std::min<uint64_t>((ntiles + mapk::WT_WARPS - 1) / mapk::WT_WARPS, (uint64_t)g.sms * occ);
@@ -1710,6 +1784,7 @@ static int run_static_impl(uint32_t n, const uint32_t *rowptr, const uint32_t *c
     h.out = out_dev ? map_out : g.xbuf;
     h.use_graph = 0;
     h.early_exit = (opts.flags & MAP_FLAG_EARLY_EXIT) ? 1 : 0;
+    h.lc_passes = 1; // (pull rounds and one-block rounds stay off: their thresholds are zero)
     h.timeout_ns = (uint64_t)(opts.timeout_ms ? opts.timeout_ms : 120000u) * 1000000ull;
     h.witness.v = mapk::NONE;
     CK(cudaMemcpyAsync(ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, s));

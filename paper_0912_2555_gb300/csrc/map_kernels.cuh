@@ -77,6 +77,8 @@ struct Ctl {
     Cnt32 bar_gen;         // ... and generation
     Cnt32 stop_req;        // k_rounds: block 0 asks every block to stop after the next barrier
     Cnt32 self_seen;       // smallest vertex seen to become its own map value (NONE: none yet)
+    Cnt32 solo_gen;        // k_rounds: hand-backs of block 0 after rounds it ran alone
+    Cnt32 solo_beat;       // ... and the last round it ran alone (the waiting blocks' heartbeat)
     // fix-point loop
     uint32_t k;            // rounds completed in the current outer iteration
     // outer loop
@@ -101,7 +103,10 @@ struct Ctl {
     uint32_t early_hit;    // it did (the run's round state is then left dirty)
     uint32_t tprev;        // |touched| of the previous outer iteration (frontier start resets their values)
     uint32_t pull_min;     // a round whose list holds at least this many vertices pulls (0: never)
-    uint32_t pad[1];
+    uint32_t solo_max;     // a round over at most this many listed vertices (and at most solo_fmax
+    uint32_t solo_fmax;    //   frontier rows to clear) runs in block 0 alone (0: never)
+    uint32_t solo_r, solo_nl, solo_nf, solo_status; // block 0's state when it hands back
+    uint32_t lc_passes;    // asynchronous single graphs: block-local passes per round
     // %globaltimer stamps of the phases (ns), summed over the run: the end of the last phase
     // (t_mark), the dense rounds, the fix-point rounds, the self-map tests and eliminations.  Each
     // phase runs from the end of the one before it, so gaps between launches count to the next.
@@ -586,7 +591,8 @@ __global__ void k_run_begin(Ctl *c, Handles hd)
 constexpr int DT_THREADS = 256;
 constexpr int WT_WARPS = DT_THREADS / 32;
 constexpr int WT_ROWS = 128;
-constexpr int WT_UNROLL = 4;
+// 128-bit colidx loads per lane in flight: a template parameter of k_dense (2, 4 or 8;
+// map_autotune picks it per handle, 4 by default)
 constexpr uint32_t WT_Q = 64; // queued accepting-target entries per warp (more are applied on the spot)
 constexpr size_t DT_SMEM = 0; // static shared memory only
 
@@ -606,6 +612,7 @@ __device__ __forceinline__ uint32_t tile_row_of(const uint32_t *rp, uint32_t row
 #define MAPGPU_DENSE_MIN_BLOCKS 6 // resident blocks per SM the register budget is sized for (measured best)
 #endif
 
+template <int WT_UNROLL>
 __global__ void __launch_bounds__(DT_THREADS, MAPGPU_DENSE_MIN_BLOCKS) k_dense(const Dev d, Handles hd)
 {
     // per warp, two buffers: the tile's rowptr slice [0, WT_ROWS], its stale words at WT_ROWS + 4
@@ -825,13 +832,13 @@ __global__ void k_acc_list(uint32_t n, const uint32_t *__restrict__ acc0, uint32
 __device__ __forceinline__ unsigned long long clear_frontier(const uint32_t *__restrict__ flist, uint32_t nf,
                                                              uint32_t p, uint4 *rec,
                                                              const uint32_t *__restrict__ rowptr,
-                                                             const Dev &d)
+                                                             const Dev &d, uint32_t nb, uint32_t bid)
 {
     unsigned long long relax = 0;
-    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t nthreads = (uint64_t)nb * blockDim.x; // nb blocks share the work (bid: this one)
     // warp-uniform loop: in batched runs the lanes of a warp add their row
     // lengths per graph (one atomic per graph present in the warp)
-    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < nf; base += nthreads) {
+    for (uint64_t base = (uint64_t)bid * blockDim.x + (threadIdx.x & ~31u); base < nf; base += nthreads) {
         const uint64_t i = base + lane_id();
         unsigned long long len = 0;
         uint32_t w = 0;
@@ -941,13 +948,10 @@ __device__ __forceinline__ bool grid_barrier(Ctl *ctl, uint32_t p = 3, uint32_t 
 constexpr int RC_E = MAPGPU_RC_E;
 constexpr int RC_ENTRIES = 256 * RC_E; // per block and chunk
 constexpr int RC_P = MAPGPU_RC_P;
-#ifndef MAPGPU_LC_PASSES
-#define MAPGPU_LC_PASSES 1 // asynchronous schedule: block-local passes over a block's own raised vertices per round
-                           // (measured on the 2^26 layered graph, ms per run for 0 / 1 / 2 / 4 / 8 passes:
-                           // 18.2 / 17.0 / 17.2 / 17.4 / 17.5 with the dense start, 9.5 / 8.4 / 8.6 / 8.9 / 9.0
-                           // with the frontier start)
-#endif
-constexpr uint32_t LC_PASSES = MAPGPU_LC_PASSES;
+// Asynchronous schedule: block-local passes over a block's own raised vertices per round
+// (Ctl::lc_passes, per handle; measured on the 2^26 layered graph, ms per run for 0 / 1 / 2 / 4 /
+// 8 passes: 18.2 / 17.0 / 17.2 / 17.4 / 17.5 with the dense start, 9.5 / 8.4 / 8.6 / 8.9 / 9.0
+// with the frontier start; map_autotune measures it on the handle's graph)
 constexpr uint32_t LC_CAP = 1024; // entries recorded per block and round (the rest only go through the list)
 
 // The fix-point loop of one outer iteration: rounds 2, 3, ... until a round
@@ -972,14 +976,17 @@ constexpr uint32_t LC_CAP = 1024; // entries recorded per block and round (the r
 // snapshots, list flags and bits of the pulled list are cleared in the next round (or after
 // the last one), when nobody reads them any more.
 constexpr int PT_ROWS = 128;
-constexpr int PT_UNROLL = 2;
+#ifndef MAPGPU_PT_UNROLL
+#define MAPGPU_PT_UNROLL 2 // 128-bit colidx loads per lane in flight in a pull round
+#endif
+constexpr int PT_UNROLL = MAPGPU_PT_UNROLL;
 constexpr uint32_t PT_Q = 64;
 
 struct NoPullSmem {
     uint32_t unused;
 };
-struct PullSmem {
-    uint32_t rp[8][PT_ROWS + 8];
+struct __align__(16) PullSmem {
+    uint32_t rp[8][PT_ROWS + 8]; // per warp: the tile's rowptr slice
     uint32_t best[8][PT_ROWS];
     uint32_t qe[8][PT_Q], qu[8][PT_Q], qn[8];
     uint32_t hit[8][PT_ROWS / 32];
@@ -1021,6 +1028,8 @@ __device__ __forceinline__ void pull_round(const Dev &d, uint32_t rr, uint32_t p
         atomicMax(&best[row], pull_offer<SYNC>(d, u, p_in));
         atomicOr(&ps.hit[warp][row >> 5], 1u << (row & 31u));
     };
+    // (a double-buffered cp.async prefetch of the next tile's slice, as in the dense round,
+    // measured slower here: the extra registers spill at this kernel's budget)
     for (uint32_t t = blockIdx.x * (blockDim.x >> 5) + warp; t < ntiles; t += nw) {
         const uint32_t r0 = t * PT_ROWS, rows = min((uint32_t)PT_ROWS, n - r0);
         if (d.comp) { // a tile inside one finished graph holds no changed vertex
@@ -1187,6 +1196,47 @@ __device__ __forceinline__ void check_phase(const Dev &d, Handles hd, bool work 
 
 __global__ void __launch_bounds__(256) k_check(const Dev d, Handles hd) { check_phase(d, hd); }
 
+// Small lists: a round over few vertices is mostly the fixed cost of the grid barrier, so
+// while the list stays small block 0 runs the rounds alone, with block barriers, and the other
+// blocks wait for it to hand back (solo_gen).  The wait is bounded: it gives up when block 0's
+// heartbeat (solo_beat, the round it is on) has not moved for about a second.
+constexpr uint32_t SOLO_BEAT_SPINS = 1u << 14; // polls between heartbeat checks
+constexpr uint32_t SOLO_BEAT_CHECKS = 1u << 8; // heartbeat checks without progress before giving up
+
+// every thread of a waiting block calls it; returns false if the wait gave up.  s_vals gets
+// block 0's r, |list|, |frontier| and status; *seen (shared: the hand-backs this block has seen)
+// counts this one
+__device__ __forceinline__ bool solo_wait(Ctl *ctl, uint32_t *seen, uint32_t *s_vals)
+{
+    __shared__ uint32_t s_ok;
+    if (threadIdx.x == 0) {
+        volatile Ctl *v = ctl;
+        uint32_t ok = 1, beat = v->solo_beat.v, still = 0;
+        for (uint32_t it = 0; v->solo_gen.v == *seen; ++it) {
+            if (it == SOLO_BEAT_SPINS) {
+                it = 0;
+                const uint32_t b = v->solo_beat.v;
+                if (b == beat && ++still > SOLO_BEAT_CHECKS) {
+                    ok = 0;
+                    break;
+                }
+                if (b != beat) still = 0;
+                beat = b;
+            }
+            __nanosleep(256);
+        }
+        __threadfence();
+        s_vals[0] = v->solo_r;
+        s_vals[1] = v->solo_nl;
+        s_vals[2] = v->solo_nf;
+        s_vals[3] = v->solo_status;
+        *seen += 1;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 // PULL: the variant with pull rounds (launched when some round may pull; the push-only
 // variant keeps the register budget of the push path free of the pull path's needs)
 template <bool SYNC, bool PULL>
@@ -1199,7 +1249,7 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
     __shared__ uint32_t *s_dst[3][2];
     __shared__ unsigned int *s_ctr[3];
     __shared__ uint32_t s_vals[4]; // after each barrier: |list|, |flist| of the round, self_seen, stop_req
-    __shared__ typename std::conditional<PULL, PullSmem, NoPullSmem>::type s_pull;
+    __shared__ __align__(16) typename std::conditional<PULL, PullSmem, NoPullSmem>::type s_pull;
     Ctl *ctl = d.ctl;
     volatile Ctl *vc = ctl;
     const unsigned lane = lane_id();
@@ -1240,17 +1290,42 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
     const uint32_t pull_min = (PULL && d.cbit[0]) ? vc->pull_min : 0u;
     uint32_t pulled = 0; // > 0: the last round pulled, over a list of that many vertices
     unsigned long long prow = 0; // frontier rows of pull rounds
+    // rounds block 0 may run alone: list and frontier limits, hand-backs seen so far (every
+    // block counts the same); in shared memory, which keeps registers for the push path
+    __shared__ uint32_t s_solo[4];
+    if (threadIdx.x == 0) {
+        s_solo[0] = vc->solo_max;
+        s_solo[1] = vc->solo_fmax;
+        s_solo[2] = vc->solo_gen.v;
+        s_solo[3] = vc->lc_passes; // (block-local passes per round, asynchronous single graphs)
+    }
+    __syncthreads();
     while (nl && status == ST_OK) {
         const uint32_t rr = r + 1; // this round
         const uint32_t p_in = (rr - 1) % 3, p_out = rr % 3, p_free = (rr + 1) % 3;
+        const bool first = rr == 1; // round 1 from the accepting vertices (frontier start only)
+        // a small list: block 0 runs this round (and the next small ones) alone
+        const bool solo = s_solo[0] && !first && !pulled && nl <= s_solo[0] && nf <= s_solo[1];
+        if (solo && blockIdx.x != 0) {
+            const bool ok = solo_wait(ctl, &s_solo[2], s_vals);
+            if (!ok) {
+                status = ST_TIMEOUT;
+                break;
+            }
+            r = s_vals[0];
+            nl = s_vals[1];
+            nf = s_vals[2];
+            status = s_vals[3];
+            continue;
+        }
+        const uint32_t nb = solo ? 1u : gridDim.x, bid = solo ? 0u : blockIdx.x; // blocks sharing the round
         if (lead) {
             vc->lcnt[p_free].v = 0;
             vc->fcnt[p_free].v = 0;
         }
         // the list the round before pulled over (list[p_free], which nothing reads any more)
         if (PULL && pulled) pull_cleanup<SYNC>(d, pick3(p_free, d.list), pulled, p_free);
-        const bool first = rr == 1; // round 1 from the accepting vertices (frontier start only)
-        const bool pull = PULL && !first && pull_min && nl >= pull_min;
+        const bool pull = PULL && !solo && !first && pull_min && nl >= pull_min;
         const uint32_t *__restrict__ list = first ? d.alist : pick3(p_in, d.list);
         uint32_t *const list_out = pick3(p_out, d.list);
         uint32_t *const flist_out = pick3(p_out, d.flist);
@@ -1272,7 +1347,7 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
         st.buf = s_stage[threadIdx.x >> 5];
         st.cnt[0] = st.cnt[1] = st.cnt[2] = 0;
         // the previous round's frontier: clear its flags, count its relaxations
-        if (track && !first) relax += clear_frontier(pick3(p_in, d.flist), nf, p_in, d.rec, d.rowptr, d);
+        if (track && !first) relax += clear_frontier(pick3(p_in, d.flist), nf, p_in, d.rec, d.rowptr, d, nb, bid);
         // round 1 of a frontier start keeps no frontier: its relaxations are the canonical m
         const bool trk = track && !first;
 
@@ -1281,8 +1356,8 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
         // threads, RC_P pairs per thread per step with all their loads and atomics
         // in flight before any result is used
         // every block takes an even contiguous share of the list (a pull round: none)
-        const uint64_t per = (nl + gridDim.x - 1) / gridDim.x;
-        const uint64_t beg = (uint64_t)blockIdx.x * per, end = pull ? beg : min((uint64_t)nl, beg + per);
+        const uint64_t per = (nl + nb - 1) / nb;
+        const uint64_t beg = (uint64_t)bid * per, end = pull ? beg : min((uint64_t)nl, beg + per);
         if constexpr (PULL) if (pull) { // the list's bits, then (once every block has set its share) the pull itself
             uint32_t *cb = pick3(p_in, d.cbit);
             const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
@@ -1298,7 +1373,7 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
         }
         // asynchronous single graph: once its share of the list is done, the block pushes again
         // the live values of the vertices it listed itself in this round (recorded in s_loc), up
-        // to LC_PASSES passes, so that values travel several edges per round.  These extra pushes
+        // to lc_passes passes, so that values travel several edges per round.  These extra pushes
         // touch no list flag: every listed vertex still goes through the list to the next round.
         if (local) {
             if (threadIdx.x == 0) s_ln = 0;
@@ -1309,7 +1384,7 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
         uint32_t lpass = 0, qend = 0;
         for (;;) {
             if (c0 >= cend) {
-                if (!local || lpass >= LC_PASSES) break;
+                if (!local || lpass >= s_solo[3]) break;
                 const uint32_t q = min(s_ln, (uint32_t)LC_CAP); // s_ln is final: a barrier ended the last chunk
                 if (q == qend) break;
                 loc = true;
@@ -1419,7 +1494,18 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
         }
         stage_flush_block<3>(st, s_cnt, s_base, dst, ctr);
         if (lead && timed_out(vc)) vc->stop_req.v = 1;
-        if (!grid_barrier(ctl, p_out, s_vals)) {
+        if (solo) { // block 0 alone: its appends are complete after a block barrier
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                s_vals[0] = vc->lcnt[p_out].v;
+                s_vals[1] = vc->fcnt[p_out].v;
+                s_vals[2] = vc->self_seen.v;
+                s_vals[3] = vc->stop_req.v;
+                vc->solo_beat.v = rr;
+            }
+            __syncthreads();
+        } else if (!grid_barrier(ctl, p_out, s_vals)) {
             status = ST_TIMEOUT;
             break;
         }
@@ -1434,9 +1520,22 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const 
         }
         if (s_vals[3]) status = ST_TIMEOUT;
         else if (nl && r + 1 > max_inner) status = ST_LIMIT;
+        // block 0 hands back when the next round is not one it runs alone (the same test every
+        // block makes at the top of the loop)
+        if (solo && !(nl && status == ST_OK && nl <= s_solo[0] && nf <= s_solo[1])) {
+            if (threadIdx.x == 0) {
+                vc->solo_r = r;
+                vc->solo_nl = nl;
+                vc->solo_nf = nf;
+                vc->solo_status = status;
+                __threadfence();
+                atomicAdd(&ctl->solo_gen.v, 1u);
+                s_solo[2] += 1; // (read by thread 0 only, in solo_wait)
+            }
+        }
     }
     // the last round's frontier: clear its flags, count its relaxations
-    if (r > 1 && track) relax += clear_frontier(pick3(r % 3, d.flist), nf, r % 3, d.rec, d.rowptr, d);
+    if (r > 1 && track) relax += clear_frontier(pick3(r % 3, d.flist), nf, r % 3, d.rec, d.rowptr, d, gridDim.x, blockIdx.x);
     if (PULL && pulled) pull_cleanup<SYNC>(d, pick3((r + 2) % 3, d.list), pulled, (r + 2) % 3); // list[p_in] of round r
     block_add_u64(relax, (unsigned long long *)&ctl->relax.v);
     block_add_u64(track ? prow : 0ull, (unsigned long long *)&ctl->frontier_rows.v);
