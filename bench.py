@@ -73,7 +73,7 @@ def _peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling (SM clock, throttle reasons) every 50 ms.  The sampler starts before the
+    """nvidia-smi sampling (SM clock, throttle reasons) every period_ms.  The sampler starts before the
     warm-up (it needs a moment to start); mark_start() / mark_end() bracket the timed region, and
     summary() keeps the samples stamped inside it (the nearest one if the region is shorter than
     the sampling interval)."""
@@ -82,8 +82,9 @@ class Clocks:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, period_ms: int = 200):
         self.index = index
+        self.period_ms = period_ms  # (nvidia-smi's queries take driver locks: sample no faster than needed)
         self.proc = None
         self.t_start = self.t_end = None
 
@@ -101,7 +102,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.period_ms)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
         return self
@@ -273,12 +274,13 @@ def configs_leg(pkg, np, torch, stream, peak, steps=10):
     return res
 
 
-def batched_leg(pkg, np, torch, stream, count=256, steps=2, sched=0):
+def batched_leg(pkg, np, torch, stream, count=256, steps=2):
     """256 graphs (sizes log-uniform in [1e3, 2e6], 40 % with a planted accepting cycle, layered
-    recipe) in one batched run, against the same 256 graphs run one after another with map_run.
-    map_autotune picks the batch's launch shapes and its start (dense round or frontier start);
-    the one-by-one runs use the same start.  Inputs resident in HBM in both legs; device time
-    by CUDA events; jobs/s = graphs / time."""
+    recipe) in one batched run, against the same 256 graphs run one after another with map_run,
+    under both schedules: the asynchronous one (the headline's) and the synchronous one, whose
+    canonical round and relaxation counts are compared too.  For each schedule map_autotune picks
+    the batch's run choices (start included) first; the one-by-one runs use the same start.
+    Inputs resident in HBM in both legs; device time by CUDA events; jobs/s = graphs / time."""
     import mapgen
 
     sizes, planted, seeds = mapgen.batch_plan(count=count, lo=1000, hi=2_000_000, frac_cycle=0.4, seed=4)
@@ -288,43 +290,51 @@ def batched_leg(pkg, np, torch, stream, count=256, steps=2, sched=0):
     hb = pkg.map_batch_create(items, stream)
     singles = [pkg.map_create(it[0], it[1], it[2], it[3], stream) for it in items]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"workload": f"{count} layered graphs, n log-uniform in [1e3, 2e6], 40 % planted cycles, seed 4",
+           "vertices": int(sum(g.n for g in gs)), "edges": int(sum(g.m for g in gs))}
     try:
-        t_tune = time.perf_counter()
-        tune = pkg.map_autotune(hb, sched)  # launch shapes for this batch, by measurement
-        t_tune = time.perf_counter() - t_tune
-        res = pkg.map_batch_run(hb, count, sched=sched)  # warm-up (builds the graph)
-        sflags = pkg.MAP_FLAG_FRONTIER_START if tune["frontier_start"] else 0
-        for h in singles:
-            pkg.map_run(h, sched=sched, flags=sflags)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(steps):
-            res = pkg.map_batch_run(hb, count, sched=sched)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        batch_ms = e0.elapsed_time(e1) / steps
-        e0.record(stream)
-        seq = None
-        for _ in range(steps):
-            seq = [pkg.map_run(h, sched=sched, flags=sflags) for h in singles]
-        e1.record(stream)
-        torch.cuda.synchronize()
-        seq_ms = e0.elapsed_time(e1) / steps
-        same = all((a.verdict, a.witness, a.outer, a.rounds, a.relaxations) ==
-                   (b.verdict, b.witness, b.outer, b.rounds, b.relaxations) for a, b in zip(res, seq))
+        for sched, name in ((1, "async"), (0, "sync")):
+            t_tune = time.perf_counter()
+            tune = pkg.map_autotune(hb, sched)  # this batch's run choices, by measurement
+            t_tune = time.perf_counter() - t_tune
+            res = pkg.map_batch_run(hb, count, sched=sched)  # warm-up (builds the graph)
+            sflags = pkg.MAP_FLAG_FRONTIER_START if tune["frontier_start"] else pkg.MAP_FLAG_DENSE_START
+            for h in singles:
+                pkg.map_run(h, sched=sched, flags=sflags)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(steps):
+                res = pkg.map_batch_run(hb, count, sched=sched)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            batch_ms = e0.elapsed_time(e1) / steps
+            e0.record(stream)
+            seq = None
+            for _ in range(steps):
+                seq = [pkg.map_run(h, sched=sched, flags=sflags) for h in singles]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            seq_ms = e0.elapsed_time(e1) / steps
+            key = lambda r: (r.verdict, r.witness, r.outer) + ((tuple(r.rounds), r.relaxations) if sched == 0 else ())
+            same = all(key(a) == key(b) for a, b in zip(res, seq))
+            edges = sum(r.edges_total for r in res)
+            out[name] = {"cycles_found": int(sum(r.verdict for r in res)), "batch_ms": batch_ms, "sequential_ms": seq_ms,
+                         "jobs_per_s_batched": count / (batch_ms / 1e3),
+                         "jobs_per_s_sequential": count / (seq_ms / 1e3), "speedup": seq_ms / batch_ms,
+                         "gteps_batched": edges / (batch_ms / 1e3) / 1e9,
+                         "start": "frontier" if tune["frontier_start"] else "dense",
+                         "results_identical": bool(same),
+                         "compared": "verdict, witness, outer" + (", rounds, relaxations" if sched == 0 else ""),
+                         "autotune": dict(tune, seconds=t_tune)}
     finally:
         pkg.map_destroy(hb)
         for h in singles:
             pkg.map_destroy(h)
-    edges = sum(r.edges_total for r in res)
-    return {"workload": f"{count} layered graphs, n log-uniform in [1e3, 2e6], 40 % planted cycles, seed 4",
-            "vertices": int(sum(g.n for g in gs)), "edges": int(sum(g.m for g in gs)),
-            "cycles_found": int(sum(r.verdict for r in res)),
-            "batch_ms": batch_ms, "sequential_ms": seq_ms,
-            "jobs_per_s_batched": count / (batch_ms / 1e3), "jobs_per_s_sequential": count / (seq_ms / 1e3),
-            "speedup": seq_ms / batch_ms, "gteps_batched": edges / (batch_ms / 1e3) / 1e9,
-            "start": "frontier" if tune["frontier_start"] else "dense",
-            "results_identical": bool(same), "autotune": dict(tune, seconds=t_tune)}
+    # the headline schedule's figures at the top level
+    out.update({k: out["async"][k] for k in ("batch_ms", "sequential_ms", "jobs_per_s_batched", "jobs_per_s_sequential",
+                                           "speedup", "gteps_batched", "results_identical")})
+    out["sched"] = "async"
+    return out
 
 
 def serving_leg(pkg, np, rates=(50, 100, 200, 500, 1000, 2000), jobs=2000, max_arrival_s=12.0, slots=8):
@@ -587,7 +597,9 @@ def main():
                                  "run_ms": prof[0].device_ms,
                                  "source": "CUDA events around each launch of 2 host-stepped runs"}}
 
-    # end to end through the C ABI from pinned host buffers
+    # end to end through the C ABI from pinned host buffers, with the bench graph's handle gone
+    # (one graph's work space in the device memory pool, as for a caller running one job at a time)
+    pkg.map_destroy(h)
     hp = [torch.from_numpy(x.view(np.int32)).pin_memory() for x in (g.rowptr, g.colidx, pkg.pack_bits(g.acc))]
     hout = torch.empty(g.n, dtype=torch.int32).pin_memory()
 
@@ -613,9 +625,9 @@ def main():
     # taken at the median step, so that one step stalled on the host does not decide it, and
     # every step's time is reported with it
     e2e_ms, e2e_edges = [], 0
-    with Clocks(local) as e2e_clk:
-        if args.e2e_steps:
-            e2e_step()  # warm-up: the device memory pool grows to hold a second copy of the graph
+    with Clocks(local, period_ms=500) as e2e_clk:
+        for _ in range(2 if args.e2e_steps else 0):
+            e2e_step()  # warm-up: the device memory pool and the pinned control slots reach their size
         e2e_clk.mark_start()
         for _ in range(args.e2e_steps):
             torch.cuda.synchronize()
@@ -646,10 +658,9 @@ def main():
             "autotune": dict(tune, seconds=t_tune) if tune else None,
             "gpu_launches": sum(r.launches for r in results),
             "clocks": clk.summary()}
-    pkg.map_destroy(h)
     if not args.no_batch and args.n is None and ws == 1:
         line["configs"] = configs_leg(pkg, np, torch, stream, peak)
-        line["batched"] = batched_leg(pkg, np, torch, stream, sched=0)  # canonical counts compared too
+        line["batched"] = batched_leg(pkg, np, torch, stream)
     if not args.no_serve and args.n is None and ws == 1:
         line["serving"] = serving_leg(pkg, np)
     if rank == 0 and ws == 1 and not args.no_cpu:

@@ -275,7 +275,7 @@ MAP_API int map_server_destroy(map_server *sv);
  *     or 1/4 of the vertices (MAP_FLAG_PUSH / MAP_FLAG_PULL still force
  *     either);
  *  2. (MAP_SCHED_ASYNC, single graphs) how many times a block pushes again, in
- *     the same round, the vertices it raised itself (0, 1, 2, 4 or 8; by
+ *     the same round, the vertices it raised itself (0, 1, 2, 4, 8, 16 or 32; by
  *     default 1), so that values travel several edges per round;
  *  3. up to which list size one block runs a round alone, with block barriers
  *     instead of the grid-wide one (never, 64, 256 or 1024 listed vertices;

@@ -173,9 +173,21 @@ int rounds_occupancy()
         occ = std::min(occ, o);
     };
     take((const void *)mapk::k_rounds<true, false>);
-    take((const void *)mapk::k_rounds<true, true>);
     take((const void *)mapk::k_rounds<false, false>);
-    take((const void *)mapk::k_rounds<false, true>);
+    return std::max(1, occ);
+}
+
+// the same for the variant with pull rounds (its grid is the handle's, at most this many blocks per SM)
+int pull_occupancy()
+{
+    int occ = 1 << 30, o = 0;
+    for (const void *k : {(const void *)mapk::k_rounds<true, true>, (const void *)mapk::k_rounds<false, true>}) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, 256, 0) != cudaSuccess) {
+            cudaGetLastError();
+            o = 1;
+        }
+        occ = std::min(occ, o);
+    }
     return std::max(1, occ);
 }
 
@@ -388,7 +400,10 @@ int launch_rounds(map_graph *g, cudaStream_t s, bool sync_sched, mapk::Handles h
 {
     const mapk::Dev d = dev_of(g);
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)g->rounds_grid);
+    // (the pull variant may fit fewer blocks per SM: its grid is clamped to its own occupancy)
+    static const int occ_pull = pull_occupancy();
+    const int grid = g->pull_on ? std::min(g->rounds_grid, g->sms * occ_pull) : g->rounds_grid;
+    cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(256);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
@@ -664,8 +679,15 @@ int create_graph(uint32_t n, uint64_t m, cudaStream_t s, const char *who, Upload
         free_graph(g);
         return rc;
     }
-    mapk::k_validate<<<grid_for(g, m > n ? m : n, 1), 256, 0, s>>>(n, g->rowptr, m, g->colidx, &g->ctl->bad);
+    // the accepting set, then one pass over the CSR: validation, in-degree histogram of the reverse
+    // CSR, and the accepting flag of each target into bit 31 of its entry (restored after every run)
+    if ((rc = ck(cudaMemsetAsync(g->rrowptr, 0, ((size_t)n + 1) * 4, s), "memset rrowptr"))) {
+        free_graph(g);
+        return rc;
+    }
     mapk::k_acc_init<<<grid_for(g, W, 1), 256, 0, s>>>(n, acc_in, g->acc0, &g->ctl->elim.v);
+    mapk::k_ingest<<<grid_for(g, std::max<uint64_t>(m / 4, n), 1), 256, 0, s>>>(n, g->rowptr, m, g->colidx, g->acc0,
+                                                                             g->rrowptr, &g->ctl->bad);
     if ((rc = ck(cudaGetLastError(), "validate")) || (rc = read_ctl(g))) {
         free_graph(g);
         return rc;
@@ -676,13 +698,8 @@ int create_graph(uint32_t n, uint64_t m, cudaStream_t s, const char *who, Upload
     }
     g->nacc0 = g->h_ctl->elim.v;
 
-    // reverse CSR: in-degree histogram, scan, scatter
-    if ((rc = ck(cudaMemsetAsync(g->rrowptr, 0, ((size_t)n + 1) * 4, s), "memset rrowptr"))) {
-        free_graph(g);
-        return rc;
-    }
-    mapk::k_indegree<<<grid_for(g, m, 1), 256, 0, s>>>(m, g->colidx, g->rrowptr);
-    if ((rc = ck(cudaGetLastError(), "indegree")) || (rc = scan_inclusive(g->rrowptr, (uint64_t)n + 1, s))) {
+    // reverse CSR: scan of the histogram, scatter
+    if ((rc = scan_inclusive(g->rrowptr, (uint64_t)n + 1, s))) {
         free_graph(g);
         return rc;
     }
@@ -695,8 +712,6 @@ int create_graph(uint32_t n, uint64_t m, cudaStream_t s, const char *who, Upload
     // in flight (fewer rows at once measured faster: 9.6 against 14.1 ms for map_create at 2^26)
     DISPATCH_G(std::max(g->G, 16), (mapk::k_transpose<GG><<<grid_for(g, n, GG), 256, 0, s>>>(n, g->rowptr, g->colidx, g->list,
                                                                               g->rcol, g->rpos)));
-    // the accepting flag of each target into bit 31 of its entry (restored after every run)
-    mapk::k_pack_flags<<<grid_for(g, m, 1), 256, 0, s>>>(m, g->colidx, g->acc0);
     if ((rc = ck(cudaGetLastError(), "transpose")) || (rc = ck(cudaStreamSynchronize(s), "create sync"))) {
         free_graph(g);
         return rc;
@@ -1016,7 +1031,7 @@ int map_autotune(map_graph *g, uint32_t sched, map_tune_result *out)
     }
     // 2. (asynchronous single graphs) block-local passes per round
     if (g->nacc0 && sched == MAP_SCHED_ASYNC && !g->comp) {
-        const uint32_t passes[] = {0, 1, 2, 4, 8};
+        const uint32_t passes[] = {0, 1, 2, 4, 8, 16, 32};
         double best = 1e30;
         uint32_t best_p = g->lc_passes;
         for (uint32_t pz : passes) {

@@ -961,6 +961,11 @@ constexpr uint32_t LC_CAP = 1024; // entries recorded per block and round (the r
 #ifndef MAPGPU_ROUNDS_MIN_BLOCKS
 #define MAPGPU_ROUNDS_MIN_BLOCKS 6 // resident blocks per SM the register budget is sized for (measured best)
 #endif
+#ifndef MAPGPU_ROUNDS_PULL_MIN_BLOCKS
+#define MAPGPU_ROUNDS_PULL_MIN_BLOCKS 5 // the same for the variant with pull rounds: 48 registers, fewer spills
+                                        // (256-graph batch, ms per synchronous / asynchronous run at its tuned
+                                        // choices: 41.0 / 41.7 with 6 blocks, 39.8 / 33.4 with 5, 40.8 / 30.7 with 4)
+#endif
 
 // ------------------------------------------------------------- pull rounds --
 //
@@ -1240,7 +1245,8 @@ __device__ __forceinline__ bool solo_wait(Ctl *ctl, uint32_t *seen, uint32_t *s_
 // PULL: the variant with pull rounds (launched when some round may pull; the push-only
 // variant keeps the register budget of the push path free of the pull path's needs)
 template <bool SYNC, bool PULL>
-__global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_rounds(const Dev d, Handles hd)
+__global__ void __launch_bounds__(256, PULL ? MAPGPU_ROUNDS_PULL_MIN_BLOCKS : MAPGPU_ROUNDS_MIN_BLOCKS)
+    k_rounds(const Dev d, Handles hd)
 {
     __shared__ uint32_t s_stage[8][3 * SB_ENTRIES];
     __shared__ uint32_t s_cnt[8][3], s_base[3];
@@ -1842,6 +1848,42 @@ __global__ void k_validate(uint32_t n, const uint32_t *__restrict__ rowptr, uint
     if (__any_sync(0xFFFFFFFFu, b) && lane_id() == 0) *bad = 1;
 }
 
+// Set-up in one pass over the CSR (map_create): rowptr must not decrease; every entry u < n is
+// counted in the in-degree histogram (cnt[u + 1]) and gets the accepting flag of u (bitmap acc)
+// in bit 31; an entry u >= n sets *bad instead (the graph is then refused, and nothing built
+// from it is used).  Four entries per thread and step (one 128-bit load and store).
+__device__ __forceinline__ uint32_t ingest_one(uint32_t u, uint32_t n, const uint32_t *__restrict__ acc, uint32_t *cnt,
+                                               bool &bad)
+{
+    if (u >= n) {
+        bad = true;
+        return u;
+    }
+    atomicAdd(cnt + u + 1, 1u);
+    return u | (((__ldg(acc + (u >> 5)) >> (u & 31u)) & 1u) << 31);
+}
+
+__global__ void k_ingest(uint32_t n, const uint32_t *__restrict__ rowptr, uint64_t m, uint32_t *colidx,
+                         const uint32_t *__restrict__ acc, uint32_t *cnt, uint32_t *bad)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool b = false;
+    for (uint64_t i = tid; i < n; i += stride) b |= __ldg(rowptr + i) > __ldg(rowptr + i + 1);
+    const uint64_t m4 = m / 4;
+    uint4 *c4 = reinterpret_cast<uint4 *>(colidx);
+    for (uint64_t q = tid; q < m4; q += stride) {
+        uint4 w = c4[q];
+        w.x = ingest_one(w.x, n, acc, cnt, b);
+        w.y = ingest_one(w.y, n, acc, cnt, b);
+        w.z = ingest_one(w.z, n, acc, cnt, b);
+        w.w = ingest_one(w.w, n, acc, cnt, b);
+        c4[q] = w;
+    }
+    for (uint64_t i = m4 * 4 + tid; i < m; i += stride) colidx[i] = ingest_one(colidx[i], n, acc, cnt, b);
+    if (__any_sync(0xFFFFFFFFu, b) && lane_id() == 0) *bad = 1;
+}
+
 // in-degree histogram: cnt[u + 1] += 1 for every edge into u
 __global__ void k_indegree(uint64_t m, const uint32_t *__restrict__ colidx, uint32_t *cnt)
 {
@@ -1898,7 +1940,7 @@ __global__ void __launch_bounds__(256) k_transpose(uint32_t n, const uint32_t *_
     for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; w < n; w += groups) {
         const uint32_t b = __ldg(rowptr + w), e = __ldg(rowptr + w + 1);
         for (uint32_t i = b + glane; i < e; i += G) {
-            const uint32_t u = __ldg(colidx + i);
+            const uint32_t u = __ldg(colidx + i) & 0x7FFFFFFFu; // (bit 31: the accepting flag, when packed already)
             const uint32_t slot = atomicAdd(cursor + u, 1u);
             rcol[slot] = (uint32_t)w;
             rpos[slot] = i;
