@@ -122,7 +122,13 @@ typedef struct {
     uint32_t *rounds_out; /* optional host array: round count of outer iteration i at [i] */
     uint32_t rounds_cap;  /* entries of rounds_out; later iterations are not stored */
     uint32_t timeout_ms;  /* the loop stops with MAP_ERR_TIMEOUT after this long; 0 = 120000 */
-    uint32_t reserved[3]; /* must be zero */
+    uint32_t repeat;      /* map_run only: run the same MAP this many times back to back, queued on the
+                             stream with no host step between them (0 or 1: once; for throughput
+                             measurements).  res and map_out describe the last run (every run gives the
+                             same), device_ms covers all of them.  Refused (MAP_ERR_ARG) with a trace,
+                             MAP_FLAG_PROFILE, MAP_FLAG_EARLY_EXIT, max_outer or max_inner, by
+                             map_submit and by map_run_static. */
+    uint32_t reserved[2]; /* must be zero */
 } map_opts;
 
 typedef struct {
@@ -404,7 +410,7 @@ MAP_API int map_graph_info(const map_graph *g, uint32_t *n, uint64_t *m);
  *   device memory; the inputs are copied into the array on every call.
  *   opts: as for map_run (schedules, limits, timeout_ms, rounds_out for every
  *   outer iteration, MAP_FLAG_EARLY_EXIT, MAP_FLAG_DENSE_START), except that
- *   traces, MAP_FLAG_PROFILE and MAP_FLAG_FRONTIER_START are refused
+ *   traces, MAP_FLAG_PROFILE, MAP_FLAG_FRONTIER_START and repeat are refused
  *   (MAP_ERR_ARG); res: as for map_run, status included (device_ms stays 0).
  *   cuda_stream: the stream all work is issued on.
  * The call blocks: it waits for cuda_stream several times (it reads rowptr[0]

@@ -57,7 +57,8 @@ class MapOpts(ctypes.Structure):
         ("rounds_out", ctypes.POINTER(ctypes.c_uint32)),
         ("rounds_cap", ctypes.c_uint32),
         ("timeout_ms", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32 * 3),
+        ("repeat", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 2),
     ]
 
 
@@ -315,11 +316,13 @@ class RunResult:
 
 def map_run(handle, sched: int = MAP_SCHED_SYNC, max_outer: int = 0, max_inner: int = 0, flags: int = 0,
             map_out=None, keep_trace: bool = False, hash_trace=None, rounds_cap: int = 1 << 16,
-            allow_limit: bool = False, timeout_ms: int = 0) -> RunResult:
-    """Run MAP on a created graph.  map_out: optional uint32 numpy array or CUDA tensor of n entries."""
+            allow_limit: bool = False, timeout_ms: int = 0, repeat: int = 0) -> RunResult:
+    """Run MAP on a created graph.  map_out: optional uint32 numpy array or CUDA tensor of n entries.
+    repeat > 1: the same run that many times back to back (see map_opts.repeat)."""
     lib = load()
     opts = MapOpts()
     opts.sched, opts.max_outer, opts.max_inner, opts.flags = sched, max_outer, max_inner, flags
+    opts.repeat = repeat
     rounds = np.zeros(max(rounds_cap, 1), dtype=np.uint32)
     opts.rounds_out = rounds.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
     opts.rounds_cap = rounds_cap

@@ -784,6 +784,10 @@ static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint
     // the CUDA-graph driver runs the whole loop on the device; per-iteration
     // traces and per-kernel timing need the host-stepped driver (same kernels)
     const bool stepped = opts.trace != nullptr || profile || force_stepped;
+    // (a run that stops early leaves round state for the host to clear, so repeated runs must not)
+    if (opts.repeat > 1 && (stepped || (opts.flags & MAP_FLAG_EARLY_EXIT) || opts.max_outer || opts.max_inner))
+        return fail(MAP_ERR_ARG, "map_run: repeat with a trace, MAP_FLAG_PROFILE, early exit or a limit");
+    const uint32_t reps = opts.repeat > 1 ? opts.repeat : 1u;
     if ((opts.flags & MAP_FLAG_FRONTIER_START) && (opts.flags & MAP_FLAG_DENSE_START))
         return fail(MAP_ERR_ARG, "map_run: MAP_FLAG_FRONTIER_START and MAP_FLAG_DENSE_START together");
     // frontier start (round 1 pushed from the accepting vertices): asked for, or chosen by
@@ -851,8 +855,10 @@ static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint
         if ((rc = build_run_graph(g, opts.sched))) return rc;
         *g->h_ctl = init;
         CK(cudaEventRecord(g->ev[0], s));
-        CK(cudaMemcpyAsync(g->ctl, g->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
-        CK(cudaGraphLaunch(g->exec[opts.sched + (fstart ? 2 : 0) + (g->pull_on ? 4 : 0)], s));
+        for (uint32_t k = 0; k < reps; ++k) { // (the mirror is read back only after the last run)
+            CK(cudaMemcpyAsync(g->ctl, g->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+            CK(cudaGraphLaunch(g->exec[opts.sched + (fstart ? 2 : 0) + (g->pull_on ? 4 : 0)], s));
+        }
         CK(cudaEventRecord(g->ev[1], s));
         if ((rc = read_ctl(g))) return rc;
         res->launches = 0; // filled below from the counts
@@ -1699,8 +1705,8 @@ static int run_static_impl(uint32_t n, const uint32_t *rowptr, const uint32_t *c
     memset(&opts, 0, sizeof opts);
     if (opts_in) opts = *opts_in;
     if (opts.sched > MAP_SCHED_ASYNC) return fail(MAP_ERR_ARG, "map_run_static: unknown schedule %u", opts.sched);
-    if (opts.trace || (opts.flags & (MAP_FLAG_PROFILE | MAP_FLAG_FRONTIER_START)))
-        return fail(MAP_ERR_ARG, "map_run_static: traces, profiling and the frontier start are not offered here");
+    if (opts.trace || (opts.flags & (MAP_FLAG_PROFILE | MAP_FLAG_FRONTIER_START)) || opts.repeat > 1)
+        return fail(MAP_ERR_ARG, "map_run_static: traces, profiling, the frontier start and repeat are not offered here");
     const bool sync_sched = opts.sched == MAP_SCHED_SYNC;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     memset(res, 0, sizeof *res);
@@ -2129,6 +2135,7 @@ int map_submit(map_server *sv, uint32_t n, const uint32_t *rowptr, const uint32_
     if (!sv || !job_id) return fail(MAP_ERR_ARG, "map_submit: NULL server or job_id");
     if (n == 0 || n >= 0x7FFFFFFFu || !rowptr || !acc_bits) return fail(MAP_ERR_ARG, "map_submit: bad graph");
     if (opts && opts->trace) return fail(MAP_ERR_ARG, "map_submit: traces are not offered for served jobs");
+    if (opts && opts->repeat > 1) return fail(MAP_ERR_ARG, "map_submit: repeat is not offered for served jobs");
     if (is_device_ptr(rowptr) || is_device_ptr(colidx) || is_device_ptr(acc_bits))
         return fail(MAP_ERR_ARG, "map_submit: inputs must be host memory (the job is copied at submission)");
     const uint64_t m = rowptr[n];
