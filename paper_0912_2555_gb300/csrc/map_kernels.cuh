@@ -843,7 +843,7 @@ __device__ __forceinline__ unsigned long long clear_frontier(const uint32_t *__r
         unsigned long long len = 0;
         uint32_t w = 0;
         if (i < nf) {
-            w = __ldg(flist + i);
+            w = __ldcg(flist + i); // (written in this launch: read at L2)
             atomicAnd(rec_flags(rec + w), ~FB(p));
             len = __ldg(rowptr + w + 1) - __ldg(rowptr + w);
             relax += len;
@@ -952,7 +952,10 @@ constexpr int RC_P = MAPGPU_RC_P;
 // (Ctl::lc_passes, per handle; measured on the 2^26 layered graph, ms per run for 0 / 1 / 2 / 4 /
 // 8 passes: 18.2 / 17.0 / 17.2 / 17.4 / 17.5 with the dense start, 9.5 / 8.4 / 8.6 / 8.9 / 9.0
 // with the frontier start; map_autotune measures it on the handle's graph)
-constexpr uint32_t LC_CAP = 1024; // entries recorded per block and round (the rest only go through the list)
+#ifndef MAPGPU_LC_CAP
+#define MAPGPU_LC_CAP 1024
+#endif
+constexpr uint32_t LC_CAP = MAPGPU_LC_CAP; // entries recorded per block and round (the rest only go through the list)
 
 // The fix-point loop of one outer iteration: rounds 2, 3, ... until a round
 // changes nothing.  Round r reads list[(r-1) % 3] and appends to list[r % 3];
@@ -1132,7 +1135,7 @@ __device__ __forceinline__ void pull_cleanup(const Dev &d, const uint32_t *__res
     const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
     uint32_t *cb = pick3(q, d.cbit);
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += nthreads) {
-        const uint32_t u = __ldg(list + i);
+        const uint32_t u = __ldcg(list + i);
         if (SYNC) *rec_snap(d.rec + u, q) = 0;
         atomicAnd(rec_flags(d.rec + u), ~CB(q));
         cb[u >> 5] = 0; // every bit set in cbit[q] belongs to this list
@@ -1159,8 +1162,9 @@ __device__ __forceinline__ void check_phase(const Dev &d, Handles hd, bool work 
         const uint64_t i = base + lane_id();
         uint32_t c = 0xFFFFFFFFu, removed = 0;
         if (i < nt) {
-            const uint32_t v = __ldg(d.touched + i);
-            const uint32_t x = __ldg(d.mval + v);
+            // (in a CUDA graph this runs in the launch that wrote both arrays: read them at L2)
+            const uint32_t v = __ldcg(d.touched + i);
+            const uint32_t x = __ldcg(d.mval + v);
             const uint32_t u = x - 1; // x != 0 for a touched vertex (checked all the same below)
             if (d.comp) c = __ldg(d.comp + v);
             if (x != 0 && u == v) {
@@ -1368,7 +1372,7 @@ __global__ void __launch_bounds__(256, PULL ? MAPGPU_ROUNDS_PULL_MIN_BLOCKS : MA
             uint32_t *cb = pick3(p_in, d.cbit);
             const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
             for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += nthreads) {
-                const uint32_t u = __ldg(list + i);
+                const uint32_t u = __ldcg(list + i);
                 atomicOr(cb + (u >> 5), 1u << (u & 31u));
             }
             if (!grid_barrier(ctl)) {
@@ -1407,7 +1411,9 @@ __global__ void __launch_bounds__(256, PULL ? MAPGPU_ROUNDS_PULL_MIN_BLOCKS : MA
                 const uint64_t i = c0 + threadIdx.x * RC_E + k;
                 o[k] = b[k] = len[k] = 0;
                 if (i < cend) {
-                    const uint32_t u = loc ? s_loc[i] : __ldg(list + i);
+                    // (lists are rewritten every third round of this launch: read them at L2, never
+                    // through the non-coherent path)
+                    const uint32_t u = loc ? s_loc[i] : __ldcg(list + i);
                     const bool listed = !loc && !(first && SYNC); // in list[p_in], with a snapshot (SYNC)
                     const uint32_t mu = SYNC ? (listed ? *(volatile uint32_t *)rec_snap(d.rec + u, p_in) : 0u)
                                              : *(volatile uint32_t *)(d.mval + u);

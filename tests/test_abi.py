@@ -66,3 +66,29 @@ def test_pack_bits_lsb_first():
     flags[[0, 31, 32, 69]] = 1
     bits = pkg.pack_bits(flags)
     assert bits.tolist() == [1 | (1 << 31), 1, 1 << 5]
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors of map_opts, map_result and map_tune_result have the header's size and
+    field offsets (compiled with the host compiler against include/map.h)."""
+    import ctypes
+
+    structs = {"map_opts": pkg.MapOpts, "map_result": pkg.MapResult, "map_tune_result": pkg.TuneResult}
+    src = ["#include <stddef.h>", "#include <stdio.h>", '#include "map.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        src.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            src.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    src += ["return 0; }"]
+    c = tmp_path / "abi.c"
+    c.write_text("\n".join(src))
+    exe = tmp_path / "abi"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(c)])
+    got = {}
+    for line in subprocess.check_output([str(exe)], text=True).splitlines():
+        cname, field, value = line.split()
+        got[(cname, field)] = int(value)
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
