@@ -294,6 +294,14 @@ MAP_API int map_server_destroy(map_server *sv);
  * It takes about thirty runs; results are unaffected (none of these
  * choices changes any map vector, verdict, witness or outer count, nor the
  * counts of the synchronous schedule).
+ *
+ * The defaults of a new handle (before any map_autotune) can be set from the
+ * environment, read by map_create and the other creating calls:
+ * MAPGPU_PULL_FRAC (share of the vertices from which a round pulls; 0, the
+ * default, = never), MAPGPU_SOLO_MAX (list size up to which one block runs a
+ * round alone; 256), MAPGPU_LC_PASSES (block-local passes of asynchronous
+ * rounds; 1), MAPGPU_ROUNDS_BLOCKS_PER_SM (resident blocks per SM of the
+ * fix-point kernel, below its occupancy limit).
  */
 typedef struct {
     uint32_t dense_blocks_per_sm;  /* chosen shape of the dense-round kernel */

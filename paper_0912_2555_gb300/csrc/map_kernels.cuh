@@ -78,7 +78,7 @@ struct Ctl {
     Cnt32 stop_req;        // k_rounds: block 0 asks every block to stop after the next barrier
     Cnt32 self_seen;       // smallest vertex seen to become its own map value (NONE: none yet)
     Cnt32 solo_gen;        // k_rounds: hand-backs of block 0 after rounds it ran alone
-    Cnt32 solo_beat;       // ... and the last round it ran alone (the waiting blocks' heartbeat)
+    Cnt32 solo_beat;       // ... and its progress in them (rounds and pushes; the waiting blocks' heartbeat)
     // fix-point loop
     uint32_t k;            // rounds completed in the current outer iteration
     // outer loop
@@ -904,6 +904,20 @@ constexpr uint32_t BAR_SPIN_LIMIT = 1u << 24;
 #define MAPGPU_BAR_SLEEP_NS 32 // back-off between polls of the barrier generation
 #endif
 
+#ifndef MAPGPU_BAR_FENCE_ACQREL
+#define MAPGPU_BAR_FENCE_ACQREL 0
+#endif
+// the barrier's fences: release before the arrival, acquire after the release (the block's
+// writes, ordered before thread 0's by the block barrier, are covered cumulatively)
+__device__ __forceinline__ void bar_fence()
+{
+#if MAPGPU_BAR_FENCE_ACQREL
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+#else
+    __threadfence();
+#endif
+}
+
 __device__ __forceinline__ bool grid_barrier(Ctl *ctl, uint32_t p = 3, uint32_t *s_vals = nullptr)
 {
     __shared__ uint32_t s_ok;
@@ -911,10 +925,10 @@ __device__ __forceinline__ bool grid_barrier(Ctl *ctl, uint32_t p = 3, uint32_t 
     if (threadIdx.x == 0) {
         uint32_t ok = 1;
         const uint32_t gen = *(volatile uint32_t *)&ctl->bar_gen.v;
-        __threadfence();
+        bar_fence();
         if (atomicAdd(&ctl->bar_count.v, 1u) == gridDim.x - 1) {
             atomicExch(&ctl->bar_count.v, 0u);
-            __threadfence();
+            bar_fence();
             atomicAdd(&ctl->bar_gen.v, 1u);
         } else {
             for (uint32_t it = 0; *(volatile uint32_t *)&ctl->bar_gen.v == gen; ++it) {
@@ -925,7 +939,7 @@ __device__ __forceinline__ bool grid_barrier(Ctl *ctl, uint32_t p = 3, uint32_t 
                 if (it > 16) __nanosleep(MAPGPU_BAR_SLEEP_NS);
             }
         }
-        __threadfence();
+        bar_fence();
         s_ok = ok;
         if (p < 3) {
             volatile Ctl *v = ctl;
@@ -1208,7 +1222,8 @@ __global__ void __launch_bounds__(256) k_check(const Dev d, Handles hd) { check_
 // Small lists: a round over few vertices is mostly the fixed cost of the grid barrier, so
 // while the list stays small block 0 runs the rounds alone, with block barriers, and the other
 // blocks wait for it to hand back (solo_gen).  The wait is bounded: it gives up when block 0's
-// heartbeat (solo_beat, the round it is on) has not moved for about a second.
+// heartbeat (solo_beat, bumped at every round and every 64 Ki pushes) has not moved for about a
+// second.
 constexpr uint32_t SOLO_BEAT_SPINS = 1u << 14; // polls between heartbeat checks
 constexpr uint32_t SOLO_BEAT_CHECKS = 1u << 8; // heartbeat checks without progress before giving up
 
@@ -1444,6 +1459,9 @@ __global__ void __launch_bounds__(256, PULL ? MAPGPU_ROUNDS_PULL_MIN_BLOCKS : MA
             const uint32_t total = s_incl[RC_ENTRIES - 1];
             if (!track && threadIdx.x == 0) relax += total; // pushes of this chunk
             for (uint32_t p0 = 0; p0 < total; p0 += 256 * RC_P) {
+                // a round block 0 runs alone shows progress every 64 Ki pushes (the waiting blocks'
+                // heartbeat), so a round over long reader lists is not taken for a stalled block
+                if (solo && threadIdx.x == 0 && (p0 & 0xFFFFu) == 0 && p0) vc->solo_beat.v = vc->solo_beat.v + 1;
                 uint32_t w[RC_P], ob[RC_P], fold[RC_P], mold[RC_P];
                 bool act[RC_P];
 #pragma unroll
@@ -1514,7 +1532,7 @@ __global__ void __launch_bounds__(256, PULL ? MAPGPU_ROUNDS_PULL_MIN_BLOCKS : MA
                 s_vals[1] = vc->fcnt[p_out].v;
                 s_vals[2] = vc->self_seen.v;
                 s_vals[3] = vc->stop_req.v;
-                vc->solo_beat.v = rr;
+                vc->solo_beat.v = vc->solo_beat.v + 1; // progress: one more round
             }
             __syncthreads();
         } else if (!grid_barrier(ctl, p_out, s_vals)) {
