@@ -904,19 +904,10 @@ constexpr uint32_t BAR_SPIN_LIMIT = 1u << 24;
 #define MAPGPU_BAR_SLEEP_NS 32 // back-off between polls of the barrier generation
 #endif
 
-#ifndef MAPGPU_BAR_FENCE_ACQREL
-#define MAPGPU_BAR_FENCE_ACQREL 0
-#endif
 // the barrier's fences: release before the arrival, acquire after the release (the block's
-// writes, ordered before thread 0's by the block barrier, are covered cumulatively)
-__device__ __forceinline__ void bar_fence()
-{
-#if MAPGPU_BAR_FENCE_ACQREL
-    asm volatile("fence.acq_rel.gpu;" ::: "memory");
-#else
-    __threadfence();
-#endif
-}
+// writes, ordered before thread 0's by the block barrier, are covered cumulatively); a
+// fence.acq_rel.gpu in their place measured the same
+__device__ __forceinline__ void bar_fence() { __threadfence(); }
 
 __device__ __forceinline__ bool grid_barrier(Ctl *ctl, uint32_t p = 3, uint32_t *s_vals = nullptr)
 {
