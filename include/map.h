@@ -240,7 +240,7 @@ MAP_API int map_batch_run(map_graph *g, const map_opts *opts, map_result *result
  * memory (a quarter of hbm_budget_bytes, at most 2 GiB; pageable memory when it
  * is full, which only costs speed), and queued; the oldest queued job is
  * started as soon as a worker is free and its device footprint (about
- * 4 * (3m + 18n) bytes) fits into what is left of hbm_budget_bytes (a job
+ * 4 * (4m + 17n) bytes at its set-up's peak) fits into what is left of hbm_budget_bytes (a job
  * larger than the whole budget runs when nothing else does).  Jobs that arrive
  * while others are running are admitted as slots and memory free up, and the
  * admitted jobs' work overlaps on the device.  Every job gets exactly the result

@@ -60,6 +60,21 @@ int fail(int code, const char *fmt, ...)
         }                                                                                                          \
     } while (0)
 
+// a pointer the kernels may read p through: device or managed memory as it is, page-locked
+// (registered) host memory by its mapped device address; null for pageable host memory
+const uint32_t *device_readable(const uint32_t *p)
+{
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+    if (a.type == cudaMemoryTypeHost) return static_cast<const uint32_t *>(a.devicePointer);
+    return nullptr;
+}
+
 bool is_device_ptr(const void *p)
 {
     if (!p) return false;
@@ -217,6 +232,10 @@ struct map_graph {
     cudaStream_t stream = nullptr;
     uint32_t *rowptr = nullptr, *colidx = nullptr, *rrowptr = nullptr, *rcol = nullptr;
     uint32_t *rpos = nullptr; // positions in colidx of the reader entries
+    // (set-up only) caller arrays the ingest pass reads and copies into rowptr / colidx itself,
+    // instead of a separate copy: device memory, or page-locked host memory the kernels read
+    // over the host link; null when the upload copied them already
+    const uint32_t *in_rowptr = nullptr, *in_colidx = nullptr;
     uint32_t *elog = nullptr; // vertices eliminated in the current run
     uint32_t *acc0 = nullptr, *acc = nullptr, *mval = nullptr;
     uint32_t *list = nullptr;  // 3n: vertices changed in a round, by round mod 3
@@ -686,33 +705,47 @@ int create_graph(uint32_t n, uint64_t m, cudaStream_t s, const char *who, Upload
         return rc;
     }
     mapk::k_acc_init<<<grid_for(g, W, 1), 256, 0, s>>>(n, acc_in, g->acc0, &g->ctl->elim.v);
-    mapk::k_ingest<<<grid_for(g, std::max<uint64_t>(m / 4, n), 1), 256, 0, s>>>(n, g->rowptr, m, g->colidx, g->acc0,
-                                                                             g->rrowptr, &g->ctl->bad);
+    // (each entry's place in its reader list, kept for the scatter; freed at the end of set-up)
+    uint32_t *rank = nullptr;
+    if ((rc = alloc(&rank, m))) {
+        free_graph(g);
+        return rc;
+    }
+    const auto free_rank = [&]() {
+        cudaFreeAsync(rank, s);
+        rank = nullptr;
+    };
+    mapk::k_ingest<<<grid_for(g, std::max<uint64_t>(m / 4, n), 1), 256, 0, s>>>(
+        n, g->in_rowptr ? g->in_rowptr : g->rowptr, g->in_rowptr ? g->rowptr : nullptr, m,
+        g->in_colidx ? g->in_colidx : g->colidx, g->colidx, g->acc0, g->rrowptr, rank, &g->ctl->bad);
+    g->in_rowptr = g->in_colidx = nullptr;
     if ((rc = ck(cudaGetLastError(), "validate")) || (rc = read_ctl(g))) {
+        free_rank();
         free_graph(g);
         return rc;
     }
     if (g->h_ctl->bad) {
+        free_rank();
         free_graph(g);
         return fail(MAP_ERR_CSR, "%s: invalid CSR (decreasing rowptr or colidx out of range)", who);
     }
     g->nacc0 = g->h_ctl->elim.v;
 
-    // reverse CSR: scan of the histogram, scatter
+    // reverse CSR: scan of the histogram, scatter by rank
     if ((rc = scan_inclusive(g->rrowptr, (uint64_t)n + 1, s))) {
+        free_rank();
         free_graph(g);
         return rc;
     }
-    // cursor = rrowptr[0..n) (reuse the list space)
-    if ((rc = ck(cudaMemcpyAsync(g->list, g->rrowptr, (size_t)n * 4, cudaMemcpyDeviceToDevice, s), "cursor"))) {
-        free_graph(g);
-        return rc;
-    }
-    // at least 16 lanes per row: the scatter is bound by the L2 locality of its window of rows
-    // in flight (fewer rows at once measured faster: 9.6 against 14.1 ms for map_create at 2^26)
-    DISPATCH_G(std::max(g->G, 16), (mapk::k_transpose<GG><<<grid_for(g, n, GG), 256, 0, s>>>(n, g->rowptr, g->colidx, g->list,
-                                                                              g->rcol, g->rpos)));
-    if ((rc = ck(cudaGetLastError(), "transpose")) || (rc = ck(cudaStreamSynchronize(s), "create sync"))) {
+#ifndef MAPGPU_TT_BPS
+#define MAPGPU_TT_BPS 4
+#endif
+    mapk::k_transpose_ranked<<<(unsigned)std::max<uint64_t>(1, std::min<uint64_t>(((uint64_t)n + mapk::TT_ROWS - 1) / mapk::TT_ROWS,
+                                                                                 (uint64_t)g->sms * MAPGPU_TT_BPS)),
+                               256, 0, s>>>(n, g->rowptr, g->colidx, rank, g->rrowptr, g->rcol, g->rpos);
+    rc = ck(cudaGetLastError(), "transpose");
+    free_rank();
+    if (rc || (rc = ck(cudaStreamSynchronize(s), "create sync"))) {
         free_graph(g);
         return rc;
     }
@@ -752,8 +785,14 @@ int map_create(uint32_t n, const uint32_t *rowptr, const uint32_t *colidx, const
     const auto kind = [](const void *p) { return is_device_ptr(p) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; };
     return create_graph(n, m, s, "map_create",
                         [&](map_graph *g, uint32_t **acc) -> int {
-                            CK(cudaMemcpyAsync(g->rowptr, rowptr, ((size_t)n + 1) * 4, kind(rowptr), s));
-                            if (m) CK(cudaMemcpyAsync(g->colidx, colidx, m * 4, kind(colidx), s));
+                            // arrays the kernels can read are copied by the ingest pass itself (one
+                            // pass over the link or HBM instead of two); colidx's 128-bit loads want
+                            // it 16-byte aligned
+                            if ((g->in_rowptr = device_readable(rowptr)) == nullptr)
+                                CK(cudaMemcpyAsync(g->rowptr, rowptr, ((size_t)n + 1) * 4, kind(rowptr), s));
+                            const uint32_t *ci = m ? device_readable(colidx) : nullptr;
+                            if (ci && ((uintptr_t)ci & 15u) == 0) g->in_colidx = ci;
+                            else if (m) CK(cudaMemcpyAsync(g->colidx, colidx, m * 4, kind(colidx), s));
                             if (is_device_ptr(acc_bits)) {
                                 *acc = const_cast<uint32_t *>(acc_bits);
                             } else {
@@ -1943,7 +1982,8 @@ struct ServerJob {
 size_t graph_footprint(uint64_t n, uint64_t m)
 {
     const uint64_t W = (n + 31) / 32;
-    const uint64_t words = 2 * (n + 5) + 3 * (m + 4) + 3 * (W + 4) + (n + 4) + 2 * 3 * (n + 4) + 4 * (n + 4) +
+    // (colidx, rcol, rpos, and the set-up's rank array: 4 words per entry at the peak)
+    const uint64_t words = 2 * (n + 5) + 4 * (m + 4) + 3 * (W + 4) + (n + 4) + 2 * 3 * (n + 4) + 4 * (n + 4) +
                            3 * (n + 4) + (1u << 16);
     // the changed-vertex bitmaps of pull rounds
     return (size_t)(words + 3 * (W + 4)) * 4 + sizeof(Ctl) + (1u << 20);

@@ -1868,35 +1868,104 @@ __global__ void k_validate(uint32_t n, const uint32_t *__restrict__ rowptr, uint
 // in bit 31; an entry u >= n sets *bad instead (the graph is then refused, and nothing built
 // from it is used).  Four entries per thread and step (one 128-bit load and store).
 __device__ __forceinline__ uint32_t ingest_one(uint32_t u, uint32_t n, const uint32_t *__restrict__ acc, uint32_t *cnt,
-                                               bool &bad)
+                                               bool &bad, uint32_t &rank)
 {
     if (u >= n) {
         bad = true;
+        rank = 0;
         return u;
     }
-    atomicAdd(cnt + u + 1, 1u);
+    rank = atomicAdd(cnt + u + 1, 1u);
     return u | (((__ldg(acc + (u >> 5)) >> (u & 31u)) & 1u) << 31);
 }
 
-__global__ void k_ingest(uint32_t n, const uint32_t *__restrict__ rowptr, uint64_t m, uint32_t *colidx,
-                         const uint32_t *__restrict__ acc, uint32_t *cnt, uint32_t *bad)
+// Reads rowptr_in and colidx_in and, where the _out array is given (not null), writes the
+// result there: the ingest pass is then also the copy from the caller's array (device memory, or
+// page-locked host memory read over the host link). colidx_in and colidx_out 16-byte aligned
+// (they may be the same array); the inputs are read once each. rank[i] = the number of entries
+// before entry i that hold the same vertex (the count each one's increment returned: entry i's
+// place in that vertex's reader list, in an arbitrary but fixed order).
+__global__ void k_ingest(uint32_t n, const uint32_t *rowptr_in, uint32_t *rowptr_out, uint64_t m,
+                         const uint32_t *colidx_in, uint32_t *colidx_out, const uint32_t *__restrict__ acc,
+                         uint32_t *cnt, uint32_t *rank, uint32_t *bad)
 {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned lane = lane_id();
     bool b = false;
-    for (uint64_t i = tid; i < n; i += stride) b |= __ldg(rowptr + i) > __ldg(rowptr + i + 1);
-    const uint64_t m4 = m / 4;
-    uint4 *c4 = reinterpret_cast<uint4 *>(colidx);
-    for (uint64_t q = tid; q < m4; q += stride) {
-        uint4 w = c4[q];
-        w.x = ingest_one(w.x, n, acc, cnt, b);
-        w.y = ingest_one(w.y, n, acc, cnt, b);
-        w.z = ingest_one(w.z, n, acc, cnt, b);
-        w.w = ingest_one(w.w, n, acc, cnt, b);
-        c4[q] = w;
+    // rowptr[0..n]: warp-uniform steps of 32 entries; a lane's successor entry comes from the next
+    // lane (lane 31 loads it)
+    for (uint64_t i0 = tid - lane; i0 <= n; i0 += stride) {
+        const uint64_t i = i0 + lane;
+        const uint32_t a = i <= n ? rowptr_in[i] : 0u;
+        uint32_t next = __shfl_down_sync(0xFFFFFFFFu, a, 1);
+        if (lane == 31 && i < n) next = rowptr_in[i + 1];
+        if (i < n) b |= a > next;
+        if (rowptr_out && i <= n) rowptr_out[i] = a;
     }
-    for (uint64_t i = m4 * 4 + tid; i < m; i += stride) colidx[i] = ingest_one(colidx[i], n, acc, cnt, b);
-    if (__any_sync(0xFFFFFFFFu, b) && lane_id() == 0) *bad = 1;
+    const uint64_t m4 = m / 4;
+    const uint4 *c4 = reinterpret_cast<const uint4 *>(colidx_in);
+    uint4 *o4 = reinterpret_cast<uint4 *>(colidx_out);
+    uint4 *r4 = reinterpret_cast<uint4 *>(rank);
+    for (uint64_t q = tid; q < m4; q += stride) {
+        uint4 w = c4[q], r;
+        w.x = ingest_one(w.x, n, acc, cnt, b, r.x);
+        w.y = ingest_one(w.y, n, acc, cnt, b, r.y);
+        w.z = ingest_one(w.z, n, acc, cnt, b, r.z);
+        w.w = ingest_one(w.w, n, acc, cnt, b, r.w);
+        o4[q] = w;
+        r4[q] = r;
+    }
+    for (uint64_t i = m4 * 4 + tid; i < m; i += stride) colidx_out[i] = ingest_one(colidx_in[i], n, acc, cnt, b, rank[i]);
+    if (__any_sync(0xFFFFFFFFu, b) && lane == 0) *bad = 1;
+}
+
+// Reverse CSR scatter from the ranks k_ingest recorded: entry i of row w holding u goes to slot
+// rrowptr[u] + rank[i] (rrowptr[u] = the start of u's reader list), with no atomics. A block takes a
+// tile of TT_ROWS consecutive rows (grid-stride over tiles), puts the tile's row starts in shared
+// memory and walks the tile's contiguous entry range with every thread, TT_E entries per thread in
+// flight, finding an entry's row by binary search there: every lane has work whatever the
+// degrees, and colidx and rank are read coalesced. Requires a validated CSR.
+constexpr uint32_t TT_ROWS = 256;
+constexpr int TT_E = 4;
+
+__global__ void __launch_bounds__(256) k_transpose_ranked(uint32_t n, const uint32_t *__restrict__ rowptr,
+                                                          const uint32_t *__restrict__ colidx,
+                                                          const uint32_t *__restrict__ rank,
+                                                          const uint32_t *__restrict__ rrowptr, uint32_t *rcol,
+                                                          uint32_t *rpos)
+{
+    __shared__ uint32_t rs[TT_ROWS + 1];
+    const uint32_t tiles = (uint32_t)(((uint64_t)n + TT_ROWS - 1) / TT_ROWS);
+    for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const uint32_t r0 = t * TT_ROWS;
+        const uint32_t nr = min(TT_ROWS, n - r0);
+        __syncthreads(); // the previous tile's searches are done
+        for (uint32_t k = threadIdx.x; k <= nr; k += blockDim.x) rs[k] = __ldg(rowptr + r0 + k);
+        __syncthreads();
+        const uint64_t e1 = rs[nr];
+        for (uint64_t base = rs[0]; base < e1; base += (uint64_t)blockDim.x * TT_E) {
+            uint32_t slot[TT_E];
+#pragma unroll
+            for (int j = 0; j < TT_E; ++j) {
+                const uint64_t i = base + (uint64_t)j * blockDim.x + threadIdx.x;
+                slot[j] = i < e1 ? __ldg(rrowptr + (__ldg(colidx + i) & 0x7FFFFFFFu)) + __ldg(rank + i) : 0u;
+            }
+#pragma unroll
+            for (int j = 0; j < TT_E; ++j) {
+                const uint64_t i = base + (uint64_t)j * blockDim.x + threadIdx.x;
+                if (i >= e1) continue;
+                uint32_t lo = 0, hi = nr; // rs[lo] <= i < rs[hi]
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (rs[mid] <= (uint32_t)i) lo = mid;
+                    else hi = mid;
+                }
+                rcol[slot[j]] = r0 + lo;
+                rpos[slot[j]] = (uint32_t)i;
+            }
+        }
+    }
 }
 
 // in-degree histogram: cnt[u + 1] += 1 for every edge into u
