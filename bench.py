@@ -22,6 +22,7 @@ Under torchrun (N > 1) every rank solves its own replica of the graph on its own
 from __future__ import annotations
 
 import argparse
+import faulthandler
 import json
 import os
 import statistics
@@ -341,8 +342,10 @@ def batched_leg(pkg, np, torch, stream, count=256, steps=2):
 def serving_leg(pkg, np, rates=(50, 100, 200, 500, 1000, 2000), jobs=2000, max_arrival_s=12.0, slots=8):
     """Poisson arrivals of verification jobs (sizes lognormal, median 1e5, sigma 1.5, within
     [1e3, 1e7]; half process products with 4-9 processes of 5-7 states, half layered graphs),
-    served with continuous admission by `slots` workers, against the same schedule served one job
-    at a time in arrival order (one worker).  Both serve every job on the asynchronous schedule
+    served with continuous admission and batching by `slots` workers (the jobs queued behind the
+    one a worker takes share its run), against the same schedule served one job at a time in
+    arrival order (one worker, no batching), and, at the rates where jobs queue up, against
+    `slots` workers running one job each (no batching).  All serve every job on the asynchronous schedule
     (same verdict, witness, outer count and map as the synchronous one).  Latency = submission to
     result, end to end (copy to the device, set-up, run, map back), split per job into the wait
     for a worker, map_create and the run with the map's copy back.  `jobs` arrivals per rate, but
@@ -358,12 +361,12 @@ def serving_leg(pkg, np, rates=(50, 100, 200, 500, 1000, 2000), jobs=2000, max_a
         graphs = list(ex.map(lambda i: mapgen.arrival_graph(arr, i), range(jobs)))
     bits = [pkg.pack_bits(g.acc) for g in graphs]
 
-    def serve(rate, nslots):
+    def serve(rate, nslots, max_batch=0):
         t_arr = arr["t"] / rate
         k = int(min(jobs, max(1, np.searchsorted(t_arr, max_arrival_s))))
         sub, done = [0.0] * k, [None] * k
         ids, res = [None] * k, [None] * k
-        with pkg.Server(slots=nslots) as sv:
+        with pkg.Server(slots=nslots, max_batch=max_batch) as sv:
             t0 = time.perf_counter()
 
             def submitter():
@@ -398,6 +401,8 @@ def serving_leg(pkg, np, rates=(50, 100, 200, 500, 1000, 2000), jobs=2000, max_a
 
         return {"jobs": k, "jobs_per_s": k / span, "p50_ms": float(np.percentile(lat, 50)),
                 "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+                "jobs_per_run_mean": float(np.mean([r.batch_jobs for r in res])),
+                "jobs_per_run_max": int(max(r.batch_jobs for r in res)),
                 "phases_ms": {"wait_for_worker": pct([r.queue_ms for r in res]),
                               "map_create": pct([r.setup_ms for r in res]),
                               "run_and_map_back": pct([r.run_ms for r in res])}}
@@ -407,14 +412,18 @@ def serving_leg(pkg, np, rates=(50, 100, 200, 500, 1000, 2000), jobs=2000, max_a
                        "asynchronous schedule",
            "vertices": int(sum(g.n for g in graphs)), "slots": slots, "rates": {}}
     for rate in rates:
-        out["rates"][str(rate)] = {"continuous": serve(rate, slots), "fifo_one_at_a_time": serve(rate, 1)}
+        r = {"continuous": serve(rate, slots), "fifo_one_at_a_time": serve(rate, 1, max_batch=1)}
+        if rate >= 500:
+            r["continuous_no_batching"] = serve(rate, slots, max_batch=1)
+        out["rates"][str(rate)] = r
     return out
 
 
 def main():
+    faulthandler.enable()  # a fatal signal prints every thread's Python stack
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--sched", type=int, default=1,

@@ -154,7 +154,7 @@ typedef struct {
     uint64_t frontier_rows;   /* frontier rows summed over the rounds after the first (single-
                                  graph ASYNC runs: the vertices that pushed) */
     uint32_t status;          /* map_status of this graph's run (batched runs report one per graph) */
-    uint32_t reserved;
+    uint32_t batch_jobs;      /* served jobs: how many jobs shared this job's run (1: it ran alone); else 0 */
     double queue_ms;          /* served jobs (map_poll): from map_submit until a worker took the job */
     double setup_ms;          /* served jobs: map_create (copy to the device, validation, readers) */
     double run_ms;            /* served jobs: the run until the map is back in host memory (host clock) */
@@ -235,16 +235,25 @@ MAP_API int map_batch_run(map_graph *g, const map_opts *opts, map_result *result
 
 /*
  * Serving: verification jobs submitted over time and run with continuous
- * admission.  The server has max_slots worker threads, each with its own CUDA
- * stream.  A job is copied at submission, into the server's pinned staging
- * memory (a quarter of hbm_budget_bytes, at most 2 GiB; pageable memory when it
- * is full, which only costs speed), and queued; the oldest queued job is
- * started as soon as a worker is free and its device footprint (about
- * 4 * (4m + 17n) bytes at its set-up's peak) fits into what is left of hbm_budget_bytes (a job
- * larger than the whole budget runs when nothing else does).  Jobs that arrive
- * while others are running are admitted as slots and memory free up, and the
- * admitted jobs' work overlaps on the device.  Every job gets exactly the result
- * map_create + map_run give it.
+ * admission and batching.  The server has max_slots worker threads, each with
+ * its own CUDA stream.  A job is copied at submission, into the server's pinned
+ * staging memory (a quarter of hbm_budget_bytes, at most 2 GiB; pageable memory
+ * when it is full, which only costs speed), and queued; the oldest queued job
+ * is started as soon as a worker is free and its device footprint (about
+ * 4 * (4m + 17n) bytes at its set-up's peak) fits into what is left of
+ * hbm_budget_bytes (a job larger than the whole budget runs when nothing else
+ * does).  When no other worker is waiting for work, queued jobs join its run,
+ * as one batched run (see map_batch_create), oldest first, while they fit into
+ * the budget and may share it: the same schedule, flags and timeout, no early
+ * exit, limit or MAP_FLAG_PROFILE, and at most 2^20 vertices each (a batched
+ * run lasts as long as its slowest graph, so larger jobs run alone); at most
+ * 128 jobs (map_server_batch_limit) and 2^26 vertices per run.  Jobs that
+ * cannot join keep their place in the queue.  Jobs that arrive while
+ * others are running are admitted as slots and memory free up, and the
+ * admitted jobs' work overlaps on the device.  Every job gets exactly the
+ * result map_create + map_run give it (map_result.batch_jobs tells how many
+ * jobs shared its run); a batch whose set-up or run fails is rerun job by job,
+ * so an error is reported by the job that causes it only.
  *
  * map_server_create -- hbm_budget_bytes = 0: half of the free device memory.
  *   The calling thread's current device is used.
@@ -254,6 +263,8 @@ MAP_API int map_batch_run(map_graph *g, const map_opts *opts, map_result *result
  *   otherwise the job's status, with res and (optional) map_out (n entries,
  *   host memory) filled, and the job and its staging memory are released (poll
  *   it once).
+ * map_server_batch_limit -- at most max_jobs (1..1024) jobs share one run from
+ *   now on (default 128; 1: every job runs alone).
  * map_server_destroy -- finishes the jobs already admitted and queued, then
  *   frees everything; unpolled results are discarded.
  * The server's calls may come from any host threads.  A job that fails (for
@@ -270,6 +281,7 @@ MAP_API int map_server_create(size_t hbm_budget_bytes, uint32_t max_slots, map_s
 MAP_API int map_submit(map_server *sv, uint32_t n, const uint32_t *rowptr, const uint32_t *colidx,
                        const uint32_t *acc_bits, const map_opts *opts, uint64_t *job_id);
 MAP_API int map_poll(map_server *sv, uint64_t job_id, map_result *res, uint32_t *map_out);
+MAP_API int map_server_batch_limit(map_server *sv, uint32_t max_jobs);
 MAP_API int map_server_destroy(map_server *sv);
 
 /*

@@ -37,6 +37,7 @@ STATUS_NAMES = ["MAP_OK", "MAP_ERR_ARG", "MAP_ERR_CSR", "MAP_ERR_OOM", "MAP_ERR_
 # exported symbols of include/map.h (checked by the tests)
 EXPORTS = ["map_create", "map_run", "map_destroy", "map_graph_info", "map_last_error", "map_run_static",
            "map_batch_create", "map_batch_run", "map_server_create", "map_submit", "map_poll", "map_server_destroy",
+           "map_server_batch_limit",
            "map_autotune", "map_lasso", "map_create_reduced", "map_graph_vertex_ids", "map_graph_csr",
            "map_grow_create", "map_append"]
 MAP_STATIC_MAX_N = 65536
@@ -80,7 +81,7 @@ class MapResult(ctypes.Structure):
         ("check_ms", ctypes.c_double),
         ("frontier_rows", ctypes.c_uint64),
         ("status", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32),
+        ("batch_jobs", ctypes.c_uint32),
         ("queue_ms", ctypes.c_double),
         ("setup_ms", ctypes.c_double),
         ("run_ms", ctypes.c_double),
@@ -165,6 +166,7 @@ def load(path: str = LIB_PATH):
     lib.map_submit.argtypes = [vp, u32, vp, vp, vp, ctypes.POINTER(MapOpts), ctypes.POINTER(ctypes.c_uint64)]
     lib.map_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(MapResult), vp]
     lib.map_server_destroy.argtypes = [vp]
+    lib.map_server_batch_limit.argtypes = [vp, u32]
     lib.map_autotune.argtypes = [vp, u32, ctypes.POINTER(TuneResult)]
     lib.map_lasso.argtypes = [vp, u32, u32, vp, u32, ctypes.POINTER(u32), ctypes.POINTER(u32)]
     lib.map_create_reduced.argtypes = [u32, vp, vp, vp, vp, vp, ctypes.POINTER(vp)]
@@ -312,6 +314,7 @@ class RunResult:
     queue_ms: float = 0.0  # served jobs: waiting for a worker
     setup_ms: float = 0.0  # served jobs: map_create
     run_ms: float = 0.0  # served jobs: run and map back to host memory
+    batch_jobs: int = 0  # served jobs: how many jobs shared the job's run (1: alone)
 
 
 def map_run(handle, sched: int = MAP_SCHED_SYNC, max_outer: int = 0, max_inner: int = 0, flags: int = 0,
@@ -438,27 +441,34 @@ def _result(r, trace=()):
     return RunResult(r.status, r.verdict, r.witness, r.outer_iters, [], r.inner_iters, bool(r.inner_canonical),
                      r.relaxations, r.edges_total, r.device_ms, r.dense_ms, r.dense_launches, r.accepting_left,
                      r.launches, r.round_ms, r.check_ms, r.frontier_rows, list(trace), r.queue_ms, r.setup_ms,
-                     r.run_ms)
+                     r.run_ms, r.batch_jobs)
 
 
 class Server:
     """Continuous-admission serving (map_server_* in include/map.h)."""
 
-    def __init__(self, hbm_budget_bytes: int = 0, slots: int = 4):
+    def __init__(self, hbm_budget_bytes: int = 0, slots: int = 4, max_batch: int = 0):
+        """max_batch: jobs per run at most (0: the library's default; 1: every job alone)."""
         lib = load()
         self.handle = ctypes.c_void_p()
         rc = lib.map_server_create(hbm_budget_bytes, slots, ctypes.byref(self.handle))
         if rc != MAP_OK:
             raise MapError(rc, "map_server_create", last_error())
         self.sizes = {}
+        if max_batch:
+            rc = lib.map_server_batch_limit(self.handle, max_batch)
+            if rc != MAP_OK:
+                self.close()
+                raise MapError(rc, "map_server_batch_limit", last_error())
 
-    def submit(self, n, rowptr, colidx, acc_bits, sched: int = MAP_SCHED_SYNC, max_outer: int = 0) -> int:
+    def submit(self, n, rowptr, colidx, acc_bits, sched: int = MAP_SCHED_SYNC, max_outer: int = 0,
+               flags: int = 0) -> int:
         lib = load()
         rp = np.ascontiguousarray(rowptr, dtype=np.uint32)
         ci = np.ascontiguousarray(colidx, dtype=np.uint32) if colidx is not None else None
         ab = np.ascontiguousarray(acc_bits, dtype=np.uint32)
         opts = MapOpts()
-        opts.sched, opts.max_outer = sched, max_outer
+        opts.sched, opts.max_outer, opts.flags = sched, max_outer, flags
         jid = ctypes.c_uint64()
         rc = lib.map_submit(self.handle, n, rp.ctypes.data, ci.ctypes.data if ci is not None and ci.size else None,
                             ab.ctypes.data, ctypes.byref(opts), ctypes.byref(jid))

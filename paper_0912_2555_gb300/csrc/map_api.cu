@@ -997,6 +997,9 @@ static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint
     }
     g->dirty = c.status != mapk::ST_OK || c.early_hit;
     if (c.status == mapk::ST_LIMIT) return fail(MAP_ERR_LIMIT, "map_run: max_outer or max_inner reached");
+    if (c.status == mapk::ST_TIMEOUT && c.gave_up)
+        return fail(MAP_ERR_TIMEOUT, "map_run: a bounded device wait (%s) gave up after seconds without progress",
+                    c.gave_up == 1 ? "grid barrier" : "hand-back of one-block rounds");
     if (c.status == mapk::ST_TIMEOUT)
         return fail(MAP_ERR_TIMEOUT, "map_run: stopped after timeout_ms = %u", opts.timeout_ms ? opts.timeout_ms : 120000u);
     return MAP_OK;
@@ -1894,15 +1897,17 @@ extern "C" int map_run_static(uint32_t n, const uint32_t *rowptr, const uint32_t
 }
 
 // ============================================================================
-// Serving: a request loop with continuous admission (map_server_*).
+// Serving: a request loop with continuous admission and batching (map_server_*).
 //
 // Jobs are copied at submission and queued.  Each of the server's worker
 // threads owns a CUDA stream; a worker takes the oldest queued job as soon as
-// the job's device footprint fits into what is left of the memory budget, and
-// runs it (map_create, map_run, map output, map_destroy) on its stream.  Jobs
-// that arrive while others are on the GPU are admitted as workers and memory
-// free up, and the work of admitted jobs overlaps on the device.  Allocation is
-// stream-ordered, so one job's set-up does not stall the others.
+// the job's device footprint fits into what is left of the memory budget, with
+// the jobs queued right behind it that may share its run, and runs them on its
+// stream: one job alone (map_create, map_run, map output, map_destroy), several
+// as one batched run (map_batch_create, map_batch_run).  Jobs that arrive while
+// others are on the GPU are admitted as workers and memory free up, and the work
+// of admitted jobs overlaps on the device.  Allocation is stream-ordered, so one
+// job's set-up does not stall the others.
 // ============================================================================
 
 namespace {
@@ -1978,6 +1983,14 @@ struct ServerJob {
     int inject_alloc = 0; // test hook: the k-th device allocation of its map_create fails
 };
 
+// jobs that may share a batched run, and the size of one
+constexpr uint32_t kBatchFlags = MAP_FLAG_FRONTIER_START | MAP_FLAG_DENSE_START | MAP_FLAG_PUSH | MAP_FLAG_PULL;
+constexpr uint32_t kMaxBatchJobs = 128;
+constexpr uint64_t kMaxBatchVertices = 1ull << 26;
+// a batched run lasts as long as its slowest graph: larger jobs run alone, so that the small
+// ones batched together do not wait for them
+constexpr uint32_t kMaxBatchedJobN = 1u << 20;
+
 // device bytes of a graph: the allocations of create_graph
 size_t graph_footprint(uint64_t n, uint64_t m)
 {
@@ -1997,6 +2010,8 @@ struct map_server {
     size_t used = 0;
     int device = 0;
     uint32_t slots = 1;
+    uint32_t max_batch = kMaxBatchJobs; // jobs per run at most (map_server_batch_limit)
+    uint32_t idle = 0;                  // workers waiting for a job
     bool stop = false;
     uint64_t next_id = 1;
     std::mutex mu;
@@ -2010,50 +2025,93 @@ struct map_server {
 
 namespace {
 
-void server_worker(map_server *sv, cudaStream_t stream)
+// a served job's inputs: its arena slot (page-locked), or its own vectors
+void job_inputs(const ServerJob *job, const uint32_t *&rp, const uint32_t *&ci, const uint32_t *&ab)
 {
-    cudaSetDevice(sv->device);
-    uint32_t *stage = nullptr; // pinned staging for the job's inputs
-    size_t stage_words = 0;
-    struct Release {
-        uint32_t *&p;
-        ~Release()
-        {
-            if (p) cudaFreeHost(p);
-        }
-    } release{stage};
-    for (;;) {
-        ServerJob *job = nullptr;
-        {
-            std::unique_lock<std::mutex> lk(sv->mu);
-            sv->cv_work.wait(lk, [&] {
-                if (sv->stop) return true;
-                if (sv->queue.empty()) return false;
-                const size_t fp = sv->queue.front()->footprint;
-                return sv->used + fp <= sv->budget || sv->used == 0; // a job larger than the budget runs alone
-            });
-            if (sv->stop && sv->queue.empty()) return;
-            if (sv->queue.empty()) continue;
-            job = sv->queue.front();
-            sv->queue.pop_front();
-            sv->used += job->footprint;
-        }
-        // a job outside the arena: its inputs into this worker's pinned staging buffer (grown
-        // when needed), so that the copies to the device are asynchronous DMA transfers
-        const size_t words = (size_t)job->n + 1 + job->m + job->acc.size();
-        if (!job->pin && words > stage_words) {
-            if (stage) cudaFreeHost(stage);
-            stage = nullptr;
-            stage_words = 0;
-            if (cudaMallocHost((void **)&stage, words * 4 * 5 / 4) == cudaSuccess) stage_words = words * 5 / 4;
-            else cudaGetLastError();
-        }
-        const uint32_t *rp = job->rowptr.data(), *ci = job->m ? job->colidx.data() : nullptr, *ab = job->acc.data();
-        if (job->pin) { // already in pinned memory
-            rp = job->pin;
-            ci = job->m ? job->pin + job->n + 1 : nullptr;
-            ab = job->pin + job->n + 1 + job->m;
-        } else if (stage) {
+    if (job->pin) {
+        rp = job->pin;
+        ci = job->m ? job->pin + job->n + 1 : nullptr;
+        ab = job->pin + job->n + 1 + job->m;
+    } else {
+        rp = job->rowptr.data();
+        ci = job->m ? job->colidx.data() : nullptr;
+        ab = job->acc.data();
+    }
+}
+
+// Jobs that may share a batched run: the batch engine gives every graph exactly its result alone
+// under the options it offers (schedule, start, push / pull); early exit, limits, profiling and an
+// injected allocation failure keep a job to itself.
+
+bool batchable(const ServerJob *j)
+{
+    return j->n <= kMaxBatchedJobN && j->inject_alloc == 0 && (j->opts.flags & ~kBatchFlags) == 0 &&
+           j->opts.max_outer == 0 && j->opts.max_inner == 0;
+}
+
+bool same_run(const map_opts &a, const map_opts &b)
+{
+    return a.sched == b.sched && a.flags == b.flags && a.timeout_ms == b.timeout_ms;
+}
+
+// grow a worker's page-locked staging buffer to at least `words` (allocating page-locked memory
+// synchronises the device, so it grows by a quarter more than asked and is kept)
+void ensure_stage(uint32_t *&stage, size_t &stage_words, size_t words)
+{
+    if (words <= stage_words) return;
+    if (stage) cudaFreeHost(stage);
+    stage = nullptr;
+    stage_words = 0;
+    if (cudaMallocHost((void **)&stage, words * 4 * 5 / 4) == cudaSuccess) stage_words = words * 5 / 4;
+    else cudaGetLastError();
+}
+
+// The fix-point kernel is a cooperative launch: with every resident slot of the device (the
+// single-graph shape) a job's rounds cannot run beside another job's.  Each worker's run takes an
+// even share of the slots, so the rounds of all workers fit side by side.
+void share_rounds(map_server *sv, map_graph *g)
+{
+    if (sv->slots <= 1) return;
+    const int share = std::max(1, (int)((int64_t)g->sms * g->occ_rounds / (int64_t)sv->slots));
+    g->rounds_grid = std::min(g->rounds_grid, share);
+}
+
+using Clock = std::chrono::steady_clock;
+
+void finish_job(map_server *sv, ServerJob *job, int rc, Clock::time_point t_take, Clock::time_point t_created,
+                uint32_t batch_jobs)
+{
+    using ms = std::chrono::duration<double, std::milli>;
+    const auto t_end = Clock::now();
+    if (rc != MAP_OK && job->err.empty()) job->err = g_err;
+    job->res.queue_ms = ms(t_take - job->t_submit).count();
+    job->res.setup_ms = ms(t_created - t_take).count();
+    job->res.run_ms = ms(t_end - t_created).count();
+    job->res.status = (uint32_t)rc;
+    job->res.batch_jobs = batch_jobs;
+    // the job's inputs are not needed any more
+    std::vector<uint32_t>().swap(job->rowptr);
+    std::vector<uint32_t>().swap(job->colidx);
+    std::vector<uint32_t>().swap(job->acc);
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        job->status = rc;
+        job->done = true;
+        sv->used -= job->footprint;
+    }
+    sv->cv_work.notify_all();
+}
+
+// one job alone: map_create, map_run, map output, map_destroy
+void serve_one(map_server *sv, cudaStream_t stream, ServerJob *job, uint32_t *&stage, size_t &stage_words)
+{
+    const uint32_t *rp, *ci, *ab;
+    job_inputs(job, rp, ci, ab);
+    // a job outside the arena: its inputs into this worker's page-locked staging buffer, so that
+    // the set-up reads them over the link directly
+    if (!job->pin) {
+        ensure_stage(stage, stage_words, (size_t)job->n + 1 + job->m + job->acc.size());
+        if (stage) {
             uint32_t *p = stage;
             memcpy(p, rp, ((size_t)job->n + 1) * 4);
             rp = p;
@@ -2066,53 +2124,150 @@ void server_worker(map_server *sv, cudaStream_t stream)
             memcpy(p, ab, job->acc.size() * 4);
             ab = p;
         }
-        NvtxRange job_range("served job");
-        const auto t_take = std::chrono::steady_clock::now();
-        map_graph *g = nullptr;
-        t_inject_alloc = job->inject_alloc;
-        int rc = map_create(job->n, rp, ci, ab, stream, &g);
-        t_inject_alloc = 0;
-        const auto t_created = std::chrono::steady_clock::now();
-        if (rc == MAP_OK && sv->slots > 1) {
-            // the fix-point kernel is a cooperative launch: with every resident slot of the device
-            // (the single-graph shape) a job's rounds cannot run beside another job's.  Each worker's
-            // job takes an even share of the slots, so the rounds of all workers fit side by side.
-            const int share = std::max(1, (int)((int64_t)g->sms * g->occ_rounds / (int64_t)sv->slots));
-            g->rounds_grid = std::min(g->rounds_grid, share);
+    }
+    NvtxRange job_range("served job");
+    const auto t_take = Clock::now();
+    map_graph *g = nullptr;
+    t_inject_alloc = job->inject_alloc;
+    int rc = map_create(job->n, rp, ci, ab, stream, &g);
+    t_inject_alloc = 0;
+    const auto t_created = Clock::now();
+    if (rc == MAP_OK) {
+        share_rounds(sv, g);
+        // the whole run as one CUDA graph; the map comes back by DMA into page-locked memory (the
+        // job's arena slot, read out by map_poll, or the staging buffer: map_create has consumed
+        // the inputs)
+        if (job->pin) {
+            rc = run_impl(g, &job->opts, &job->res, job->pin);
+        } else {
+            job->map.resize(job->n);
+            rc = run_impl(g, &job->opts, &job->res, stage ? stage : job->map.data());
+            if (stage && rc == MAP_OK) memcpy(job->map.data(), stage, (size_t)job->n * 4);
         }
-        if (rc == MAP_OK) {
-            // the whole run as one CUDA graph (building it costs well under a millisecond); the
-            // map comes back by DMA into the staging buffer (map_create has consumed the inputs)
-            if (job->pin) { // into the job's arena slot, read out by map_poll
-                rc = run_impl(g, &job->opts, &job->res, job->pin);
+        map_destroy(g);
+    }
+    finish_job(sv, job, rc, t_take, t_created, 1);
+}
+
+// Continuous batching: jobs that were queued together and may share a run are joined into one
+// batched run (map_batch_create / map_batch_run), every one with exactly its own result.  If the
+// batch cannot be set up (memory, or an invalid graph among them), each job runs alone, so a
+// failure is reported by the job that causes it only.
+void serve_batch(map_server *sv, cudaStream_t stream, std::vector<ServerJob *> &batch, uint32_t *&stage,
+                 size_t &stage_words)
+{
+    const uint32_t count = (uint32_t)batch.size();
+    std::vector<uint32_t> ns(count);
+    std::vector<const uint32_t *> rps(count), cis(count), abs(count);
+    uint64_t total_n = 0;
+    for (uint32_t c = 0; c < count; ++c) {
+        ns[c] = batch[c]->n;
+        job_inputs(batch[c], rps[c], cis[c], abs[c]);
+        total_n += batch[c]->n;
+    }
+    NvtxRange job_range("served batch");
+    const auto t_take = Clock::now();
+    map_graph *g = nullptr;
+    int rc = map_batch_create(count, ns.data(), rps.data(), cis.data(), abs.data(), stream, &g);
+    const auto t_created = Clock::now();
+    if (rc != MAP_OK) {
+        for (ServerJob *job : batch) serve_one(sv, stream, job, stage, stage_words);
+        return;
+    }
+    share_rounds(sv, g);
+    // the union's map vectors, one after another, into page-locked staging (pageable when it
+    // cannot grow), then into each job's slot
+    ensure_stage(stage, stage_words, total_n);
+    std::vector<uint32_t> pageable;
+    uint32_t *maps = stage;
+    if (!maps) {
+        pageable.resize(total_n);
+        maps = pageable.data();
+    }
+    std::vector<map_result> res(count);
+    const int brc = map_batch_run(g, &batch[0]->opts, res.data(), maps, nullptr, 0);
+    const std::string err = g_err;
+    map_destroy(g);
+    if (brc != MAP_OK && brc != MAP_ERR_LIMIT && brc != MAP_ERR_TIMEOUT) { // no per-graph result
+        for (ServerJob *job : batch) serve_one(sv, stream, job, stage, stage_words);
+        return;
+    }
+    uint64_t off = 0;
+    for (uint32_t c = 0; c < count; ++c) {
+        ServerJob *job = batch[c];
+        const int rc_c = (int)res[c].status; // (a limit or timeout: each graph's own status)
+        job->res = res[c];
+        if (rc_c == MAP_OK) {
+            if (job->pin) {
+                memcpy(job->pin, maps + off, (size_t)job->n * 4);
             } else {
-                job->map.resize(job->n);
-                rc = run_impl(g, &job->opts, &job->res, stage ? stage : job->map.data());
-                if (stage && rc == MAP_OK) memcpy(job->map.data(), stage, (size_t)job->n * 4);
+                job->map.assign(maps + off, maps + off + job->n);
             }
-            job->res.status = (uint32_t)rc;
-            map_destroy(g);
+        } else {
+            job->err = err;
         }
-        if (rc != MAP_OK) job->err = g_err;
+        off += job->n;
+        finish_job(sv, job, rc_c, t_take, t_created, count);
+    }
+}
+
+void server_worker(map_server *sv, cudaStream_t stream)
+{
+    cudaSetDevice(sv->device);
+    uint32_t *stage = nullptr; // page-locked staging for inputs and maps
+    size_t stage_words = 0;
+    struct Release {
+        uint32_t *&p;
+        ~Release()
         {
-            using ms = std::chrono::duration<double, std::milli>;
-            const auto t_end = std::chrono::steady_clock::now();
-            job->res.queue_ms = ms(t_take - job->t_submit).count();
-            job->res.setup_ms = ms(t_created - t_take).count();
-            job->res.run_ms = ms(t_end - t_created).count();
-            job->res.status = (uint32_t)rc;
+            if (p) cudaFreeHost(p);
         }
-        // the job's inputs are not needed any more
-        std::vector<uint32_t>().swap(job->rowptr);
-        std::vector<uint32_t>().swap(job->colidx);
-        std::vector<uint32_t>().swap(job->acc);
+    } release{stage};
+    for (;;) {
+        std::vector<ServerJob *> batch;
         {
-            std::lock_guard<std::mutex> lk(sv->mu);
-            job->status = rc;
-            job->done = true;
-            sv->used -= job->footprint;
+            std::unique_lock<std::mutex> lk(sv->mu);
+            ++sv->idle;
+            sv->cv_work.wait(lk, [&] {
+                if (sv->stop) return true;
+                if (sv->queue.empty()) return false;
+                const size_t fp = sv->queue.front()->footprint;
+                return sv->used + fp <= sv->budget || sv->used == 0; // a job larger than the budget runs alone
+            });
+            --sv->idle;
+            if (sv->stop && sv->queue.empty()) return;
+            if (sv->queue.empty()) continue;
+            ServerJob *job = sv->queue.front();
+            sv->queue.pop_front();
+            sv->used += job->footprint;
+            batch.push_back(job);
+            // the jobs queued right behind it join its run while they may share it and fit, when no
+            // other worker is waiting to take them (a load the workers keep up with runs job by
+            // job, at the latency of a job alone)
+            if (batchable(job) && sv->idle == 0) {
+                // (jobs that cannot join stay queued in their order for the next worker)
+                uint64_t un = job->n, um = job->m;
+                uint32_t looked = 0;
+                for (auto it = sv->queue.begin(); it != sv->queue.end() && batch.size() < sv->max_batch &&
+                                                  looked < 4 * sv->max_batch;
+                     ++looked) {
+                    ServerJob *j = *it;
+                    if (!batchable(j) || !same_run(j->opts, job->opts) || un + j->n > kMaxBatchVertices ||
+                        um + j->m >= 0xFFFFFFFFull) {
+                        ++it;
+                        continue;
+                    }
+                    if (sv->used + j->footprint > sv->budget) break; // the budget is full
+                    it = sv->queue.erase(it);
+                    sv->used += j->footprint;
+                    un += j->n;
+                    um += j->m;
+                    batch.push_back(j);
+                }
+            }
         }
-        sv->cv_work.notify_all();
+        if (batch.size() == 1) serve_one(sv, stream, batch[0], stage, stage_words);
+        else serve_batch(sv, stream, batch, stage, stage_words);
     }
 }
 
@@ -2219,6 +2374,16 @@ int map_submit(map_server *sv, uint32_t n, const uint32_t *rowptr, const uint32_
         *job_id = job->id;
     }
     sv->cv_work.notify_all();
+    return MAP_OK;
+}
+
+int map_server_batch_limit(map_server *sv, uint32_t max_jobs)
+{
+    g_err.clear();
+    if (!sv || max_jobs == 0 || max_jobs > 1024)
+        return fail(MAP_ERR_ARG, "map_server_batch_limit: NULL server or max_jobs outside 1..1024");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->max_batch = max_jobs;
     return MAP_OK;
 }
 

@@ -107,6 +107,8 @@ struct Ctl {
     uint32_t solo_fmax;    //   frontier rows to clear) runs in block 0 alone (0: never)
     uint32_t solo_r, solo_nl, solo_nf, solo_status; // block 0's state when it hands back
     uint32_t lc_passes;    // asynchronous single graphs: block-local passes per round
+    uint32_t gave_up;      // a bounded device wait gave up (ST_TIMEOUT): 1 = grid barrier, 2 = the
+    uint32_t pad1;         //   hand-back of one-block rounds; 0 = none (the time limit, if any)
     // %globaltimer stamps of the phases (ns), summed over the run: the end of the last phase
     // (t_mark), the dense rounds, the fix-point rounds, the self-map tests and eliminations.  Each
     // phase runs from the end of the one before it, so gaps between launches count to the next.
@@ -373,9 +375,11 @@ __device__ __forceinline__ void default_stop(const Ctl *c, unsigned long long h)
     if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(c, h, 0);
 }
 
+// (differences of %globaltimer readings are taken signed: a reading on another SM may lag the
+// one that set t0 by a little, and that must not wrap to a huge elapsed time)
 __device__ __forceinline__ bool timed_out(volatile Ctl *v)
 {
-    return global_ns() - v->t0 > v->timeout_ns;
+    return (int64_t)(global_ns() - v->t0) > (int64_t)v->timeout_ns;
 }
 
 // After round 1 (the dense round) of an outer iteration: list[1] holds the
@@ -384,8 +388,11 @@ __device__ __forceinline__ bool timed_out(volatile Ctl *v)
 __device__ __forceinline__ void phase_end(volatile Ctl *v, volatile uint64_t *acc)
 {
     const uint64_t now = global_ns();
-    *acc = *acc + (now - v->t_mark);
-    v->t_mark = now;
+    const int64_t d = (int64_t)(now - v->t_mark);
+    if (d > 0) { // (a lagging reading adds nothing and does not move the mark back)
+        *acc = *acc + (uint64_t)d;
+        v->t_mark = now;
+    }
 }
 
 __device__ void epilogue_dense(Ctl *c)
@@ -925,6 +932,7 @@ __device__ __forceinline__ bool grid_barrier(Ctl *ctl, uint32_t p = 3, uint32_t 
             for (uint32_t it = 0; *(volatile uint32_t *)&ctl->bar_gen.v == gen; ++it) {
                 if (it > BAR_SPIN_LIMIT) {
                     ok = 0;
+                    ((volatile Ctl *)ctl)->gave_up = 1;
                     break;
                 }
                 if (it > 16) __nanosleep(MAPGPU_BAR_SLEEP_NS);
@@ -1233,6 +1241,7 @@ __device__ __forceinline__ bool solo_wait(Ctl *ctl, uint32_t *seen, uint32_t *s_
                 const uint32_t b = v->solo_beat.v;
                 if (b == beat && ++still > SOLO_BEAT_CHECKS) {
                     ok = 0;
+                    v->gave_up = 2;
                     break;
                 }
                 if (b != beat) still = 0;

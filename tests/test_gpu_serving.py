@@ -141,3 +141,66 @@ def test_injected_allocation_failure_fails_only_that_job(pkg, monkeypatch):
             got = sv.poll(jid)
             time.sleep(0.001)
         assert np.array_equal(got[1], want[2].map)
+
+
+def test_queued_jobs_share_batched_runs(pkg):
+    """Continuous batching: with one worker busy on a larger job, the jobs queued behind it are
+    joined into batched runs (jobs with the same schedule and start only; early exit keeps a job
+    to itself).  Every job still gets exactly its own result, and a job with an invalid graph
+    fails alone: its batch falls back to single runs."""
+    big = mapgen.layered_graph(4_000_000, 240, seed=8)
+    gs, scheds, flags = [], [], []
+    for seed in range(48):
+        rng = np.random.default_rng(7000 + seed)
+        if seed % 6 == 5:
+            g = mapgen.layered_graph(int(rng.integers(2000, 30000)), 6, seed=seed, plant=bool(seed % 2))
+        else:
+            g = mapgen.tiny_graph(seed + 300, int(rng.integers(1, 400)), max_deg=int(rng.integers(0, 6)),
+                                  acc_p=float(rng.choice([0.0, 0.1, 0.5])))
+        gs.append(g)
+        scheds.append(0 if (seed // 12) % 2 == 0 else 1)  # runs of 12 sync jobs, then 12 async ones
+        flags.append(pkg.MAP_FLAG_EARLY_EXIT if seed == 30 else (pkg.MAP_FLAG_FRONTIER_START if seed % 7 == 3 else 0))
+    want = [oracle.run_graph(g) for g in gs]
+    bad_at = 20  # an entry >= n: the graph is refused
+    bad_rowptr = np.array([0, 1, 2], np.uint32)
+    bad_colidx = np.array([1, 5], np.uint32)
+    with pkg.Server(slots=1) as sv:
+        first = sv.submit(big.n, big.rowptr, big.colidx, pkg.pack_bits(big.acc))
+        ids = []
+        for i, g in enumerate(gs):
+            if i == bad_at:
+                ids.append(sv.submit(2, bad_rowptr, bad_colidx, np.array([3], np.uint32), sched=scheds[i]))
+            ids.append(sv.submit(g.n, g.rowptr, g.colidx if g.m else None, pkg.pack_bits(g.acc), sched=scheds[i],
+                                 flags=flags[i]))
+        deadline = time.time() + 120
+        done = {}
+        while len(done) < len(ids) + 1 and time.time() < deadline:
+            for jid in [first] + ids:
+                if jid in done:
+                    continue
+                try:
+                    got = sv.poll(jid)
+                except pkg.MapError as e:
+                    got = e
+                if got is not None:
+                    done[jid] = got
+            time.sleep(0.001)
+    assert len(done) == len(ids) + 1
+    bad_id = ids.pop(bad_at)
+    assert isinstance(done[bad_id], pkg.MapError) and done[bad_id].code == pkg.MAP_ERR_CSR
+    batched = 0
+    for i, (g, w, jid) in enumerate(zip(gs, want, ids)):
+        r, mp = done[jid]
+        assert r.status == pkg.MAP_OK, g.name
+        assert r.verdict == w.verdict, g.name
+        if flags[i] == pkg.MAP_FLAG_EARLY_EXIT:
+            assert r.batch_jobs == 1
+            continue
+        assert (r.witness, r.outer) == (w.witness, w.outer), g.name
+        assert np.array_equal(mp, w.map), g.name
+        if scheds[i] == 0:
+            assert (r.relaxations, r.inner_iters) == (w.relaxations, w.inner_total), g.name
+        else:
+            assert r.inner_iters <= w.inner_total, g.name
+        batched += r.batch_jobs > 1
+    assert batched >= len(ids) // 2  # most of the queued jobs shared a run
