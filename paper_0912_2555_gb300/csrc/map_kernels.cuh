@@ -77,7 +77,7 @@ struct Ctl {
     Cnt32 bar_gen;         // ... and generation
     Cnt32 stop_req;        // k_rounds: block 0 asks every block to stop after the next barrier
     Cnt32 self_seen;       // smallest vertex seen to become its own map value (NONE: none yet)
-    Cnt32 solo_gen;        // k_rounds: hand-backs of block 0 after rounds it ran alone
+    Cnt32 solo_gen;        // k_rounds: hand-backs of block 0 after rounds it ran alone (0 at every launch)
     Cnt32 solo_beat;       // ... and its progress in them (rounds and pushes; the waiting blocks' heartbeat)
     // fix-point loop
     uint32_t k;            // rounds completed in the current outer iteration
@@ -439,6 +439,10 @@ __device__ void epilogue_check(Ctl *c, Handles hd)
             go = 0;
         }
     }
+    // every block of the fix-point launch has left its rounds: the next launch counts block 0's
+    // hand-backs from 0 (a block that starts late must not take a hand-back already made in
+    // its own launch as its starting point)
+    v->solo_gen.v = 0;
     if (go) {
         v->outer = outer + 1;
         v->lcnt[0].v = v->lcnt[1].v = v->lcnt[2].v = 0;
@@ -479,6 +483,7 @@ __device__ void epilogue_batch(const Dev &d, Handles hd)
     volatile Ctl *v = d.ctl;
     if (threadIdx.x == 0) {
         phase_end(v, &v->ph_check);
+        v->solo_gen.v = 0; // (as in epilogue_check: the next fix-point launch counts hand-backs from 0)
         uint32_t gst = v->status; // a limit or timeout inside the fix-point loop
         if (gst == ST_OK && timed_out(v)) gst = ST_TIMEOUT;
         s_gst = gst;
@@ -1321,7 +1326,7 @@ __global__ void __launch_bounds__(256, PULL ? MAPGPU_ROUNDS_PULL_MIN_BLOCKS : MA
     if (threadIdx.x == 0) {
         s_solo[0] = vc->solo_max;
         s_solo[1] = vc->solo_fmax;
-        s_solo[2] = vc->solo_gen.v;
+        s_solo[2] = 0; // hand-backs seen: every launch starts from 0 (the check epilogue resets the count)
         s_solo[3] = vc->lc_passes; // (block-local passes per round, asynchronous single graphs)
     }
     __syncthreads();

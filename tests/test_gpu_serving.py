@@ -204,3 +204,43 @@ def test_queued_jobs_share_batched_runs(pkg):
             assert r.inner_iters <= w.inner_total, g.name
         batched += r.batch_jobs > 1
     assert batched >= len(ids) // 2  # most of the queued jobs shared a run
+
+
+def test_many_workers_many_small_jobs(pkg):
+    """Eight workers, one job each (no batching), hundreds of small jobs submitted at once: the
+    device is shared by up to eight cooperative fix-point launches plus the others' set-up and
+    dense rounds, so a launch's blocks may start well apart.  Rounds over few vertices run in
+    block 0 alone while the other blocks wait for its hand-back; every job must finish with
+    exactly its own result (a late-starting block must not miss or mistake a hand-back)."""
+    gs, scheds = [], []
+    for seed in range(320):
+        rng = np.random.default_rng(9100 + seed)
+        kind = seed % 4
+        if kind == 0:
+            g = mapgen.tiny_graph(seed + 5000, int(rng.integers(20, 400)), max_deg=int(rng.integers(1, 5)),
+                                  acc_p=float(rng.choice([0.02, 0.1, 0.3])))
+        elif kind in (1, 2):
+            g = mapgen.layered_graph(int(rng.integers(2000, 40000)), int(rng.integers(6, 30)), seed=seed,
+                                     plant=bool(seed % 3 == 0))
+        else:
+            g = mapgen.product_graph(4, int(rng.integers(4, 6)), interleave=bool(seed % 2))
+        gs.append(g)
+        scheds.append(int(seed % 2))
+    want = [oracle.run_graph(g) for g in gs]
+    with pkg.Server(slots=8, max_batch=1) as sv:
+        ids = [sv.submit(g.n, g.rowptr, g.colidx if g.m else None, pkg.pack_bits(g.acc), sched=sc)
+               for g, sc in zip(gs, scheds)]
+        results = [None] * len(ids)
+        deadline = time.time() + 180
+        while any(r is None for r in results) and time.time() < deadline:
+            for i, jid in enumerate(ids):
+                if results[i] is None:
+                    results[i] = sv.poll(jid)
+            time.sleep(0.001)
+    assert all(r is not None for r in results)
+    for g, w, sc, (r, mp) in zip(gs, want, scheds, results):
+        assert r.batch_jobs == 1
+        assert (r.status, r.verdict, r.witness, r.outer) == (pkg.MAP_OK, w.verdict, w.witness, w.outer), g.name
+        assert np.array_equal(mp, w.map), g.name
+        if sc == 0:
+            assert (r.relaxations, r.inner_iters) == (w.relaxations, w.inner_total), g.name
