@@ -193,6 +193,16 @@ int rounds_occupancy()
 }
 
 // the same for the variant with pull rounds (its grid is the handle's, at most this many blocks per SM)
+int func_occupancy()
+{
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, mapk::k_func, 256, 0) != cudaSuccess) {
+        cudaGetLastError();
+        o = 1;
+    }
+    return std::max(1, o);
+}
+
 int pull_occupancy()
 {
     int occ = 1 << 30, o = 0;
@@ -274,11 +284,14 @@ struct map_graph {
     bool fstart_on = false;
     bool tuned_fstart = false; // map_autotune found the frontier start faster on this graph
     bool pull_on = false;     // the launches being issued may pull (the fix-point kernel's pull variant)
+    bool functional = false;  // every row holds at most one entry (set-up): pointer doubling applies
+    bool func_on = false;     // the launches being issued propagate by pointer doubling (k_func)
     // the whole run as one CUDA graph, per schedule, start and kernel variant (built on first
     // use): index sched + 2 * frontier start + 4 * pull variant
-    cudaGraph_t graph[8] = {};
-    cudaGraphExec_t exec[8] = {};
-    mapk::Handles handles[8] = {};
+    // captured runs: slot = schedule + 2 (frontier start) + 4 (pull variant); 8 = pointer doubling
+    cudaGraph_t graph[9] = {};
+    cudaGraphExec_t exec[9] = {};
+    mapk::Handles handles[9] = {};
 };
 
 namespace {
@@ -286,7 +299,7 @@ namespace {
 void free_graph(map_graph *g)
 {
     if (!g) return;
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < 9; ++i) {
         if (g->exec[i]) cudaGraphExecDestroy(g->exec[i]);
         if (g->graph[i]) cudaGraphDestroy(g->graph[i]);
     }
@@ -415,6 +428,13 @@ int launch_dense(map_graph *g, cudaStream_t s, mapk::Handles hd)
 }
 
 // the fix-point loop: one cooperative launch (its grid barrier needs every block resident)
+// the captured run a schedule uses with the launches' current choices
+int run_slot(const map_graph *g, int sched)
+{
+    if (g->func_on && sched == MAP_SCHED_ASYNC) return 8;
+    return sched + (g->fstart_on ? 2 : 0) + (g->pull_on ? 4 : 0);
+}
+
 int launch_rounds(map_graph *g, cudaStream_t s, bool sync_sched, mapk::Handles hd)
 {
     const mapk::Dev d = dev_of(g);
@@ -431,7 +451,11 @@ int launch_rounds(map_graph *g, cudaStream_t s, bool sync_sched, mapk::Handles h
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (sync_sched && g->pull_on) CK(cudaLaunchKernelEx(&cfg, mapk::k_rounds<true, true>, d, hd));
+    if (g->func_on && !sync_sched) { // pointer doubling (its own occupancy)
+        static const int occ_func = func_occupancy();
+        cfg.gridDim = dim3((unsigned)std::min(g->rounds_grid, g->sms * occ_func));
+        CK(cudaLaunchKernelEx(&cfg, mapk::k_func, d, hd));
+    } else if (sync_sched && g->pull_on) CK(cudaLaunchKernelEx(&cfg, mapk::k_rounds<true, true>, d, hd));
     else if (sync_sched) CK(cudaLaunchKernelEx(&cfg, mapk::k_rounds<true, false>, d, hd));
     else if (g->pull_on) CK(cudaLaunchKernelEx(&cfg, mapk::k_rounds<false, true>, d, hd));
     else CK(cudaLaunchKernelEx(&cfg, mapk::k_rounds<false, false>, d, hd));
@@ -491,7 +515,7 @@ int add_while(cudaStream_t cs, unsigned long long handle, cudaGraph_t *body)
 
 int build_run_graph(map_graph *g, int sched)
 {
-    const int slot = sched + (g->fstart_on ? 2 : 0) + (g->pull_on ? 4 : 0);
+    const int slot = run_slot(g, sched);
     if (g->exec[slot]) return MAP_OK;
     const bool sync_sched = sched == MAP_SCHED_SYNC;
     cudaStream_t cs;
@@ -717,7 +741,8 @@ int create_graph(uint32_t n, uint64_t m, cudaStream_t s, const char *who, Upload
     };
     mapk::k_ingest<<<grid_for(g, std::max<uint64_t>(m / 4, n), 1), 256, 0, s>>>(
         n, g->in_rowptr ? g->in_rowptr : g->rowptr, g->in_rowptr ? g->rowptr : nullptr, m,
-        g->in_colidx ? g->in_colidx : g->colidx, g->colidx, g->acc0, g->rrowptr, rank, &g->ctl->bad);
+        g->in_colidx ? g->in_colidx : g->colidx, g->colidx, g->acc0, g->rrowptr, rank, &g->ctl->bad,
+        &g->ctl->long_rows);
     g->in_rowptr = g->in_colidx = nullptr;
     if ((rc = ck(cudaGetLastError(), "validate")) || (rc = read_ctl(g))) {
         free_rank();
@@ -730,6 +755,7 @@ int create_graph(uint32_t n, uint64_t m, cudaStream_t s, const char *who, Upload
         return fail(MAP_ERR_CSR, "%s: invalid CSR (decreasing rowptr or colidx out of range)", who);
     }
     g->nacc0 = g->h_ctl->elim.v;
+    g->functional = m > 0 && g->h_ctl->long_rows == 0;
 
     // reverse CSR: scan of the histogram, scatter by rank
     if ((rc = scan_inclusive(g->rrowptr, (uint64_t)n + 1, s))) {
@@ -836,8 +862,6 @@ static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint
     const bool fstart = ((opts.flags & MAP_FLAG_FRONTIER_START) ||
                          (g->tuned_fstart && !(opts.flags & MAP_FLAG_DENSE_START))) &&
                         g->nacc0 > 0;
-    // the worklist fix-point for the asynchronous schedule of a single graph (unless map_autotune
-    // chose the rounds for this handle); a limit of one round per outer iteration needs the rounds
     if ((opts.flags & MAP_FLAG_PUSH) && (opts.flags & MAP_FLAG_PULL))
         return fail(MAP_ERR_ARG, "map_run: MAP_FLAG_PUSH and MAP_FLAG_PULL together");
     struct FstartOff { // the flags only hold for the launches of this run
@@ -846,6 +870,7 @@ static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint
         {
             g->fstart_on = false;
             g->pull_on = false;
+            g->func_on = false;
         }
     } fstart_off{g};
     memset(res, 0, sizeof *res);
@@ -867,7 +892,10 @@ static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint
     init.early_exit = (opts.flags & MAP_FLAG_EARLY_EXIT) ? 1 : 0;
     init.timeout_ns = (uint64_t)(opts.timeout_ms ? opts.timeout_ms : 120000u) * 1000000ull;
     init.witness.v = mapk::NONE;
-    init.pull_min = (opts.flags & MAP_FLAG_PULL) ? 1u : (opts.flags & MAP_FLAG_PUSH) ? 0u : g->pull_min;
+    // an asynchronous single-graph run with the dense start on a graph whose every row holds at
+    // most one entry propagates by pointer doubling (MAP_FLAG_PUSH or MAP_FLAG_PULL keep the rounds)
+    g->func_on = g->functional && !sync_sched && !fstart && !g->comp && !(opts.flags & (MAP_FLAG_PUSH | MAP_FLAG_PULL));
+    init.pull_min = g->func_on ? 0u : (opts.flags & MAP_FLAG_PULL) ? 1u : (opts.flags & MAP_FLAG_PUSH) ? 0u : g->pull_min;
     g->pull_on = init.pull_min != 0;
     init.solo_max = g->solo_max;
     init.lc_passes = g->lc_passes;
@@ -896,7 +924,7 @@ static int run_impl(map_graph *g, const map_opts *opts_in, map_result *res, uint
         CK(cudaEventRecord(g->ev[0], s));
         for (uint32_t k = 0; k < reps; ++k) { // (the mirror is read back only after the last run)
             CK(cudaMemcpyAsync(g->ctl, g->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
-            CK(cudaGraphLaunch(g->exec[opts.sched + (fstart ? 2 : 0) + (g->pull_on ? 4 : 0)], s));
+            CK(cudaGraphLaunch(g->exec[run_slot(g, (int)opts.sched)], s));
         }
         CK(cudaEventRecord(g->ev[1], s));
         if ((rc = read_ctl(g))) return rc;
@@ -1023,7 +1051,7 @@ static void set_shapes(map_graph *g, uint32_t dense_bps, uint32_t rounds_bps)
         1, std::min<uint64_t>((ntiles + mapk::WT_WARPS - 1) / mapk::WT_WARPS, (uint64_t)g->sms * dense_bps));
     g->rounds_grid = (int)std::max<uint64_t>(
         1, std::min<uint64_t>(((uint64_t)g->n + 255) / 256, (uint64_t)g->sms * rounds_bps));
-    for (int i = 0; i < 8; ++i) { // the captured graphs hold the old shapes
+    for (int i = 0; i < 9; ++i) { // the captured graphs hold the old shapes
         if (g->exec[i]) cudaGraphExecDestroy(g->exec[i]);
         if (g->graph[i]) cudaGraphDestroy(g->graph[i]);
         g->exec[i] = nullptr;

@@ -108,7 +108,8 @@ struct Ctl {
     uint32_t solo_r, solo_nl, solo_nf, solo_status; // block 0's state when it hands back
     uint32_t lc_passes;    // asynchronous single graphs: block-local passes per round
     uint32_t gave_up;      // a bounded device wait gave up (ST_TIMEOUT): 1 = grid barrier, 2 = the
-    uint32_t pad1;         //   hand-back of one-block rounds; 0 = none (the time limit, if any)
+                           //   hand-back of one-block rounds; 0 = none (the time limit, if any)
+    uint32_t long_rows;    // set-up: some row holds two entries or more (else: pointer doubling applies)
     // %globaltimer stamps of the phases (ns), summed over the run: the end of the last phase
     // (t_mark), the dense rounds, the fix-point rounds, the self-map tests and eliminations.  Each
     // phase runs from the end of the one before it, so gaps between launches count to the next.
@@ -1587,6 +1588,122 @@ __global__ void __launch_bounds__(256, PULL ? MAPGPU_ROUNDS_PULL_MIN_BLOCKS : MA
     if (vc->use_graph) check_phase(d, hd, status == ST_OK);
 }
 
+// ------------------------------------------------------- pointer doubling --
+//
+// The fix-point of one outer iteration, asynchronous schedule, on a graph whose every row holds
+// at most one entry (the state graph of a deterministic system: each state has one successor,
+// and its row is that one entry).  Row v then takes its value from one vertex only, src(v), so
+// the map value of v is the largest offer along the chain src(v), src(src(v)), ...  With
+// Q_k(v) = src^{2^k}(v) (NONE past the end of the chain) and B_k(v) the largest offer of
+// src^j(v) for 1 <= j <= 2^k, the dense round gives B_0, and
+//     B_{k+1}(v) = max(B_k(v), B_k(Q_k(v))),   Q_{k+1}(v) = Q_k(Q_k(v)).
+// A round is one pass over every vertex: a pure gather (v alone writes its own value; a value
+// another vertex raised earlier in the same round covers a longer stretch of its chain and is
+// as valid), with the pointers double-buffered.  When a round raises nothing, B_k covers the
+// whole chain (a vertex at distance d in (2^{k+1}, 2^{k+2}] from v lies within 2^{k+1} of
+// Q_k(v), whose value B_{k+1}(v) already took), so the loop stops there: about log2 of the
+// propagation depth rounds instead of the depth.  The values are the least fix-point's, as the
+// oracle's rounds give them; the round count is the number of passes (at most the synchronous
+// schedule's rounds).
+__global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_func(const Dev d, Handles hd)
+{
+    __shared__ uint32_t s_stage[8][SB_ENTRIES];
+    __shared__ uint32_t s_cnt[8][1], s_base[1];
+    __shared__ uint32_t s_vals[4];
+    Ctl *ctl = d.ctl;
+    volatile Ctl *vc = ctl;
+    const unsigned lane = lane_id();
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    const uint32_t n = d.n, max_inner = vc->max_inner;
+    const bool early = vc->early_exit != 0;
+    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t status = ST_OK;
+    unsigned long long relax = 0;
+    uint32_t r = 1;              // rounds completed (round 1: the dense round)
+    uint32_t nl = vc->lcnt[1].v; // vertices that got a value in the dense round
+    if (early && vc->self_seen.v != NONE) nl = 0; // the dense round already found a self-mapped vertex
+    if (nl && max_inner < 2) status = ST_LIMIT;
+    uint32_t *pa = d.flist[0], *pb = d.flist[1]; // Q_k and Q_{k+1}
+    if (nl && status == ST_OK) {
+        // Q_0: the one entry of each row (its flag bit cleared), or NONE
+        for (uint64_t v = tid; v < n; v += nthreads) {
+            const uint32_t b = __ldg(d.rowptr + v), e = __ldg(d.rowptr + v + 1);
+            pa[v] = e > b ? (__ldcg(d.colidx + b) & 0x7FFFFFFFu) : NONE;
+        }
+        if (!grid_barrier(ctl)) status = ST_TIMEOUT;
+    }
+    // vertices raised from "no value" join the touched list (and the stale bitmap)
+    uint32_t *const dst[1][2] = {{d.touched, nullptr}};
+    unsigned int *const ctr[1] = {&ctl->tcnt.v};
+    Stage<1> st;
+    st.buf = s_stage[threadIdx.x >> 5];
+    st.cnt[0] = 0;
+    while (nl && status == ST_OK) {
+        const uint32_t rr = r + 1, p_out = rr % 3, p_free = (rr + 1) % 3;
+        if (lead) vc->lcnt[p_free].v = 0; // (counts the round after this one)
+        uint32_t changed = 0, pulls = 0;
+        // warp-uniform steps (every lane takes part in the appends)
+        for (uint64_t base = tid - lane; base < n; base += nthreads) {
+            const uint64_t v = base + lane;
+            bool fresh = false;
+            if (v < n) {
+                // (both buffers and the values are written within this launch: read them at L2)
+                const uint32_t q = __ldcg(pa + v);
+                uint32_t nxt = NONE;
+                if (q != NONE) {
+                    nxt = __ldcg(pa + q);
+                    const uint32_t bq = __ldcg(d.mval + q);
+                    if (bq) {
+                        ++pulls;
+                        const uint32_t bv = __ldcg(d.mval + v);
+                        if (bq > bv) {
+                            d.mval[v] = bq; // (v's own thread is its only writer in this round)
+                            ++changed;
+                            fresh = bv == 0;
+                            if (bq == (uint32_t)v + 1u) atomicMin(&ctl->self_seen.v, (uint32_t)v); // v reaches itself
+                            if (fresh && d.stale) atomicOr(d.stale + (v >> 5), 1u << (v & 31u));
+                        }
+                    }
+                }
+                pb[v] = nxt;
+            }
+            stage_append<1>(st, 0, fresh, (uint32_t)v, dst, ctr);
+        }
+        stage_flush_block<1>(st, s_cnt, s_base, dst, ctr);
+        st.cnt[0] = 0;
+        const uint32_t wc = __reduce_add_sync(0xFFFFFFFFu, changed);
+        if (lane == 0 && wc) atomicAdd(&ctl->lcnt[p_out].v, wc);
+        relax += pulls;
+        if (lead && timed_out(vc)) vc->stop_req.v = 1;
+        if (!grid_barrier(ctl, p_out, s_vals)) {
+            status = ST_TIMEOUT;
+            break;
+        }
+        r = rr;
+        nl = s_vals[0]; // vertices raised in this round
+        if (early && nl && s_vals[2] != NONE) { // stop here: the recorded vertex is the witness
+            nl = 0;
+            if (lead) vc->early_hit = 1;
+        }
+        if (s_vals[3]) status = ST_TIMEOUT;
+        else if (nl && r + 1 > max_inner) status = ST_LIMIT;
+        uint32_t *const tmp = pa;
+        pa = pb;
+        pb = tmp;
+    }
+    // (relaxations of an asynchronous run: m per outer iteration, plus one per value taken)
+    block_add_u64(relax, (unsigned long long *)&ctl->relax.v);
+    block_add_u64(relax, (unsigned long long *)&ctl->frontier_rows.v); // (the vertices that took one)
+    if (threadIdx.x == 0 && status != ST_OK) vc->status = status;
+    if (lead) {
+        vc->k = r;
+        phase_end(vc, &vc->ph_rounds); // every block has passed the last barrier
+        __threadfence();
+    }
+    if (vc->use_graph) check_phase(d, hd, status == ST_OK);
+}
+
 // Batched runs, start of a run: every graph's record (the host keeps off, m, nacc0).
 __global__ void k_batch_begin(const Dev d)
 {
@@ -1898,15 +2015,16 @@ __device__ __forceinline__ uint32_t ingest_one(uint32_t u, uint32_t n, const uin
 // page-locked host memory read over the host link). colidx_in and colidx_out 16-byte aligned
 // (they may be the same array); the inputs are read once each. rank[i] = the number of entries
 // before entry i that hold the same vertex (the count each one's increment returned: entry i's
-// place in that vertex's reader list, in an arbitrary but fixed order).
+// place in that vertex's reader list, in an arbitrary but fixed order); *long_rows is set when
+// some row holds two entries or more.
 __global__ void k_ingest(uint32_t n, const uint32_t *rowptr_in, uint32_t *rowptr_out, uint64_t m,
                          const uint32_t *colidx_in, uint32_t *colidx_out, const uint32_t *__restrict__ acc,
-                         uint32_t *cnt, uint32_t *rank, uint32_t *bad)
+                         uint32_t *cnt, uint32_t *rank, uint32_t *bad, uint32_t *long_rows)
 {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned lane = lane_id();
-    bool b = false;
+    bool b = false, lr = false;
     // rowptr[0..n]: warp-uniform steps of 32 entries; a lane's successor entry comes from the next
     // lane (lane 31 loads it)
     for (uint64_t i0 = tid - lane; i0 <= n; i0 += stride) {
@@ -1914,7 +2032,10 @@ __global__ void k_ingest(uint32_t n, const uint32_t *rowptr_in, uint32_t *rowptr
         const uint32_t a = i <= n ? rowptr_in[i] : 0u;
         uint32_t next = __shfl_down_sync(0xFFFFFFFFu, a, 1);
         if (lane == 31 && i < n) next = rowptr_in[i + 1];
-        if (i < n) b |= a > next;
+        if (i < n) {
+            b |= a > next;
+            lr |= next - a > 1u;
+        }
         if (rowptr_out && i <= n) rowptr_out[i] = a;
     }
     const uint64_t m4 = m / 4;
@@ -1932,6 +2053,7 @@ __global__ void k_ingest(uint32_t n, const uint32_t *rowptr_in, uint32_t *rowptr
     }
     for (uint64_t i = m4 * 4 + tid; i < m; i += stride) colidx_out[i] = ingest_one(colidx_in[i], n, acc, cnt, b, rank[i]);
     if (__any_sync(0xFFFFFFFFu, b) && lane == 0) *bad = 1;
+    if (__any_sync(0xFFFFFFFFu, lr) && lane == 0) *long_rows = 1;
 }
 
 // Reverse CSR scatter from the ranks k_ingest recorded: entry i of row w holding u goes to slot
