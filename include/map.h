@@ -65,7 +65,13 @@ enum { MAP_NO_CYCLE = 0, MAP_CYCLE = 1 };
  *    a sweep may be read in the same sweep.  The fix-point (the least one, which
  *    is unique) and therefore every map vector, the verdict, the witness and the
  *    outer count are the same as under SYNC; the sweep count is at most the
- *    SYNC round count. */
+ *    SYNC round count.  On a graph whose every row holds at most one entry (the
+ *    state graph of a deterministic system; map_create detects it), a single
+ *    graph's run with the dense start, without MAP_FLAG_PUSH / MAP_FLAG_PULL,
+ *    propagates by pointer doubling instead: each pass takes, for every vertex,
+ *    the value found at the end of its jump pointer along its chain of entries
+ *    and doubles the pointer, so about log2(propagation depth) passes replace
+ *    the sweeps (a sweep count is then that pass count). */
 enum { MAP_SCHED_SYNC = 0, MAP_SCHED_ASYNC = 1 };
 
 /* opts.flags */
@@ -97,7 +103,8 @@ enum { MAP_SCHED_SYNC = 0, MAP_SCHED_ASYNC = 1 };
                                    by default with the dense round).  Both start flags together: MAP_ERR_ARG. */
 
 #define MAP_FLAG_PUSH 64u  /* every round after round 1 pushes from the vertices changed in the round before
-                              to their readers (the reverse CSR) */
+                              to their readers (the reverse CSR); also keeps a graph whose rows hold one
+                              entry at most on the rounds instead of pointer doubling */
 #define MAP_FLAG_PULL 128u /* every round after round 1 pulls: each row takes the largest offer of the
                               vertices in it that changed in the round before (one pass over the whole
                               matrix, like the dense round).  Without either flag a round pulls when its
@@ -139,7 +146,8 @@ typedef struct {
     uint64_t inner_iters;     /* rounds (or sweeps) summed over outer iterations */
     uint64_t relaxations;     /* edges examined.  SYNC (canonical): the row lengths of every
                                  round's frontier (round 1: all m); ASYNC: m per outer
-                                 iteration plus one per push (batched ASYNC runs: frontier) */
+                                 iteration plus one per push (batched ASYNC runs: frontier;
+                                 pointer doubling: plus one per value taken along a chain) */
     uint64_t edges_total;     /* m x outer_iters: the edges a fix-point must examine at least once */
     double device_ms;         /* stream time of the whole run (CUDA events) */
     double dense_ms;          /* time of the dense rounds summed over the run: CUDA events around each
