@@ -120,6 +120,18 @@ class Clocks:
                 out = ""
             self.lines = [line for line in out.splitlines() if line.strip()]
 
+    def stamps(self):
+        """The time stamp of every sample taken (nvidia-smi's own, host clock)."""
+        import datetime
+
+        out = []
+        for line in getattr(self, "lines", []):
+            try:
+                out.append(datetime.datetime.strptime(line.split(",")[0].strip(), "%Y/%m/%d %H:%M:%S.%f"))
+            except ValueError:
+                continue
+        return out
+
     def summary(self):
         import datetime
 
@@ -152,6 +164,16 @@ class Clocks:
         return {"sm_mhz": statistics.median([r[1] for r in sel]) if sel else None,
                 "sm_max_mhz": sel[-1][2] if sel else None, "reasons": sorted(reasons), "samples": len(sel),
                 "window": window}
+
+
+def queries_per_window(stamps, windows, lead_ms=50):
+    """For each (start, end) window: the clock samples stamped inside it or up to lead_ms before
+    its start (a query holds driver locks while it runs, so one that began just before a window
+    can still stall a CUDA call inside it)."""
+    import datetime
+
+    lead = datetime.timedelta(milliseconds=lead_ms)
+    return [sum(1 for t in stamps if a - lead <= t <= b) for a, b in windows]
 
 
 def replica_value(ms, edges, device="cuda"):
@@ -635,25 +657,33 @@ def main():
     # each step timed on its own (host clock, device synchronised on both sides); the value is
     # taken at the median step, so that one step stalled on the host does not decide it, and
     # every step's time is reported with it
-    e2e_ms, e2e_edges = [], 0
+    import datetime
+
+    e2e_ms, e2e_edges, e2e_win = [], 0, []
     with Clocks(local, period_ms=500) as e2e_clk:
         for _ in range(2 if args.e2e_steps else 0):
             e2e_step()  # warm-up: the device memory pool and the pinned control slots reach their size
         e2e_clk.mark_start()
         for _ in range(args.e2e_steps):
             torch.cuda.synchronize()
+            w0 = datetime.datetime.now()
             t0 = time.perf_counter()
             e2e_edges = e2e_step().edges_total
             torch.cuda.synchronize()
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
+            e2e_win.append((w0, datetime.datetime.now()))
         e2e_clk.mark_end()
     e2e = None
     if args.e2e_steps:
+        # clock queries that began in a step or up to 50 ms before it: a query holds driver locks
+        # while it runs, and a CUDA call that meets one waits
+        queries = queries_per_window(e2e_clk.stamps(), e2e_win, lead_ms=50)
         med = float(np.median(e2e_ms))
         e2e = {"value": e2e_edges / (med / 1e3) / 1e9 * ws, "unit": "GTEPS",
                "h2d_bytes_per_step": 4 * (g.n + 1) + 4 * g.m + 4 * words, "d2h_bytes_per_step": 4 * g.n,
                "ms_per_step_median": med, "ms_per_step": e2e_ms, "value_from": "median step",
                "calls_ms": e2e_split[-args.e2e_steps:],
+               "clock_queries_per_step": queries,
                "clocks": e2e_clk.summary(),
                "includes": "map_create (H2D, validation, transpose) + map_run + map D2H + map_destroy"}
 

@@ -61,3 +61,16 @@ def test_dense_traffic_reference_follows_the_dense_section(tmp_path, monkeypatch
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     traffic, note = bench._dense_traffic(1.0)
     assert traffic is None and "changed" in note
+
+
+def test_clock_queries_are_matched_to_the_steps_they_may_stall():
+    t0 = datetime.datetime(2026, 12, 4, 2, 0, 0)
+    ms = datetime.timedelta(milliseconds=1)
+    c = bench.Clocks(0)
+    c.lines = [_line(t0 + k * 500 * ms, 2070) for k in range(4)] + ["garbage line"]
+    stamps = c.stamps()
+    assert stamps == [t0 + k * 500 * ms for k in range(4)]
+    # steps of 30 ms: one holds a sample, one starts 20 ms after a sample, one has none near it
+    wins = [(t0 + 480 * ms, t0 + 510 * ms), (t0 + 1020 * ms, t0 + 1050 * ms), (t0 + 1200 * ms, t0 + 1230 * ms)]
+    assert bench.queries_per_window(stamps, wins, lead_ms=50) == [1, 1, 0]
+    assert bench.queries_per_window(stamps, wins, lead_ms=10) == [1, 0, 0]
