@@ -1597,9 +1597,9 @@ __global__ void __launch_bounds__(256, PULL ? MAPGPU_ROUNDS_PULL_MIN_BLOCKS : MA
 // Q_k(v) = src^{2^k}(v) (NONE past the end of the chain) and B_k(v) the largest offer of
 // src^j(v) for 1 <= j <= 2^k, the dense round gives B_0, and
 //     B_{k+1}(v) = max(B_k(v), B_k(Q_k(v))),   Q_{k+1}(v) = Q_k(Q_k(v)).
-// A round is one pass over every vertex: a pure gather (v alone writes its own value; a value
-// another vertex raised earlier in the same round covers a longer stretch of its chain and is
-// as valid), with the pointers double-buffered.  When a round raises nothing, B_k covers the
+// A round is one pass over every vertex: a pure gather of one 8-byte (B_k, Q_k) pair at Q_k(v),
+// the pairs double-buffered (v alone writes its own pair, and its value when it rises).  When a
+// round raises nothing, B_k covers the
 // whole chain (a vertex at distance d in (2^{k+1}, 2^{k+2}] from v lies within 2^{k+1} of
 // Q_k(v), whose value B_{k+1}(v) already took), so the loop stops there: about log2 of the
 // propagation depth rounds instead of the depth.  The values are the least fix-point's, as the
@@ -1624,12 +1624,14 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_func(const De
     uint32_t nl = vc->lcnt[1].v; // vertices that got a value in the dense round
     if (early && vc->self_seen.v != NONE) nl = 0; // the dense round already found a self-mapped vertex
     if (nl && max_inner < 2) status = ST_LIMIT;
-    uint32_t *pa = d.flist[0], *pb = d.flist[1]; // Q_k and Q_{k+1}
+    // (B_k(v), Q_k(v)) and (B_{k+1}(v), Q_{k+1}(v)), 8n bytes each, in the change-list and
+    // frontier-list spaces (12n bytes each, unused by these rounds), so that one gather brings both
+    uint2 *pa = reinterpret_cast<uint2 *>(d.list[0]), *pb = reinterpret_cast<uint2 *>(d.flist[0]);
     if (nl && status == ST_OK) {
-        // Q_0: the one entry of each row (its flag bit cleared), or NONE
+        // B_0: the dense round's values; Q_0: the one entry of each row (its flag bit cleared), or NONE
         for (uint64_t v = tid; v < n; v += nthreads) {
             const uint32_t b = __ldg(d.rowptr + v), e = __ldg(d.rowptr + v + 1);
-            pa[v] = e > b ? (__ldcg(d.colidx + b) & 0x7FFFFFFFu) : NONE;
+            pa[v] = make_uint2(__ldcg(d.mval + v), e > b ? (__ldcg(d.colidx + b) & 0x7FFFFFFFu) : NONE);
         }
         if (!grid_barrier(ctl)) status = ST_TIMEOUT;
     }
@@ -1648,20 +1650,20 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_func(const De
             const uint64_t v = base + lane;
             bool fresh = false;
             if (v < n) {
-                // (both buffers and the values are written within this launch: read them at L2)
-                const uint32_t q = __ldcg(pa + v);
-                uint32_t nxt = NONE;
-                if (q != NONE) {
-                    nxt = __ldcg(pa + q);
-                    const uint32_t bq = __ldcg(d.mval + q);
-                    if (bq) {
+                // (both buffers are written within this launch: read them at L2)
+                const uint2 cur = __ldcg(pa + v);
+                uint2 nxt = make_uint2(cur.x, NONE);
+                if (cur.y != NONE) {
+                    const uint2 at = __ldcg(pa + cur.y); // (B_k, Q_k) at Q_k(v)
+                    nxt.y = at.y;
+                    if (at.x) {
                         ++pulls;
-                        const uint32_t bv = __ldcg(d.mval + v);
-                        if (bq > bv) {
-                            d.mval[v] = bq; // (v's own thread is its only writer in this round)
+                        if (at.x > cur.x) {
+                            nxt.x = at.x;
+                            d.mval[v] = at.x; // (v's own thread is its only writer)
                             ++changed;
-                            fresh = bv == 0;
-                            if (bq == (uint32_t)v + 1u) atomicMin(&ctl->self_seen.v, (uint32_t)v); // v reaches itself
+                            fresh = cur.x == 0;
+                            if (at.x == (uint32_t)v + 1u) atomicMin(&ctl->self_seen.v, (uint32_t)v); // v reaches itself
                             if (fresh && d.stale) atomicOr(d.stale + (v >> 5), 1u << (v & 31u));
                         }
                     }
@@ -1688,7 +1690,7 @@ __global__ void __launch_bounds__(256, MAPGPU_ROUNDS_MIN_BLOCKS) k_func(const De
         }
         if (s_vals[3]) status = ST_TIMEOUT;
         else if (nl && r + 1 > max_inner) status = ST_LIMIT;
-        uint32_t *const tmp = pa;
+        uint2 *const tmp = pa;
         pa = pb;
         pb = tmp;
     }
