@@ -550,7 +550,9 @@ def main():
     ovalue, oms, _ = replica_value(e0.elapsed_time(e1), sum(r.edges_total for r in ores), device="cuda")
     other_line = {"sched": "sync" if other == 0 else "async", "value": ovalue, "unit": "GTEPS",
                   "ms_per_step": oms / args.steps, "rounds_per_run": sum(ores[0].rounds),
-                  "relaxations_per_run": ores[0].relaxations, "canonical_counts": bool(ores[0].inner_canonical),
+                  "relaxations_per_run": ores[0].relaxations,
+                  "work_ratio": ores[0].relaxations / (g.m * ores[0].outer) if ores[0].outer else None,
+                  "canonical_counts": bool(ores[0].inner_canonical),
                   "same_result": (ores[0].verdict, ores[0].witness, ores[0].outer) == (r0.verdict, r0.witness,
                                                                                        r0.outer)}
 
@@ -692,7 +694,10 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": workload_config(g, layers),
             "run": {"sched": "sync" if args.sched == 0 else "async", "start": args.start, "outer_iters": r0.outer,
-                    "rounds_per_run": sum(r0.rounds), "relaxations_per_run": r0.relaxations, "verdict": r0.verdict,
+                    "rounds_per_run": sum(r0.rounds), "relaxations_per_run": r0.relaxations,
+                    # relaxations executed / (m x outer iterations): the edges the run examined per edge
+                    # the metric counts (asynchronous: every push counted as one)
+                    "work_ratio": r0.relaxations / (g.m * r0.outer) if r0.outer else None, "verdict": r0.verdict,
                     "placement": "replicas, one per GPU" if ws > 1 else "single GPU"},
             "roofline": roofline, "run_roofline": run_roofline, "phases": phases, "e2e": e2e,
             "other_schedule": other_line, "frontier_start": frontier_line,
