@@ -311,9 +311,9 @@ MAP_API int map_server_destroy(map_server *sv);
  *     dense round's 16-byte loads in flight per lane (2, 4 or 8);
  *  5. the start of every outer iteration: the dense round or the frontier
  *     start (MAP_FLAG_DENSE_START / MAP_FLAG_FRONTIER_START still force either).
- * It takes about thirty runs; results are unaffected (none of these
- * choices changes any map vector, verdict, witness or outer count, nor the
- * counts of the synchronous schedule).
+ * It takes about fifty runs (counted in `trials`); results are unaffected
+ * (none of these choices changes any map vector, verdict, witness or outer
+ * count, nor the counts of the synchronous schedule).
  *
  * The defaults of a new handle (before any map_autotune) can be set from the
  * environment, read by map_create and the other creating calls:
