@@ -1191,7 +1191,10 @@ __device__ __forceinline__ void check_phase(const Dev &d, Handles hd, bool work 
                 if (d.comp) atomicMin(&d.cs[c].witness, u);
             }
             const uint32_t bit = 1u << (u & 31u);
-            if (x != 0 && (*(volatile uint32_t *)(d.acc + (u >> 5)) & bit)) {
+            // a plain load (it may be served by L1 and be stale): it only saves the atomic when
+            // the bit is already clear, and the atomic's old value decides who removed u.  Many
+            // vertices share a few map values (state graphs), and their reads stay off the L2 line
+            if (x != 0 && (d.acc[u >> 5] & bit)) {
                 const uint32_t old = atomicAnd(d.acc + (u >> 5), ~bit);
                 if (old & bit) { // this thread removed u
                     elim++;
