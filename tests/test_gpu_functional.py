@@ -164,3 +164,24 @@ def test_early_exit_and_limits(pkg, seed):
     if want.outer > 1:
         assert r1.status == pkg.MAP_ERR_LIMIT and r1.outer == 1
         assert np.array_equal(out1, want.trace[0][1])
+
+
+@pytest.mark.parametrize("n,seed", [(5000, 31), (300_001, 32)])
+def test_other_schedules_after_doubling_on_one_handle(pkg, n, seed):
+    """Pointer doubling keeps its (value, pointer) pairs in the change-list and frontier-list
+    spaces; the runs that follow on the same handle (synchronous rounds with their canonical
+    counts, forced push rounds, the frontier start, doubling again) must still equal the oracle."""
+    g = functional_graph(n, seed, acc_p=0.01, none_p=0.02)
+    want = oracle.run_graph(g)
+    h = pkg.map_create(g.n, g.rowptr, g.colidx, pkg.pack_bits(g.acc))
+    try:
+        plan = [(1, 0), (0, 0), (1, pkg.MAP_FLAG_PUSH), (1, 0), (1, pkg.MAP_FLAG_FRONTIER_START),
+                (0, pkg.MAP_FLAG_FRONTIER_START), (1, 0)]
+        for sched, flags in plan:
+            out = np.empty(g.n, np.uint32)
+            r = pkg.map_run(h, sched=sched, flags=flags, map_out=out)
+            same_as_oracle(pkg, r, out, want)
+            if sched == 0:
+                assert (r.rounds, r.relaxations) == (want.rounds, want.relaxations)
+    finally:
+        pkg.map_destroy(h)
