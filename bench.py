@@ -251,6 +251,16 @@ def cpu_baseline(g, outer):
                       f"including the oracle's own set-up)"}
 
 
+def doubling_bytes(n, rounds):
+    """Algorithmic bytes of the pointer-doubling fix-point of one run (one entry per row at most):
+    per outer iteration an initial pass (rowptr 4(n+1), the entries 4n at most, the dense round's
+    values 4n read, the 8-byte (value, pointer) pairs 8n written: 20n) and, for each of its
+    rounds after the dense one, a pass that reads the pairs (8n), gathers one pair per vertex (8n)
+    and writes the next pairs (8n): 24n.  An outer iteration whose dense round gave no vertex a
+    value (one round) makes no pass at all.  rounds: the run's rounds per outer iteration."""
+    return sum(20 * n + 24 * n * (k - 1) for k in rounds if k > 1)
+
+
 def configs_leg(pkg, np, torch, stream, peak, steps=10):
     """The two other single-graph workloads, resident in HBM, both schedules: the 16,384-vertex
     random graph (both variants; latency-bound, reported in microseconds per run) and the
@@ -285,6 +295,18 @@ def configs_leg(pkg, np, torch, stream, peak, steps=10):
                              "phases_ms": {"dense": r.dense_ms, "rounds": r.round_ms, "check": r.check_ms},
                              "roofline": {"bytes_per_run": alg, "achieved_gbs": alg / (ms / 1e3) / 1e9,
                                           "peak_gbs": peak, "frac": alg / (ms / 1e3) / 1e9 / peak}}
+                # a graph whose rows hold one entry at most, asynchronous with the dense start: the
+                # fix-point is pointer doubling (k_func); its own roofline from a host-stepped run
+                # with CUDA events around each launch
+                if sched == 1 and g.m and int(np.diff(g.rowptr).max()) <= 1:
+                    rp = pkg.map_run(h, sched=sched, flags=pkg.MAP_FLAG_PROFILE)
+                    if rp.dense_ms > 0 and rp.round_ms > 0:
+                        b = doubling_bytes(g.n, rp.rounds)
+                        out[name]["doubling_roofline"] = {
+                            "kernel": "k_func", "passes": [k - 1 for k in rp.rounds], "bytes_per_run": b,
+                            "ms_per_run": rp.round_ms, "achieved_gbs": b / (rp.round_ms / 1e3) / 1e9,
+                            "peak_gbs": peak, "frac": b / (rp.round_ms / 1e3) / 1e9 / peak,
+                            "timing": "CUDA events around the fix-point launch of a host-stepped run"}
         finally:
             pkg.map_destroy(h)
         return out

@@ -74,3 +74,11 @@ def test_clock_queries_are_matched_to_the_steps_they_may_stall():
     wins = [(t0 + 480 * ms, t0 + 510 * ms), (t0 + 1020 * ms, t0 + 1050 * ms), (t0 + 1200 * ms, t0 + 1230 * ms)]
     assert bench.queries_per_window(stamps, wins, lead_ms=50) == [1, 1, 0]
     assert bench.queries_per_window(stamps, wins, lead_ms=10) == [1, 0, 0]
+
+
+def test_doubling_bytes():
+    # one outer iteration of 12 rounds (the dense round and 11 doubling passes): 20n + 11 * 24n
+    assert bench.doubling_bytes(1000, [12]) == 20 * 1000 + 11 * 24 * 1000
+    # two outer iterations, the second with the dense round alone (no value: no pass at all)
+    assert bench.doubling_bytes(10, [3, 1]) == 20 * 10 + 2 * 24 * 10
+    assert bench.doubling_bytes(10, []) == 0
