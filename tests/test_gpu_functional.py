@@ -10,6 +10,7 @@ import pytest
 
 import mapgen
 import oracle
+from tests.test_doubling_model import doubling_run
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -77,6 +78,10 @@ def test_random_functional_graphs(pkg, seed):
     want = oracle.run_graph(g, keep_trace=True)
     r, out = run(pkg, g)
     same_as_oracle(pkg, r, out, want)
+    # the passes are exact doubling steps: the same round count per outer iteration as the
+    # recurrence stepped on the CPU (tests/test_doubling_model.py, pinned to brute force)
+    if g.acc.any():
+        assert list(r.rounds) == doubling_run(g)[4]
     # every outer iteration's map (host-stepped: the same kernels, one launch per step)
     h = pkg.map_create(g.n, g.rowptr, g.colidx if g.m else None, pkg.pack_bits(g.acc))
     try:
@@ -131,6 +136,7 @@ def test_product_8x7(pkg):
     want = oracle.run_graph(g)
     r, out = run(pkg, g)
     same_as_oracle(pkg, r, out, want)
+    assert list(r.rounds) == doubling_run(g)[4]
     rp, outp = run(pkg, g, flags=pkg.MAP_FLAG_PUSH)
     same_as_oracle(pkg, rp, outp, want)
     assert r.inner_iters * 5 < rp.inner_iters
