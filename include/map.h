@@ -70,8 +70,10 @@ enum { MAP_NO_CYCLE = 0, MAP_CYCLE = 1 };
  *    graph's run with the dense start, without MAP_FLAG_PUSH / MAP_FLAG_PULL,
  *    propagates by pointer doubling instead: each pass takes, for every vertex,
  *    the value found at the end of its jump pointer along its chain of entries
- *    and doubles the pointer, so about log2(propagation depth) passes replace
- *    the sweeps (a sweep count is then that pass count). */
+ *    and doubles the pointer.  With D the largest distance from a vertex to
+ *    its map value, an outer iteration then takes 2 + ceil(log2 D) rounds (the
+ *    dense round and the passes; 1 if no vertex gets a value) instead of the
+ *    1 + D synchronous rounds, and its sweep count is that round count. */
 enum { MAP_SCHED_SYNC = 0, MAP_SCHED_ASYNC = 1 };
 
 /* opts.flags */
